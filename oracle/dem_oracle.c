@@ -1,0 +1,603 @@
+/*
+ * dem_oracle.c -- plain FP64 CPU oracle for the space-time contact-detection
+ * path of Noble & Weinzierl, "Parallel local time stepping for rigid bodies
+ * represented by triangulated meshes".
+ *
+ * TEST INFRASTRUCTURE ONLY: the slow, obviously correct definition that the
+ * CUDA library is checked against.  Only tests, the smoke check and the
+ * benchmark's CPU-baseline leg load it.  It shares no code with the CUDA
+ * library.
+ *
+ * Arithmetic: IEEE binary64, compiled with -ffp-contract=off (no fused
+ * multiply-add), every expression evaluated left to right as written.  The
+ * order of operations of every formula is part of the definition: the CUDA
+ * library's FP64 decisions follow the same order so that decisions near a
+ * threshold come out the same.
+ *
+ * Pins (tests/test_oracle_*.py): closed forms for poses and triangle
+ * distances, symmetry, rigid-motion invariance, convex QP via scipy,
+ * brute-force barycentric sampling, icosphere distance bounds, closed-form
+ * collision times, k-d tree broad phase, scipy connected components.
+ */
+#include "dem_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdatomic.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { FX = 0, FY, FZ, FVX, FVY, FVZ, FQW, FQX, FQY, FQZ, FWX, FWY, FWZ, FTCUR, FDT, FEPS,
+       FRADIUS };
+
+typedef struct { double x, y, z; } vec3;
+
+static vec3 mk(double x, double y, double z) { vec3 r; r.x = x; r.y = y; r.z = z; return r; }
+static vec3 sub(vec3 a, vec3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+static double dot(vec3 a, vec3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static vec3 cross(vec3 a, vec3 b) {
+  return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+/* a + d * s, componentwise */
+static vec3 axpy(vec3 a, vec3 d, double s) { return mk(a.x + d.x * s, a.y + d.y * s, a.z + d.z * s); }
+static double clamp01(double s) { return s < 0.0 ? 0.0 : (s > 1.0 ? 1.0 : s); }
+static vec3 ld(const double *p) { return mk(p[0], p[1], p[2]); }
+static void st(double *p, vec3 v) { p[0] = v.x; p[1] = v.y; p[2] = v.z; }
+
+/* ------------------------------------------------------------------------ */
+/* Pose at time t (paper Section 2.1: snapshots of position, velocity,
+ * rotation and angular velocity; between snapshots the position moves
+ * linearly and the rotation along the great circle, i.e. free flight with
+ * constant linear velocity v and constant world-frame angular velocity w).
+ *
+ *   h = t - t_cur,  X(t) = x + v h,  q(t) = dq (x) q0,
+ *   dq = (cos(phi), sin(phi)/phi * (h/2) * w),  phi = |w| h / 2.
+ *
+ * cos(phi) and sin(phi)/phi are evaluated from their Taylor series in
+ * z = phi^2 = |w|^2 h^2 / 4 (Horner form, 10 terms, exact integer
+ * denominators (2k-1)2k and 2k(2k+1)); no square root, no library
+ * trigonometry.  Truncation error < 1e-17 for phi <= 1.5. */
+#define POSE_TERMS 10
+
+void demo_pose(const double *state, int64_t n, int64_t p, double t, double R[9], double X[3]) {
+  const double *s = state;
+  double h = t - s[FTCUR * n + p];
+  vec3 w = mk(s[FWX * n + p], s[FWY * n + p], s[FWZ * n + p]);
+  double w2 = dot(w, w);
+  double z = (w2 * (h * h)) * 0.25;
+  double c = 1.0, sn = 1.0;
+  for (int k = POSE_TERMS; k >= 1; --k) {
+    c = 1.0 - (z / (double)((2 * k - 1) * (2 * k))) * c;
+    sn = 1.0 - (z / (double)((2 * k) * (2 * k + 1))) * sn;
+  }
+  double g = (h * 0.5) * sn;
+  /* dq = (c, g w) */
+  double pw = c, px = g * w.x, py = g * w.y, pz = g * w.z;
+  double qw = s[FQW * n + p], qx = s[FQX * n + p], qy = s[FQY * n + p], qz = s[FQZ * n + p];
+  /* Hamilton product dq (x) q0 */
+  double rw = pw * qw - px * qx - py * qy - pz * qz;
+  double rx = pw * qx + px * qw + py * qz - pz * qy;
+  double ry = pw * qy - px * qz + py * qw + pz * qx;
+  double rz = pw * qz + px * qy - py * qx + pz * qw;
+  /* rotation matrix of the unit quaternion (row-major) */
+  R[0] = 1.0 - 2.0 * (ry * ry + rz * rz);
+  R[1] = 2.0 * (rx * ry - rw * rz);
+  R[2] = 2.0 * (rx * rz + rw * ry);
+  R[3] = 2.0 * (rx * ry + rw * rz);
+  R[4] = 1.0 - 2.0 * (rx * rx + rz * rz);
+  R[5] = 2.0 * (ry * rz - rw * rx);
+  R[6] = 2.0 * (rx * rz - rw * ry);
+  R[7] = 2.0 * (ry * rz + rw * rx);
+  R[8] = 1.0 - 2.0 * (rx * rx + ry * ry);
+  X[0] = s[FX * n + p] + s[FVX * n + p] * h;
+  X[1] = s[FY * n + p] + s[FVY * n + p] * h;
+  X[2] = s[FZ * n + p] + s[FVZ * n + p] * h;
+}
+
+/* world position of body-frame vertex b: R b + X, rows left to right */
+static vec3 to_world(const double R[9], const double X[3], vec3 b) {
+  return mk(R[0] * b.x + R[1] * b.y + R[2] * b.z + X[0],
+            R[3] * b.x + R[4] * b.y + R[5] * b.z + X[1],
+            R[6] * b.x + R[7] * b.y + R[8] * b.z + X[2]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Closest point of triangle (a,b,c) to p by Voronoi-region classification
+ * (Ericson, Real-Time Collision Detection, 2005, Sec. 5.1.5).  With
+ * e1 = b-a, e2 = c-a and the six projections s1..s6 of p-a, p-b, p-c on
+ * e1, e2, the signs of s_i and of the three barycentric areas va, vb, vc
+ * select a vertex, an edge or the face.  Returns |p-q|^2. */
+static double closest_pt_tri(vec3 p, vec3 a, vec3 b, vec3 c, vec3 *q) {
+  vec3 e1 = sub(b, a), e2 = sub(c, a);
+  vec3 pa = sub(p, a);
+  double s1 = dot(e1, pa), s2 = dot(e2, pa);
+  if (s1 <= 0.0 && s2 <= 0.0) { *q = a; goto done; }
+  {
+    vec3 pb = sub(p, b);
+    double s3 = dot(e1, pb), s4 = dot(e2, pb);
+    if (s3 >= 0.0 && s4 <= s3) { *q = b; goto done; }
+    double vc = s1 * s4 - s3 * s2;
+    if (vc <= 0.0 && s1 >= 0.0 && s3 <= 0.0) {
+      *q = axpy(a, e1, s1 / (s1 - s3));
+      goto done;
+    }
+    vec3 pc = sub(p, c);
+    double s5 = dot(e1, pc), s6 = dot(e2, pc);
+    if (s6 >= 0.0 && s5 <= s6) { *q = c; goto done; }
+    double vb = s5 * s2 - s1 * s6;
+    if (vb <= 0.0 && s2 >= 0.0 && s6 <= 0.0) {
+      *q = axpy(a, e2, s2 / (s2 - s6));
+      goto done;
+    }
+    double va = s3 * s6 - s5 * s4;
+    double u43 = s4 - s3, u56 = s5 - s6;
+    if (va <= 0.0 && u43 >= 0.0 && u56 >= 0.0) {
+      *q = axpy(b, sub(c, b), u43 / (u43 + u56));
+      goto done;
+    }
+    double sum = va + vb + vc;
+    double v = vb / sum, w = vc / sum;
+    *q = mk(a.x + e1.x * v + e2.x * w, a.y + e1.y * v + e2.y * w, a.z + e1.z * v + e2.z * w);
+  }
+done:;
+  vec3 d = sub(p, *q);
+  return dot(d, d);
+}
+
+/* Closest points of segments p1 + s d1 and p2 + t d2, s,t in [0,1]
+ * (Ericson 2005, Sec. 5.1.9): stationary point of the quadratic in (s,t),
+ * clamped, with t re-solved for the clamped s and s re-solved when t is
+ * clamped.  Returns |c1-c2|^2. */
+static double seg_seg(vec3 p1, vec3 q1, vec3 p2, vec3 q2, vec3 *c1, vec3 *c2) {
+  vec3 d1 = sub(q1, p1), d2 = sub(q2, p2), r = sub(p1, p2);
+  double a = dot(d1, d1), e = dot(d2, d2), f = dot(d2, r);
+  double s, t;
+  if (a <= 0.0 && e <= 0.0) {
+    s = 0.0;
+    t = 0.0;
+  } else if (a <= 0.0) {
+    s = 0.0;
+    t = clamp01(f / e);
+  } else {
+    double c = dot(d1, r);
+    if (e <= 0.0) {
+      t = 0.0;
+      s = clamp01(-c / a);
+    } else {
+      double b = dot(d1, d2);
+      double denom = a * e - b * b;
+      s = denom > 0.0 ? clamp01((b * f - c * e) / denom) : 0.0;
+      t = (b * s + f) / e;
+      if (t < 0.0) {
+        t = 0.0;
+        s = clamp01(-c / a);
+      } else if (t > 1.0) {
+        t = 1.0;
+        s = clamp01((b - c) / a);
+      }
+    }
+  }
+  *c1 = axpy(p1, d1, s);
+  *c2 = axpy(p2, d2, t);
+  vec3 d = sub(*c1, *c2);
+  return dot(d, d);
+}
+
+/* Does segment pq cross triangle (a,b,c)?  Signed heights of p and q over the
+ * triangle's plane must not have the same strict sign (both zero = coplanar,
+ * left to the vertex/edge distances); the crossing point x must lie on the
+ * inner side of all three edges. */
+static int seg_tri_cross(vec3 p, vec3 q, vec3 a, vec3 b, vec3 c, vec3 *x) {
+  vec3 nrm = cross(sub(b, a), sub(c, a));
+  double sp = dot(nrm, sub(p, a)), sq = dot(nrm, sub(q, a));
+  if ((sp > 0.0 && sq > 0.0) || (sp < 0.0 && sq < 0.0) || (sp == 0.0 && sq == 0.0)) return 0;
+  double t = sp / (sp - sq);
+  *x = axpy(p, sub(q, p), t);
+  double g0 = dot(cross(sub(b, a), sub(*x, a)), nrm);
+  double g1 = dot(cross(sub(c, b), sub(*x, b)), nrm);
+  double g2 = dot(cross(sub(a, c), sub(*x, c)), nrm);
+  return g0 >= 0.0 && g1 >= 0.0 && g2 >= 0.0;
+}
+
+/* Triangle-triangle distance (paper Section 5, "Collision time detection":
+ * the closest points of two triangles are a vertex and the other triangle's
+ * surface, or lie on two edges).  Intersecting triangles have distance 0 and
+ * the first edge-triangle crossing point (edges of A against B, then edges of
+ * B against A) as both closest points.  Otherwise the minimum over the 6
+ * vertex-triangle and 9 edge-edge distances, first attaining feature pair in
+ * the order VT(A->B), VT(B->A), EE(i of A major, j of B minor), strict "<".
+ * Returns the squared distance. */
+static double tri_dist2(const vec3 A[3], const vec3 B[3], vec3 *pa, vec3 *pb) {
+  vec3 x;
+  for (int i = 0; i < 3; ++i)
+    if (seg_tri_cross(A[i], A[(i + 1) % 3], B[0], B[1], B[2], &x)) { *pa = x; *pb = x; return 0.0; }
+  for (int j = 0; j < 3; ++j)
+    if (seg_tri_cross(B[j], B[(j + 1) % 3], A[0], A[1], A[2], &x)) { *pa = x; *pb = x; return 0.0; }
+  double best = INFINITY;
+  vec3 q, c1, c2;
+  for (int i = 0; i < 3; ++i) {
+    double d2 = closest_pt_tri(A[i], B[0], B[1], B[2], &q);
+    if (d2 < best) { best = d2; *pa = A[i]; *pb = q; }
+  }
+  for (int j = 0; j < 3; ++j) {
+    double d2 = closest_pt_tri(B[j], A[0], A[1], A[2], &q);
+    if (d2 < best) { best = d2; *pa = q; *pb = B[j]; }
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double d2 = seg_seg(A[i], A[(i + 1) % 3], B[j], B[(j + 1) % 3], &c1, &c2);
+      if (d2 < best) { best = d2; *pa = c1; *pb = c2; }
+    }
+  return best;
+}
+
+double demo_tri_dist(const double A[9], const double B[9], double pa[3], double pb[3]) {
+  vec3 a[3] = {ld(A), ld(A + 3), ld(A + 6)}, b[3] = {ld(B), ld(B + 3), ld(B + 6)};
+  vec3 x, y;
+  double d2 = tri_dist2(a, b, &x, &y);
+  st(pa, x);
+  st(pb, y);
+  return sqrt(d2);
+}
+
+double demo_closest_pt_tri(const double p[3], const double T[9], double q[3]) {
+  vec3 r;
+  double d2 = closest_pt_tri(ld(p), ld(T), ld(T + 3), ld(T + 6), &r);
+  st(q, r);
+  return d2;
+}
+
+double demo_seg_seg(const double p1[3], const double q1[3], const double p2[3], const double q2[3],
+                    double c1[3], double c2[3]) {
+  vec3 x, y;
+  double d2 = seg_seg(ld(p1), ld(q1), ld(p2), ld(q2), &x, &y);
+  st(c1, x);
+  st(c2, y);
+  return d2;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Broad phase (paper Section 3: free-flight extrapolation of each particle
+ * over its own step, bounding spheres that cover the particle and its halo,
+ * symmetric pairwise overlap test).  Swept sphere of p over [t_cur, t_cur+dt]:
+ * centre m = x + v (dt/2), radius rho = (radius + eps) + |v| (dt/2).
+ * Candidate iff |m_i - m_j|^2 <= (rho_i + rho_j)^2.  Pairs of two static
+ * particles are never candidates.  Brute force over all i < j. */
+static void swept_sphere(const double *s, int64_t n, int64_t p, vec3 *m, double *rho) {
+  double hdt = s[FDT * n + p] * 0.5;
+  vec3 v = mk(s[FVX * n + p], s[FVY * n + p], s[FVZ * n + p]);
+  *m = mk(s[FX * n + p] + v.x * hdt, s[FY * n + p] + v.y * hdt, s[FZ * n + p] + v.z * hdt);
+  *rho = (s[FRADIUS * n + p] + s[FEPS * n + p]) + sqrt(dot(v, v)) * hdt;
+}
+
+int64_t demo_broad_phase(const double *state, const uint8_t *is_static, int64_t n, int32_t *pairs,
+                         int64_t cap) {
+  int64_t cnt = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    vec3 mi;
+    double ri;
+    swept_sphere(state, n, i, &mi, &ri);
+    for (int64_t j = i + 1; j < n; ++j) {
+      if (is_static && is_static[i] && is_static[j]) continue;
+      vec3 mj;
+      double rj;
+      swept_sphere(state, n, j, &mj, &rj);
+      vec3 d = sub(mi, mj);
+      double rr = ri + rj;
+      if (dot(d, d) <= rr * rr) {
+        if (cnt < cap) {
+          pairs[2 * cnt] = (int32_t)i;
+          pairs[2 * cnt + 1] = (int32_t)j;
+        }
+        ++cnt;
+      }
+    }
+  }
+  return cnt;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pair evaluation at one time: world vertices of both particles, then every
+ * triangle pair in (a, b) lexicographic order. */
+
+typedef struct {
+  double d2min;
+  int32_t a, b;
+  vec3 pa, pb;
+  /* contact list (optional) */
+  int64_t nc, capc;
+  int32_t *cab;   /* (a,b) per contact */
+  double *cgeom;  /* (d, pa, pb) per contact */
+} pair_eval;
+
+static vec3 *world_verts(const double *state, int64_t n, const int64_t *tri_off, const float *tris,
+                         int64_t n_tris, int64_t p, double t) {
+  double R[9], X[3];
+  demo_pose(state, n, p, t, R, X);
+  int64_t t0 = tri_off[p], cnt = tri_off[p + 1] - tri_off[p];
+  vec3 *w = (vec3 *)malloc(sizeof(vec3) * 3 * (size_t)(cnt > 0 ? cnt : 1));
+  for (int64_t k = 0; k < cnt; ++k)
+    for (int s = 0; s < 3; ++s) {
+      const float *v = tris + ((size_t)s * (size_t)n_tris + (size_t)(t0 + k)) * 4;
+      w[3 * k + s] = to_world(R, X, mk((double)v[0], (double)v[1], (double)v[2]));
+    }
+  return w;
+}
+
+static void push_contact(pair_eval *e, int32_t a, int32_t b, double d, vec3 pa, vec3 pb) {
+  if (e->nc == e->capc) {
+    e->capc = e->capc ? 2 * e->capc : 64;
+    e->cab = (int32_t *)realloc(e->cab, sizeof(int32_t) * 2 * (size_t)e->capc);
+    e->cgeom = (double *)realloc(e->cgeom, sizeof(double) * 7 * (size_t)e->capc);
+  }
+  e->cab[2 * e->nc] = a;
+  e->cab[2 * e->nc + 1] = b;
+  double *g = e->cgeom + 7 * e->nc;
+  g[0] = d;
+  st(g + 1, pa);
+  st(g + 4, pb);
+  e->nc++;
+}
+
+/* eps_pair = eps_i + eps_j (paper Section 2.1: particles touch when their
+ * halos overlap; the contact-point definition of Section 5 bounds the
+ * distance by the halo). */
+static double eps_pair(const double *s, int64_t n, int64_t i, int64_t j) {
+  return s[FEPS * n + i] + s[FEPS * n + j];
+}
+
+static void eval_pair(const double *state, int64_t n, const int64_t *tri_off, const float *tris,
+                      int64_t n_tris, int64_t i, int64_t j, double t, int want_contacts,
+                      pair_eval *e) {
+  vec3 *WA = world_verts(state, n, tri_off, tris, n_tris, i, t);
+  vec3 *WB = world_verts(state, n, tri_off, tris, n_tris, j, t);
+  int64_t na = tri_off[i + 1] - tri_off[i], nb = tri_off[j + 1] - tri_off[j];
+  double eps = eps_pair(state, n, i, j);
+  e->d2min = INFINITY;
+  e->a = e->b = -1;
+  e->pa = e->pb = mk(0, 0, 0);
+  for (int64_t a = 0; a < na; ++a)
+    for (int64_t b = 0; b < nb; ++b) {
+      vec3 pa, pb;
+      double d2 = tri_dist2(WA + 3 * a, WB + 3 * b, &pa, &pb);
+      if (d2 < e->d2min) {
+        e->d2min = d2;
+        e->a = (int32_t)a;
+        e->b = (int32_t)b;
+        e->pa = pa;
+        e->pb = pb;
+      }
+      if (want_contacts) {
+        double d = sqrt(d2);
+        if (d <= eps) push_contact(e, (int32_t)a, (int32_t)b, d, pa, pb);
+      }
+    }
+  free(WA);
+  free(WB);
+}
+
+static double pair_start(const double *s, int64_t n, int64_t i, int64_t j) {
+  double a = s[FTCUR * n + i], b = s[FTCUR * n + j];
+  return a < b ? a : b;
+}
+static double pair_span(const double *s, int64_t n, int64_t i, int64_t j) {
+  double a = s[FDT * n + i], b = s[FDT * n + j];
+  return a < b ? a : b;
+}
+
+/* ------------------------------------------------------------------------ */
+/* threading over independent pairs */
+typedef struct {
+  const double *state;
+  int64_t n;
+  const int64_t *tri_off;
+  const float *tris;
+  int64_t n_tris;
+  const int32_t *pairs;
+  int64_t m;
+  const double *t_eval;
+  int K;
+  double tol;
+  pair_eval *ev;         /* narrow */
+  double *t_coll;        /* collision times */
+  uint8_t *status;
+  int32_t *tri_ab;
+  int32_t *n_evals;
+  atomic_llong next;
+  int mode;              /* 0 narrow, 1 collision times */
+} job;
+
+/* Collision time of one pair (paper Section 5, case distinction and the
+ * definition of narrowing; interval of Eq. "max time span between two
+ * particles").  Interval [ts, ts+T], ts = min(t_cur_i, t_cur_j),
+ * T = min(dt_i, dt_j).  f(t) <= eps  <=>  some triangle pair is within
+ * eps_pair at t.
+ *   f(ts) <= eps           -> status 1, t = ts + T (already touching)
+ *   first k in 1..K with f(ts + T k / K) <= eps -> bisection on
+ *     [t_{k-1}, t_k] while hi - lo > tol T with mid = lo + (hi-lo)/2;
+ *     the returned time is hi (the upper bracket: the halos overlap there,
+ *     the "widening" of Section 5) -> status 2
+ *   no sample touches     -> status 0, t = ts + T. */
+static void collision_time_one(job *J, int64_t k) {
+  int64_t i = J->pairs[2 * k], j = J->pairs[2 * k + 1];
+  const double *s = J->state;
+  int64_t n = J->n;
+  double eps = eps_pair(s, n, i, j);
+  double ts = pair_start(s, n, i, j), T = pair_span(s, n, i, j);
+  pair_eval e;
+  memset(&e, 0, sizeof e);
+  int evals = 0;
+#define FLE(tt) (eval_pair(s, n, J->tri_off, J->tris, J->n_tris, i, j, (tt), 0, &e), ++evals, \
+                 sqrt(e.d2min) <= eps)
+  uint8_t status;
+  double tc;
+  int32_t ta = -1, tb = -1;
+  if (FLE(ts)) {
+    status = 1;
+    tc = ts + T;
+    ta = e.a;
+    tb = e.b;
+  } else {
+    int found = 0;
+    double lo = ts, hi = ts;
+    for (int q = 1; q <= J->K; ++q) {
+      double tq = ts + (T * (double)q) / (double)J->K;
+      if (FLE(tq)) {
+        lo = ts + (T * (double)(q - 1)) / (double)J->K;
+        hi = tq;
+        found = 1;
+        break;
+      }
+    }
+    if (!found) {
+      status = 0;
+      tc = ts + T;
+    } else {
+      double lim = J->tol * T;
+      while (hi - lo > lim) {
+        double mid = lo + 0.5 * (hi - lo);
+        if (FLE(mid))
+          hi = mid;
+        else
+          lo = mid;
+      }
+      status = 2;
+      tc = hi;
+      /* closest triangle pair at the returned time */
+      eval_pair(s, n, J->tri_off, J->tris, J->n_tris, i, j, hi, 0, &e);
+      ta = e.a;
+      tb = e.b;
+    }
+  }
+#undef FLE
+  J->t_coll[k] = tc;
+  J->status[k] = status;
+  J->tri_ab[2 * k] = ta;
+  J->tri_ab[2 * k + 1] = tb;
+  if (J->n_evals) J->n_evals[k] = evals;
+}
+
+static void *worker(void *arg) {
+  job *J = (job *)arg;
+  for (;;) {
+    int64_t k = (int64_t)atomic_fetch_add(&J->next, 1);
+    if (k >= J->m) break;
+    if (J->mode == 0) {
+      int64_t i = J->pairs[2 * k], j = J->pairs[2 * k + 1];
+      double t = J->t_eval ? J->t_eval[k] : pair_start(J->state, J->n, i, j);
+      eval_pair(J->state, J->n, J->tri_off, J->tris, J->n_tris, i, j, t, 1, &J->ev[k]);
+    } else {
+      collision_time_one(J, k);
+    }
+  }
+  return NULL;
+}
+
+static void run_job(job *J, int n_threads) {
+  atomic_init(&J->next, 0);
+  if (n_threads <= 1 || J->m <= 1) {
+    worker(J);
+    return;
+  }
+  if (n_threads > 256) n_threads = 256;
+  pthread_t th[256];
+  int started = 0;
+  for (int k = 0; k < n_threads; ++k)
+    if (pthread_create(&th[k], NULL, worker, J) == 0) ++started;
+  if (started == 0) worker(J);
+  for (int k = 0; k < started; ++k) pthread_join(th[k], NULL);
+}
+
+int64_t demo_narrow_phase(const double *state, int64_t n, const int64_t *tri_off, const float *tris,
+                          int64_t n_tris, const int32_t *pairs, int64_t m, const double *t_eval,
+                          double *dmin, double *pa, double *pb, int32_t *tri_ab, uint8_t *flag,
+                          int32_t *contacts, double *geom, int64_t cap, int n_threads) {
+  job J;
+  memset(&J, 0, sizeof J);
+  J.state = state;
+  J.n = n;
+  J.tri_off = tri_off;
+  J.tris = tris;
+  J.n_tris = n_tris;
+  J.pairs = pairs;
+  J.m = m;
+  J.t_eval = t_eval;
+  J.mode = 0;
+  J.ev = (pair_eval *)calloc((size_t)(m > 0 ? m : 1), sizeof(pair_eval));
+  run_job(&J, n_threads);
+  int64_t nc = 0;
+  for (int64_t k = 0; k < m; ++k) {
+    pair_eval *e = &J.ev[k];
+    int64_t i = pairs[2 * k], j = pairs[2 * k + 1];
+    double d = sqrt(e->d2min);
+    dmin[k] = d;
+    st(pa + 3 * k, e->pa);
+    st(pb + 3 * k, e->pb);
+    tri_ab[2 * k] = e->a;
+    tri_ab[2 * k + 1] = e->b;
+    flag[k] = (uint8_t)(d <= eps_pair(state, n, i, j));
+    for (int64_t c = 0; c < e->nc; ++c, ++nc) {
+      if (nc < cap) {
+        contacts[3 * nc] = (int32_t)k;
+        contacts[3 * nc + 1] = e->cab[2 * c];
+        contacts[3 * nc + 2] = e->cab[2 * c + 1];
+        memcpy(geom + 7 * nc, e->cgeom + 7 * c, 7 * sizeof(double));
+      }
+    }
+    free(e->cab);
+    free(e->cgeom);
+  }
+  free(J.ev);
+  return nc;
+}
+
+void demo_collision_times(const double *state, int64_t n, const int64_t *tri_off, const float *tris,
+                          int64_t n_tris, const int32_t *pairs, int64_t m, int K, double tol,
+                          double *t_coll, uint8_t *status, int32_t *tri_ab, int32_t *n_evals,
+                          int n_threads) {
+  job J;
+  memset(&J, 0, sizeof J);
+  J.state = state;
+  J.n = n;
+  J.tri_off = tri_off;
+  J.tris = tris;
+  J.n_tris = n_tris;
+  J.pairs = pairs;
+  J.m = m;
+  J.K = K;
+  J.tol = tol;
+  J.t_coll = t_coll;
+  J.status = status;
+  J.tri_ab = tri_ab;
+  J.n_evals = n_evals;
+  J.mode = 1;
+  run_job(&J, n_threads);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Clusters (paper Section 3: the pruned graph splits into disconnected
+ * subgraphs; each is a cluster; static objects take no part).  The paper
+ * relabels nodes iteratively from their neighbours until nothing changes;
+ * read as minimum-label propagation: every non-static node starts with its
+ * own index and repeatedly takes the minimum label over itself and its
+ * neighbours, until a sweep changes nothing.  The fixpoint labels every
+ * connected component with its smallest index. */
+int64_t demo_clusters(int64_t n, const int32_t *edges, int64_t e, const uint8_t *is_static,
+                      int32_t *id) {
+  for (int64_t i = 0; i < n; ++i) id[i] = (is_static && is_static[i]) ? -1 : (int32_t)i;
+  int changed = 1;
+  while (changed) {
+    changed = 0;
+    for (int64_t k = 0; k < e; ++k) {
+      int32_t u = edges[2 * k], v = edges[2 * k + 1];
+      if (id[u] < 0 || id[v] < 0) continue;
+      int32_t lo = id[u] < id[v] ? id[u] : id[v];
+      if (id[u] != lo) { id[u] = lo; changed = 1; }
+      if (id[v] != lo) { id[v] = lo; changed = 1; }
+    }
+  }
+  int64_t c = 0;
+  for (int64_t i = 0; i < n; ++i)
+    if (id[i] == (int32_t)i) ++c;
+  return c;
+}

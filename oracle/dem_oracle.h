@@ -1,0 +1,76 @@
+/*
+ * dem_oracle.h -- plain FP64 CPU oracle for space-time contact detection
+ * between rigid triangulated particles (Noble & Weinzierl, "Parallel local
+ * time stepping for rigid bodies represented by triangulated meshes").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the slow, obviously correct
+ * definition the CUDA library is checked against.  Only the tests, the smoke
+ * check and the benchmark's CPU-baseline leg may load it; the product path
+ * never calls it and shares no code with it.
+ *
+ * All arrays are host arrays.  Particle data use the same layout as the CUDA
+ * library (field-major double state[DEMO_NFIELDS][n], float4 triangle soup
+ * tris[3][n_tris][4], int64 tri_off[n+1]) because both are fed by the same
+ * seeded generators.
+ */
+#ifndef DEM_ORACLE_H
+#define DEM_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DEMO_NFIELDS 17
+
+/* Pose of particle p at time t: rotation matrix R (row-major) and centre X. */
+void demo_pose(const double *state, int64_t n, int64_t p, double t, double R[9], double X[3]);
+
+/* Triangle-triangle minimum distance and closest points (world frame).
+ * A, B: 3 vertices x 3 coordinates each.  Returns d (not squared). */
+double demo_tri_dist(const double A[9], const double B[9], double pa[3], double pb[3]);
+
+/* Closest point on triangle T to point p; returns squared distance. */
+double demo_closest_pt_tri(const double p[3], const double T[9], double q[3]);
+
+/* Closest points of segments (p1,q1) and (p2,q2); returns squared distance. */
+double demo_seg_seg(const double p1[3], const double q1[3], const double p2[3],
+                    const double q2[3], double c1[3], double c2[3]);
+
+/* Broad phase: all pairs i<j whose swept halo spheres overlap.  Writes up to
+ * cap pairs (i,j interleaved) in (i,j) order; returns the number of pairs. */
+int64_t demo_broad_phase(const double *state, const uint8_t *is_static, int64_t n,
+                         int32_t *pairs, int64_t cap);
+
+/* Narrow phase over m pairs at times t_eval[k] (NULL: the pair's start time).
+ * Per pair: dmin, pa[3], pb[3], tri_ab[2] (indices local to each particle),
+ * flag (dmin <= eps_pair).  Contacts (all triangle pairs with d <= eps_pair)
+ * in (pair, a, b) order: contacts[3*c] = (pair, a, b), geom[7*c] =
+ * (d, pa, pb).  Returns the number of contacts (may exceed cap; then only
+ * cap are written).  n_threads >= 1 splits the pairs over threads. */
+int64_t demo_narrow_phase(const double *state, int64_t n, const int64_t *tri_off,
+                          const float *tris, int64_t n_tris, const int32_t *pairs, int64_t m,
+                          const double *t_eval, double *dmin, double *pa, double *pb,
+                          int32_t *tri_ab, uint8_t *flag, int32_t *contacts, double *geom,
+                          int64_t cap, int n_threads);
+
+/* Collision-time search over m pairs: K uniform samples, then bisection to
+ * tol * T.  Outputs t_coll, status (0 none, 1 in contact at start, 2 proper),
+ * tri_ab[2] of the closest triangles at the returned time (-1 for status 0),
+ * n_evals (number of pair-distance evaluations the search made; may be NULL). */
+void demo_collision_times(const double *state, int64_t n, const int64_t *tri_off,
+                          const float *tris, int64_t n_tris, const int32_t *pairs, int64_t m,
+                          int K, double tol, double *t_coll, uint8_t *status, int32_t *tri_ab,
+                          int32_t *n_evals, int n_threads);
+
+/* Connected components of the graph over n particles with e edges (pairs of
+ * indices, interleaved); edges with a static endpoint are ignored.  id[i] =
+ * smallest particle index in i's component, -1 for static particles.
+ * Returns the number of components among non-static particles. */
+int64_t demo_clusters(int64_t n, const int32_t *edges, int64_t e, const uint8_t *is_static,
+                      int32_t *id);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
