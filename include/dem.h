@@ -1,0 +1,217 @@
+/*
+ * dem.h -- C-ABI of the GB300 (sm_103a) space-time contact-detection library
+ * for rigid particles represented by triangulated meshes, after Noble &
+ * Weinzierl, "Parallel local time stepping for rigid bodies represented by
+ * triangulated meshes" (arXiv:2309.15417).
+ *
+ * Four calls make up one detection step: candidate pairs (broad phase),
+ * triangle-pair distances and contacts (narrow phase), collision time stamps,
+ * and clusters (connected components).
+ *
+ * Conventions shared by every call:
+ *  - Every array argument is a DEVICE pointer owned by the caller, unless the
+ *    comment says "host".  The library never frees caller memory; it owns only
+ *    the scratch it allocates in dem_create().
+ *  - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL
+ *    = legacy default stream).  No call synchronises except dem_check() and
+ *    dem_get_stats().  No call allocates device memory, so a sequence of calls
+ *    can be captured into a CUDA graph.
+ *  - Argument errors (null pointers, sizes beyond the capacities given to
+ *    dem_create, misaligned triangle buffers) are detected on the host and
+ *    returned immediately as DEM_ERR_ARG / DEM_ERR_CAPACITY; nothing is
+ *    launched then.
+ *  - Conditions found on the device (an output capacity exceeded, an index
+ *    out of range, a bounded wait that ran out) set a sticky error word in the
+ *    context.  dem_check() synchronises the stream, returns the first such
+ *    condition as a status and clears it.  Kernels never trap.
+ *  - Counts that kernels produce are written to device int64 scalars, and the
+ *    consuming calls read them on the device (`n_pairs` below), so a whole
+ *    step runs without host round trips.
+ *  - Pairs (and edges) are int32 [M][2] (i, j interleaved), with i < j.
+ *
+ * Particle data (paper Section 2.1, "Physical model"; Section 5, "Geometric
+ * model"): see dem_particles.
+ */
+#ifndef DEM_H
+#define DEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dem_ctx dem_ctx;
+
+typedef enum {
+  DEM_OK = 0,
+  DEM_ERR_ARG = -1,       /* invalid argument (detected on the host) */
+  DEM_ERR_CAPACITY = -2,  /* a size exceeds a capacity (host or device) */
+  DEM_ERR_CUDA = -3,      /* a CUDA runtime call failed; see dem_last_error */
+  DEM_ERR_INDEX = -4,     /* a device kernel met an index out of range */
+  DEM_ERR_TIMEOUT = -5    /* a bounded device wait ran out */
+} dem_status;
+
+/* Arithmetic of the triangle-pair distances. */
+enum {
+  DEM_PREC_FP32_FIXUP = 0, /* FP32 bulk, FP64 recomputation within the FP32 error bound */
+  DEM_PREC_FP64 = 1        /* every distance in FP64 */
+};
+
+/* Fields of the particle state, field-major: state[f * n + p]. */
+#define DEM_NFIELDS 17
+enum {
+  DEM_F_X = 0, DEM_F_Y, DEM_F_Z,        /* centre of mass at t_cur (world) */
+  DEM_F_VX, DEM_F_VY, DEM_F_VZ,         /* linear velocity (world) */
+  DEM_F_QW, DEM_F_QX, DEM_F_QY, DEM_F_QZ, /* unit quaternion body -> world at t_cur */
+  DEM_F_WX, DEM_F_WY, DEM_F_WZ,         /* angular velocity (world frame) */
+  DEM_F_TCUR,                           /* the particle's current time stamp */
+  DEM_F_DT,                             /* the particle's own step size */
+  DEM_F_EPS,                            /* halo width eps(p) */
+  DEM_F_RADIUS                          /* bound on |body-frame vertex| */
+};
+
+/* Particles (paper Section 2.1): rigid triangle meshes with a halo, moving in
+ * free flight with constant linear velocity v and constant world-frame angular
+ * velocity w between snapshots.  The pose at time t is
+ *   X(t) = x + v (t - t_cur),  q(t) = dq(w, t - t_cur) (x) q,
+ * dq the rotation by angle |w| (t - t_cur) about w.
+ * Triangles (Section 5, "Geometric model") are given in the body frame as a
+ * float4 soup: tris[(s * n_tris + k) * 4 + c], vertex slot s = 0..2, triangle
+ * k, coordinate c = x,y,z (the 4th float is ignored).  Particle p owns
+ * triangles tri_off[p] .. tri_off[p+1]-1. */
+typedef struct {
+  int64_t n;                /* number of particles */
+  const double *state;      /* device [DEM_NFIELDS][n] */
+  const uint8_t *is_static; /* device [n], nonzero = static object; NULL = none */
+  const int64_t *tri_off;   /* device [n+1], non-decreasing, tri_off[0] = 0 */
+  const float *tris;        /* device float4 [3][n_tris], 16-byte aligned */
+  int64_t n_tris;           /* total triangles = tri_off[n] */
+} dem_particles;
+
+typedef struct {
+  int32_t K;            /* collision-time samples per pair interval (>= 1; 0 -> 8) */
+  double bisect_tol;    /* bisection stops at bracket <= bisect_tol * T (0 -> 1e-3) */
+  int32_t precision;    /* DEM_PREC_* */
+  int32_t reserved;
+  int64_t max_particles; /* capacity: particles per call (0 -> 65536) */
+  int64_t max_pairs;     /* capacity: pairs / edges per call (0 -> 1<<20) */
+  int64_t max_contacts;  /* capacity: contact staging per narrow-phase call (0 -> 1<<20) */
+} dem_config;
+
+/* Outputs of dem_narrow_phase.  Per pair k (M = pair count):
+ *   dmin[k]        minimum triangle-pair distance (FP64)
+ *   pa[3k..], pb[3k..]  its closest points on particle i and j (world, FP64)
+ *   tri_ab[2k..]   (a, b): the closest triangle pair, indices local to each
+ *                  particle, smallest (a, b) among equal distances; -1 if a
+ *                  particle has no triangles
+ *   flag[k]        1 iff dmin <= eps_i + eps_j
+ *   dmin32[k]      optional (NULL to skip): the pair minimum as computed in
+ *                  FP32 before any FP64 recomputation (FP32 mode); dmin in
+ *                  FP64 mode
+ * Contacts: every triangle pair with distance <= eps_i + eps_j, sorted by
+ * (pair, a, b): contacts[3c..] = (pair index k, a, b) int32,
+ * contact_geom[7c..] = (d, pa.xyz, pb.xyz) FP64 world.  *n_contacts (device)
+ * receives the total; only min(total, contact_cap) are written. */
+typedef struct {
+  double *dmin;
+  double *pa;
+  double *pb;
+  int32_t *tri_ab;
+  uint8_t *flag;
+  float *dmin32;
+  int32_t *contacts;
+  double *contact_geom;
+  int64_t contact_cap;
+  int64_t *n_contacts;
+} dem_narrow_out;
+
+/* Device counters, summed since the last reset. */
+typedef struct {
+  int64_t sphere_tests;     /* triangle-pair bounding-sphere tests */
+  int64_t group_tests;      /* triangle-group bounding-sphere tests */
+  int64_t dist_fp32;        /* triangle-pair distances in FP32 */
+  int64_t dist_fp64;        /* triangle-pair distances in FP64 */
+  int64_t pair_evals;       /* pair-distance evaluations (decisions + minima) */
+  int64_t method_checks;    /* sum over the method's evaluations of T_i * T_j */
+  int64_t bisect_steps;     /* bisection steps */
+  int64_t contacts;         /* contacts found */
+  int64_t pairs_done;       /* pairs processed */
+  int64_t reserved[7];
+} dem_stats;
+
+/* Create a context: validates and copies *cfg, allocates scratch for the
+ * capacities it names.  Returns DEM_ERR_CUDA if allocation fails. */
+dem_status dem_create(const dem_config *cfg, dem_ctx **out);
+
+/* Destroy a context and free its scratch (NULL is a no-op). */
+void dem_destroy(dem_ctx *ctx);
+
+/* Message of the last host-side error of ctx (never NULL). */
+const char *dem_last_error(const dem_ctx *ctx);
+
+/* Broad phase (paper Section 3, "Broad phase collision detection to identify
+ * clusters", and the pair interval of Eq. "max time span between two
+ * particles"): the candidate pairs c(i, j) = true.  Each particle is extruded
+ * over its own step in free flight: swept sphere centre m = x + v dt/2,
+ * radius rho = (radius + eps) + |v| dt/2; (i, j) is a candidate iff
+ * |m_i - m_j|^2 <= (rho_i + rho_j)^2 (binary64).  Pairs of two static
+ * particles are never candidates.  Uses a uniform hashed cell grid of cell
+ * size >= 2 max rho; the result equals the brute-force set.
+ * Output: pairs [cap][2] in (i, j) order, *n_pairs (device) = number of
+ * candidates; if it exceeds cap only cap are written and dem_check() returns
+ * DEM_ERR_CAPACITY. */
+dem_status dem_build_candidates(dem_ctx *ctx, const dem_particles *P, int32_t *pairs, int64_t cap,
+                                int64_t *n_pairs, void *stream);
+
+/* Narrow phase (paper Section 5, "Geometric model", Definition of a contact
+ * point, and "Collision time detection": triangle distance = minimum over
+ * vertex-triangle and edge-edge distances, 0 for intersecting triangles).
+ * Evaluates every triangle pair of every pair at time t_eval[k] (NULL: the
+ * pair's start time min(t_cur_i, t_cur_j)).
+ * pairs: [max_pairs][2]; n_pairs: device count (NULL: max_pairs pairs); the
+ * call processes min(*n_pairs, max_pairs) pairs. */
+dem_status dem_narrow_phase(dem_ctx *ctx, const dem_particles *P, const int32_t *pairs,
+                            int64_t max_pairs, const int64_t *n_pairs, const double *t_eval,
+                            const dem_narrow_out *out, void *stream);
+
+/* Collision time stamps (paper Section 5, "Time step size calculation": case
+ * distinction, narrowing and widening; interval of Eq. "max time span between
+ * two particles").  Pair interval [ts, ts + T], ts = min(t_cur_i, t_cur_j),
+ * T = min(dt_i, dt_j); f(t) = minimum triangle-pair distance at t.
+ *   f(ts) <= eps_pair                  -> status 1, t_coll = ts + T
+ *   first k in 1..K: f(ts + T k/K) <= eps_pair -> bisection on
+ *     [ts + T (k-1)/K, ts + T k/K] until the bracket is <= tol T,
+ *     t_coll = the upper end                                -> status 2
+ *   otherwise                          -> status 0, t_coll = ts + T
+ * tri_ab[2k..]: the closest triangle pair at t_coll for status 1 (at ts) and
+ * 2; -1 for status 0.  Every decision f(t) <= eps_pair equals the binary64
+ * decision of the definition. */
+dem_status dem_collision_times(dem_ctx *ctx, const dem_particles *P, const int32_t *pairs,
+                               int64_t max_pairs, const int64_t *n_pairs, double *t_coll,
+                               uint8_t *status, int32_t *tri_ab, void *stream);
+
+/* Clusters (paper Section 3: the pruned graph's disconnected subgraphs are
+ * the clusters; static objects take no part in the clustering).  Connected
+ * components of the undirected graph over n particles given by edges
+ * [max_edges][2] (count: device *n_edges, NULL = max_edges); edges with a
+ * static endpoint are ignored.  cluster_id[i] = smallest particle index in
+ * i's component, -1 for static particles; *n_clusters (device) = number of
+ * components among non-static particles.  is_static may be NULL. */
+dem_status dem_clusters(dem_ctx *ctx, int64_t n, const int32_t *edges, int64_t max_edges,
+                        const int64_t *n_edges, const uint8_t *is_static, int32_t *cluster_id,
+                        int64_t *n_clusters, void *stream);
+
+/* Synchronise `stream`, return (and clear) the sticky device error as a
+ * status (DEM_OK if none). */
+dem_status dem_check(dem_ctx *ctx, void *stream);
+
+/* Synchronise the device, copy the counters to host *out; reset them if
+ * `reset` is nonzero. */
+dem_status dem_get_stats(dem_ctx *ctx, dem_stats *out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DEM_H */

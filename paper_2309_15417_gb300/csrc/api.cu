@@ -1,0 +1,213 @@
+// api.cu -- the C-ABI entry points (include/dem.h): argument checks on the
+// host, scratch ownership, launches on the caller's stream, sticky device
+// error word and counters.
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "internal.cuh"
+
+struct dem_ctx {
+  dem_config cfg;
+  dem::Scratch S;
+  int device;
+  int num_sms;
+  std::string last_error;
+  void *allocs[32];
+  int n_allocs;
+};
+
+namespace {
+
+dem_status fail(dem_ctx *c, dem_status st, const std::string &msg) {
+  if (c) c->last_error = msg;
+  return st;
+}
+
+dem_status cuda_fail(dem_ctx *c, cudaError_t e, const char *where) {
+  return fail(c, DEM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+template <class T>
+bool alloc(dem_ctx *c, T **p, size_t count) {
+  const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
+  void *q = nullptr;
+  if (cudaMalloc(&q, bytes) != cudaSuccess) return false;
+  if (cudaMemset(q, 0, bytes) != cudaSuccess) {
+    cudaFree(q);
+    return false;
+  }
+  c->allocs[c->n_allocs++] = q;
+  *p = static_cast<T *>(q);
+  return true;
+}
+
+int64_t pow2_at_least(int64_t v) {
+  int64_t p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+dem_status check_particles(dem_ctx *c, const dem_particles *P) {
+  if (!P) return fail(c, DEM_ERR_ARG, "particles: null");
+  if (P->n < 0) return fail(c, DEM_ERR_ARG, "particles: n < 0");
+  if (P->n > c->S.cap_particles) return fail(c, DEM_ERR_CAPACITY, "particles: n exceeds max_particles");
+  if (P->n > 0 && (!P->state || !P->tri_off)) return fail(c, DEM_ERR_ARG, "particles: null state or tri_off");
+  if (P->n_tris < 0) return fail(c, DEM_ERR_ARG, "particles: n_tris < 0");
+  if (P->n_tris > 0 && !P->tris) return fail(c, DEM_ERR_ARG, "particles: null tris");
+  if (reinterpret_cast<uintptr_t>(P->tris) % 16 != 0)
+    return fail(c, DEM_ERR_ARG, "particles: tris must be 16-byte aligned (float4)");
+  return DEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dem_status dem_create(const dem_config *cfg, dem_ctx **out) {
+  if (!out) return DEM_ERR_ARG;
+  *out = nullptr;
+  dem_ctx *c = new dem_ctx();
+  c->n_allocs = 0;
+  dem_config k{};
+  if (cfg) k = *cfg;
+  if (k.K == 0) k.K = 8;
+  if (k.bisect_tol == 0.0) k.bisect_tol = 1e-3;
+  if (k.max_particles == 0) k.max_particles = 65536;
+  if (k.max_pairs == 0) k.max_pairs = 1 << 20;
+  if (k.max_contacts == 0) k.max_contacts = 1 << 20;
+  if (k.K < 1 || !(k.bisect_tol > 0.0) || (k.precision != DEM_PREC_FP32_FIXUP && k.precision != DEM_PREC_FP64) ||
+      k.max_particles < 0 || k.max_pairs < 0 || k.max_contacts < 0 ||
+      k.max_particles > (int64_t)(dem::SCAN_BLOCK * dem::SCAN_PART_CAP / 2) ||
+      k.max_pairs > (int64_t)(dem::SCAN_BLOCK * dem::SCAN_PART_CAP) || k.max_contacts > ((int64_t)1 << 31) - 1) {
+    delete c;
+    return DEM_ERR_ARG;
+  }
+  c->cfg = k;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return DEM_ERR_CUDA;
+  }
+  dem::Scratch &S = c->S;
+  S.cap_particles = k.max_particles;
+  S.table_size = pow2_at_least(2 * (k.max_particles > 512 ? k.max_particles : 512));
+  S.cap_pairs = k.max_pairs;
+  S.cap_contacts = k.max_contacts;
+  const int64_t np = k.max_particles, nq = k.max_pairs, nc = k.max_contacts;
+  bool ok = alloc(c, &S.err, 1) && alloc(c, &S.stats, dem::ST_N) && alloc(c, &S.work, 4) &&
+            alloc(c, &S.scan_part, dem::SCAN_PART_CAP) && alloc(c, &S.tmp, 8) && alloc(c, &S.sph, np) &&
+            alloc(c, &S.cell, np) && alloc(c, &S.bucket_cnt, S.table_size) &&
+            alloc(c, &S.bucket_start, S.table_size) && alloc(c, &S.bucket_cur, S.table_size) &&
+            alloc(c, &S.bucket_ids, np) && alloc(c, &S.pcnt, np) && alloc(c, &S.poff, np) &&
+            alloc(c, &S.rho_max, 1) && alloc(c, &S.st_keys, 3 * nc) && alloc(c, &S.st_geom, 7 * nc) &&
+            alloc(c, &S.st_count, 1) && alloc(c, &S.pc, nq) && alloc(c, &S.po, nq) && alloc(c, &S.pcur, nq) &&
+            alloc(c, &S.sidx, nc);
+  if (!ok) {
+    dem_destroy(c);
+    return DEM_ERR_CUDA;
+  }
+  *out = c;
+  return DEM_OK;
+}
+
+void dem_destroy(dem_ctx *c) {
+  if (!c) return;
+  for (int q = 0; q < c->n_allocs; ++q) cudaFree(c->allocs[q]);
+  delete c;
+}
+
+const char *dem_last_error(const dem_ctx *c) {
+  if (!c) return "null context";
+  return c->last_error.c_str();
+}
+
+dem_status dem_build_candidates(dem_ctx *c, const dem_particles *P, int32_t *pairs, int64_t cap,
+                                int64_t *n_pairs, void *stream) {
+  if (!c) return DEM_ERR_ARG;
+  dem_status st = check_particles(c, P);
+  if (st != DEM_OK) return st;
+  if (!n_pairs || (cap > 0 && !pairs) || cap < 0) return fail(c, DEM_ERR_ARG, "build_candidates: bad output");
+  cudaError_t e = dem::launch_broad(*P, pairs, cap, n_pairs, c->S, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "build_candidates");
+  return DEM_OK;
+}
+
+dem_status dem_narrow_phase(dem_ctx *c, const dem_particles *P, const int32_t *pairs, int64_t max_pairs,
+                            const int64_t *n_pairs, const double *t_eval, const dem_narrow_out *out,
+                            void *stream) {
+  if (!c) return DEM_ERR_ARG;
+  dem_status st = check_particles(c, P);
+  if (st != DEM_OK) return st;
+  if (max_pairs < 0 || (max_pairs > 0 && !pairs)) return fail(c, DEM_ERR_ARG, "narrow_phase: bad pairs");
+  if (max_pairs > c->S.cap_pairs) return fail(c, DEM_ERR_CAPACITY, "narrow_phase: max_pairs exceeds capacity");
+  if (!out || !out->n_contacts || out->contact_cap < 0 ||
+      (max_pairs > 0 && (!out->dmin || !out->pa || !out->pb || !out->tri_ab || !out->flag)) ||
+      (out->contact_cap > 0 && (!out->contacts || !out->contact_geom)))
+    return fail(c, DEM_ERR_ARG, "narrow_phase: bad outputs");
+  cudaError_t e = dem::launch_narrow(c->cfg.precision, *P, pairs, max_pairs, n_pairs, t_eval, *out, c->S,
+                                     c->num_sms, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "narrow_phase");
+  return DEM_OK;
+}
+
+dem_status dem_collision_times(dem_ctx *c, const dem_particles *P, const int32_t *pairs, int64_t max_pairs,
+                               const int64_t *n_pairs, double *t_coll, uint8_t *status, int32_t *tri_ab,
+                               void *stream) {
+  if (!c) return DEM_ERR_ARG;
+  dem_status st = check_particles(c, P);
+  if (st != DEM_OK) return st;
+  if (max_pairs < 0 || (max_pairs > 0 && (!pairs || !t_coll || !status || !tri_ab)))
+    return fail(c, DEM_ERR_ARG, "collision_times: bad arguments");
+  cudaError_t e = dem::launch_ctime(c->cfg.precision, *P, pairs, max_pairs, n_pairs, c->cfg.K, c->cfg.bisect_tol,
+                                    t_coll, status, tri_ab, c->S, c->num_sms, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "collision_times");
+  return DEM_OK;
+}
+
+dem_status dem_clusters(dem_ctx *c, int64_t n, const int32_t *edges, int64_t max_edges, const int64_t *n_edges,
+                        const uint8_t *is_static, int32_t *cluster_id, int64_t *n_clusters, void *stream) {
+  if (!c) return DEM_ERR_ARG;
+  if (n < 0 || max_edges < 0 || (max_edges > 0 && !edges) || (n > 0 && !cluster_id) || !n_clusters)
+    return fail(c, DEM_ERR_ARG, "clusters: bad arguments");
+  if (n > (int64_t)INT32_MAX) return fail(c, DEM_ERR_CAPACITY, "clusters: n exceeds int32 ids");
+  cudaError_t e = dem::launch_clusters(n, edges, max_edges, n_edges, is_static, cluster_id, n_clusters, c->S,
+                                       static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "clusters");
+  return DEM_OK;
+}
+
+dem_status dem_check(dem_ctx *c, void *stream) {
+  if (!c) return DEM_ERR_ARG;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "check: stream");
+  uint32_t bits = 0;
+  e = cudaMemcpy(&bits, c->S.err, sizeof(bits), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "check: read error word");
+  if (!bits) return DEM_OK;
+  e = cudaMemset(c->S.err, 0, sizeof(uint32_t));
+  if (e != cudaSuccess) return cuda_fail(c, e, "check: clear error word");
+  if (bits & dem::ERR_INDEX) return fail(c, DEM_ERR_INDEX, "device: index out of range");
+  if (bits & dem::ERR_CAPACITY) return fail(c, DEM_ERR_CAPACITY, "device: output capacity exceeded");
+  return fail(c, DEM_ERR_TIMEOUT, "device: bounded wait ran out");
+}
+
+dem_status dem_get_stats(dem_ctx *c, dem_stats *out, int reset) {
+  if (!c || !out) return DEM_ERR_ARG;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "get_stats");
+  unsigned long long v[dem::ST_N];
+  e = cudaMemcpy(v, c->S.stats, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "get_stats: copy");
+  std::memset(out, 0, sizeof(*out));
+  int64_t *o = reinterpret_cast<int64_t *>(out);
+  for (int q = 0; q < dem::ST_N && q < (int)(sizeof(dem_stats) / sizeof(int64_t)); ++q) o[q] = (int64_t)v[q];
+  if (reset) {
+    e = cudaMemset(c->S.stats, 0, sizeof(v));
+    if (e != cudaSuccess) return cuda_fail(c, e, "get_stats: reset");
+  }
+  return DEM_OK;
+}
+
+}  // extern "C"

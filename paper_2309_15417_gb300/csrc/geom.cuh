@@ -1,0 +1,295 @@
+// geom.cuh -- device geometry for the contact-detection kernels.
+//
+// Triangle-triangle distance (paper Section 5, "Collision time detection": the
+// closest points of two triangles are a vertex and the other triangle's
+// surface, or two edges; intersecting triangles are at distance 0) and the
+// free-flight pose (Section 2.1: constant linear and angular velocity between
+// snapshots, spherical interpolation of the rotation).
+//
+// Every routine is a template over an arithmetic policy:
+//   OpsD -- binary64 with every operation rounded on its own (__dadd_rn etc.
+//           are never fused into FMA).  With OpsD the routines evaluate each
+//           formula in one fixed order, the order documented beside it, so
+//           that an FP64 result (and every decision taken on it) is a
+//           well-defined function of the inputs.
+//   OpsF -- binary32, FMA contraction allowed; used for the bulk filter,
+//           whose error is bounded by the caller (see pairs.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dem {
+
+struct OpsD {
+  using T = double;
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+  static __device__ __forceinline__ double sqrt(double a) { return __dsqrt_rn(a); }
+  static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000LL); }
+};
+
+struct OpsF {
+  using T = float;
+  static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+  static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
+  static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+  static __device__ __forceinline__ float sqrt(float a) { return __fsqrt_rn(a); }
+  static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+};
+
+template <class T>
+struct V3 {
+  T x, y, z;
+};
+
+template <class O>
+struct Geo {
+  using T = typename O::T;
+  using V = V3<T>;
+
+  static __device__ __forceinline__ V mk(T x, T y, T z) { return V{x, y, z}; }
+  static __device__ __forceinline__ V sub(V a, V b) {
+    return mk(O::sub(a.x, b.x), O::sub(a.y, b.y), O::sub(a.z, b.z));
+  }
+  // (ax bx + ay by) + az bz
+  static __device__ __forceinline__ T dot(V a, V b) {
+    return O::add(O::add(O::mul(a.x, b.x), O::mul(a.y, b.y)), O::mul(a.z, b.z));
+  }
+  static __device__ __forceinline__ V cross(V a, V b) {
+    return mk(O::sub(O::mul(a.y, b.z), O::mul(a.z, b.y)), O::sub(O::mul(a.z, b.x), O::mul(a.x, b.z)),
+              O::sub(O::mul(a.x, b.y), O::mul(a.y, b.x)));
+  }
+  // a + d s, componentwise
+  static __device__ __forceinline__ V axpy(V a, V d, T s) {
+    return mk(O::add(a.x, O::mul(d.x, s)), O::add(a.y, O::mul(d.y, s)), O::add(a.z, O::mul(d.z, s)));
+  }
+  static __device__ __forceinline__ T clamp01(T s) {
+    return s < T(0) ? T(0) : (s > T(1) ? T(1) : s);
+  }
+
+  // Closest point q of triangle (a,b,c) to p, by Voronoi regions of the
+  // triangle (Ericson, Real-Time Collision Detection, Sec. 5.1.5).  e1 = b-a,
+  // e2 = c-a; s1..s6 project p-a, p-b, p-c on e1, e2; va, vb, vc are the
+  // (scaled) barycentric areas.  Returns |p-q|^2.
+  static __device__ __forceinline__ T closest_pt_tri(V p, V a, V b, V c, V &q) {
+    V e1 = sub(b, a), e2 = sub(c, a);
+    V pa = sub(p, a);
+    T s1 = dot(e1, pa), s2 = dot(e2, pa);
+    if (s1 <= T(0) && s2 <= T(0)) {
+      q = a;
+    } else {
+      V pb = sub(p, b);
+      T s3 = dot(e1, pb), s4 = dot(e2, pb);
+      if (s3 >= T(0) && s4 <= s3) {
+        q = b;
+      } else {
+        T vc = O::sub(O::mul(s1, s4), O::mul(s3, s2));
+        if (vc <= T(0) && s1 >= T(0) && s3 <= T(0)) {
+          q = axpy(a, e1, O::div(s1, O::sub(s1, s3)));
+        } else {
+          V pc = sub(p, c);
+          T s5 = dot(e1, pc), s6 = dot(e2, pc);
+          if (s6 >= T(0) && s5 <= s6) {
+            q = c;
+          } else {
+            T vb = O::sub(O::mul(s5, s2), O::mul(s1, s6));
+            if (vb <= T(0) && s2 >= T(0) && s6 <= T(0)) {
+              q = axpy(a, e2, O::div(s2, O::sub(s2, s6)));
+            } else {
+              T va = O::sub(O::mul(s3, s6), O::mul(s5, s4));
+              T u43 = O::sub(s4, s3), u56 = O::sub(s5, s6);
+              if (va <= T(0) && u43 >= T(0) && u56 >= T(0)) {
+                q = axpy(b, sub(c, b), O::div(u43, O::add(u43, u56)));
+              } else {
+                T sum = O::add(O::add(va, vb), vc);
+                T v = O::div(vb, sum), w = O::div(vc, sum);
+                q = mk(O::add(O::add(a.x, O::mul(e1.x, v)), O::mul(e2.x, w)),
+                       O::add(O::add(a.y, O::mul(e1.y, v)), O::mul(e2.y, w)),
+                       O::add(O::add(a.z, O::mul(e1.z, v)), O::mul(e2.z, w)));
+              }
+            }
+          }
+        }
+      }
+    }
+    V d = sub(p, q);
+    return dot(d, d);
+  }
+
+  // Closest points of segments p1 + s d1, p2 + t d2 (s, t in [0,1]): the
+  // stationary point of the quadratic, s clamped, t re-solved for s; if t is
+  // clamped, s re-solved for t (Ericson 2005, Sec. 5.1.9).  Returns |c1-c2|^2.
+  static __device__ __forceinline__ T seg_seg(V p1, V q1, V p2, V q2, V &c1, V &c2) {
+    V d1 = sub(q1, p1), d2 = sub(q2, p2), r = sub(p1, p2);
+    T a = dot(d1, d1), e = dot(d2, d2), f = dot(d2, r);
+    T s, t;
+    if (a <= T(0) && e <= T(0)) {
+      s = T(0);
+      t = T(0);
+    } else if (a <= T(0)) {
+      s = T(0);
+      t = clamp01(O::div(f, e));
+    } else {
+      T c = dot(d1, r);
+      if (e <= T(0)) {
+        t = T(0);
+        s = clamp01(O::div(-c, a));
+      } else {
+        T b = dot(d1, d2);
+        T denom = O::sub(O::mul(a, e), O::mul(b, b));
+        s = denom > T(0) ? clamp01(O::div(O::sub(O::mul(b, f), O::mul(c, e)), denom)) : T(0);
+        t = O::div(O::add(O::mul(b, s), f), e);
+        if (t < T(0)) {
+          t = T(0);
+          s = clamp01(O::div(-c, a));
+        } else if (t > T(1)) {
+          t = T(1);
+          s = clamp01(O::div(O::sub(b, c), a));
+        }
+      }
+    }
+    c1 = axpy(p1, d1, s);
+    c2 = axpy(p2, d2, t);
+    V d = sub(c1, c2);
+    return dot(d, d);
+  }
+
+  // Segment pq crosses triangle (a,b,c): the signed heights of p and q over
+  // the plane do not share a strict sign (both zero = coplanar, left to the
+  // vertex/edge distances) and the crossing point x is on the inner side of
+  // all three edges.
+  static __device__ __forceinline__ bool seg_tri_cross(V p, V q, V a, V b, V c, V &x) {
+    V nrm = cross(sub(b, a), sub(c, a));
+    T sp = dot(nrm, sub(p, a)), sq = dot(nrm, sub(q, a));
+    if ((sp > T(0) && sq > T(0)) || (sp < T(0) && sq < T(0)) || (sp == T(0) && sq == T(0)))
+      return false;
+    T t = O::div(sp, O::sub(sp, sq));
+    x = axpy(p, sub(q, p), t);
+    T g0 = dot(cross(sub(b, a), sub(x, a)), nrm);
+    T g1 = dot(cross(sub(c, b), sub(x, b)), nrm);
+    T g2 = dot(cross(sub(a, c), sub(x, c)), nrm);
+    return g0 >= T(0) && g1 >= T(0) && g2 >= T(0);
+  }
+
+  // Triangle-triangle squared distance and closest points.  Intersecting
+  // triangles: 0 and the first edge-triangle crossing (edges of A against B,
+  // then of B against A) as both points.  Otherwise the first minimum, under
+  // strict "<", in the order: vertices of A against B, vertices of B against
+  // A, edge i of A against edge j of B (i major).
+  static __device__ __forceinline__ T tri_dist2(const V A[3], const V B[3], V &pa, V &pb) {
+    V x;
+#pragma unroll 1
+    for (int i = 0; i < 3; ++i)
+      if (seg_tri_cross(A[i], A[i == 2 ? 0 : i + 1], B[0], B[1], B[2], x)) {
+        pa = x;
+        pb = x;
+        return T(0);
+      }
+#pragma unroll 1
+    for (int j = 0; j < 3; ++j)
+      if (seg_tri_cross(B[j], B[j == 2 ? 0 : j + 1], A[0], A[1], A[2], x)) {
+        pa = x;
+        pb = x;
+        return T(0);
+      }
+    return tri_dist2_features(A, B, pa, pb);
+  }
+
+  // Minimum over the 15 vertex-triangle and edge-edge feature pairs only.
+  static __device__ __forceinline__ T tri_dist2_features(const V A[3], const V B[3], V &pa, V &pb) {
+    T best = O::inf();
+    V q, c1, c2;
+#pragma unroll 1
+    for (int i = 0; i < 3; ++i) {
+      T d2 = closest_pt_tri(A[i], B[0], B[1], B[2], q);
+      if (d2 < best) {
+        best = d2;
+        pa = A[i];
+        pb = q;
+      }
+    }
+#pragma unroll 1
+    for (int j = 0; j < 3; ++j) {
+      T d2 = closest_pt_tri(B[j], A[0], A[1], A[2], q);
+      if (d2 < best) {
+        best = d2;
+        pa = q;
+        pb = B[j];
+      }
+    }
+#pragma unroll 1
+    for (int i = 0; i < 3; ++i)
+#pragma unroll 1
+      for (int j = 0; j < 3; ++j) {
+        T d2 = seg_seg(A[i], A[i == 2 ? 0 : i + 1], B[j], B[j == 2 ? 0 : j + 1], c1, c2);
+        if (d2 < best) {
+          best = d2;
+          pa = c1;
+          pb = c2;
+        }
+      }
+    return best;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Free-flight pose at time t in binary64, every operation rounded on its own
+// (paper Section 2.1).  h = t - t_cur, X = x + v h, q(t) = dq (x) q0 with
+// dq = (cos phi, (sin phi / phi) (h/2) w), phi = |w| h / 2.  cos phi and
+// sin phi / phi come from their Taylor series in z = phi^2 = (|w|^2 h^2) / 4,
+// Horner form with 10 terms and exact integer denominators (2k-1)2k and
+// 2k(2k+1), k = 10..1 (no square root, no library trigonometry; truncation
+// error below 1e-17 for phi <= 1.5).  R is the rotation matrix of q(t),
+// row-major.
+constexpr int POSE_TERMS = 10;
+
+__device__ __forceinline__ void pose_exact(const double *st, int64_t n, int64_t p, double t,
+                                           double R[9], double X[3]) {
+  using O = OpsD;
+  const double h = O::sub(t, st[13 * n + p]);
+  const double wx = st[10 * n + p], wy = st[11 * n + p], wz = st[12 * n + p];
+  const double w2 = O::add(O::add(O::mul(wx, wx), O::mul(wy, wy)), O::mul(wz, wz));
+  const double z = O::mul(O::mul(w2, O::mul(h, h)), 0.25);
+  double c = 1.0, sn = 1.0;
+#pragma unroll
+  for (int k = POSE_TERMS; k >= 1; --k) {
+    c = O::sub(1.0, O::mul(O::div(z, (double)((2 * k - 1) * (2 * k))), c));
+    sn = O::sub(1.0, O::mul(O::div(z, (double)((2 * k) * (2 * k + 1))), sn));
+  }
+  const double g = O::mul(O::mul(h, 0.5), sn);
+  const double pw = c, px = O::mul(g, wx), py = O::mul(g, wy), pz = O::mul(g, wz);
+  const double qw = st[6 * n + p], qx = st[7 * n + p], qy = st[8 * n + p], qz = st[9 * n + p];
+  // Hamilton product dq (x) q0, each component summed left to right
+  const double rw = O::sub(O::sub(O::sub(O::mul(pw, qw), O::mul(px, qx)), O::mul(py, qy)), O::mul(pz, qz));
+  const double rx = O::sub(O::add(O::add(O::mul(pw, qx), O::mul(px, qw)), O::mul(py, qz)), O::mul(pz, qy));
+  const double ry = O::add(O::add(O::sub(O::mul(pw, qy), O::mul(px, qz)), O::mul(py, qw)), O::mul(pz, qx));
+  const double rz = O::add(O::sub(O::add(O::mul(pw, qz), O::mul(px, qy)), O::mul(py, qx)), O::mul(pz, qw));
+  R[0] = O::sub(1.0, O::mul(2.0, O::add(O::mul(ry, ry), O::mul(rz, rz))));
+  R[1] = O::mul(2.0, O::sub(O::mul(rx, ry), O::mul(rw, rz)));
+  R[2] = O::mul(2.0, O::add(O::mul(rx, rz), O::mul(rw, ry)));
+  R[3] = O::mul(2.0, O::add(O::mul(rx, ry), O::mul(rw, rz)));
+  R[4] = O::sub(1.0, O::mul(2.0, O::add(O::mul(rx, rx), O::mul(rz, rz))));
+  R[5] = O::mul(2.0, O::sub(O::mul(ry, rz), O::mul(rw, rx)));
+  R[6] = O::mul(2.0, O::sub(O::mul(rx, rz), O::mul(rw, ry)));
+  R[7] = O::mul(2.0, O::add(O::mul(ry, rz), O::mul(rw, rx)));
+  R[8] = O::sub(1.0, O::mul(2.0, O::add(O::mul(rx, rx), O::mul(ry, ry))));
+  X[0] = O::add(st[0 * n + p], O::mul(st[3 * n + p], h));
+  X[1] = O::add(st[1 * n + p], O::mul(st[4 * n + p], h));
+  X[2] = O::add(st[2 * n + p], O::mul(st[5 * n + p], h));
+}
+
+// World position R b + X of a body-frame vertex: ((R0 bx + R1 by) + R2 bz) + X0.
+__device__ __forceinline__ V3<double> to_world_exact(const double *R, const double *X, float bx,
+                                                     float by, float bz) {
+  using O = OpsD;
+  const double x = bx, y = by, z = bz;
+  return V3<double>{
+      O::add(O::add(O::add(O::mul(R[0], x), O::mul(R[1], y)), O::mul(R[2], z)), X[0]),
+      O::add(O::add(O::add(O::mul(R[3], x), O::mul(R[4], y)), O::mul(R[5], z)), X[1]),
+      O::add(O::add(O::add(O::mul(R[6], x), O::mul(R[7], y)), O::mul(R[8], z)), X[2])};
+}
+
+}  // namespace dem

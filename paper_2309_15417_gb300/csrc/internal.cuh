@@ -1,0 +1,93 @@
+// internal.cuh -- declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dem.h"
+#include "geom.cuh"
+
+namespace dem {
+
+// sticky device error bits (context error word)
+constexpr uint32_t ERR_CAPACITY = 1u;  // an output capacity was exceeded
+constexpr uint32_t ERR_TIMEOUT = 2u;   // a bounded wait ran out
+constexpr uint32_t ERR_INDEX = 4u;     // an index out of range was met
+
+// counters, same order as dem_stats
+enum {
+  ST_SPHERE = 0,
+  ST_GROUP,
+  ST_FP32,
+  ST_FP64,
+  ST_EVALS,
+  ST_CHECKS,
+  ST_BISECT,
+  ST_CONTACTS,
+  ST_PAIRS,
+  ST_N = 16
+};
+
+// swept sphere of a particle (centre, radius), binary64
+struct __align__(32) Sphere4 {
+  double x, y, z, w;
+};
+
+struct Scratch {
+  // common
+  uint32_t *err;                  // [1]
+  unsigned long long *stats;      // [ST_N]
+  unsigned int *work;             // [4] work counters of persistent kernels
+  // scan temporaries
+  int64_t *scan_part;             // [SCAN_PART_CAP]
+  int64_t *tmp;                   // [8] device scalars (totals)
+  // broad phase
+  int64_t cap_particles;
+  int64_t table_size;             // hash buckets (power of two)
+  Sphere4 *sph;                   // [n] swept spheres (mx, my, mz, rho)
+  int4 *cell;                     // [n] (cx, cy, cz, bucket)
+  int32_t *bucket_cnt;            // [table]
+  int64_t *bucket_start;          // [table]
+  int32_t *bucket_cur;            // [table]
+  int32_t *bucket_ids;            // [n]
+  int64_t *pcnt;                  // [n] candidates per particle
+  int64_t *poff;                  // [n]
+  unsigned long long *rho_max;    // [1] (bits of a non-negative double)
+  // narrow phase
+  int64_t cap_pairs;
+  int64_t cap_contacts;
+  int32_t *st_keys;               // [cap_contacts][3] staging
+  double *st_geom;                // [cap_contacts][7]
+  unsigned long long *st_count;   // [1]
+  int64_t *pc;                    // [cap_pairs] contacts per pair
+  int64_t *po;                    // [cap_pairs] exclusive offsets
+  int32_t *pcur;                  // [cap_pairs] scatter cursors
+  int32_t *sidx;                  // [cap_contacts] staging index per output slot
+};
+
+constexpr int64_t SCAN_BLOCK = 2048;           // elements per scan block
+constexpr int64_t SCAN_PART_CAP = 4096;        // partial sums (=> up to 8M elements)
+
+// exclusive scan of n int64 values (in may alias out); total written to
+// *total if non-null.  Grid-wide, no inter-block waits.
+void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total,
+                        int64_t *part, cudaStream_t s);
+void scan_exclusive_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *part,
+                               cudaStream_t s);
+
+// launchers
+cudaError_t launch_broad(const dem_particles &P, int32_t *pairs, int64_t cap, int64_t *n_pairs,
+                         Scratch &S, cudaStream_t s);
+cudaError_t launch_narrow(int prec, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
+                          const int64_t *n_pairs, const double *t_eval, const dem_narrow_out &out,
+                          Scratch &S, int num_sms, cudaStream_t s);
+cudaError_t launch_ctime(int prec, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
+                         const int64_t *n_pairs, int K, double tol, double *t_coll,
+                         uint8_t *status, int32_t *tri_ab, Scratch &S, int num_sms,
+                         cudaStream_t s);
+cudaError_t launch_clusters(int64_t n, const int32_t *edges, int64_t max_edges,
+                            const int64_t *n_edges, const uint8_t *is_static, int32_t *id,
+                            int64_t *n_clusters, Scratch &S, cudaStream_t s);
+
+__device__ __forceinline__ void set_err(uint32_t *err, uint32_t bit) { atomicOr(err, bit); }
+
+}  // namespace dem

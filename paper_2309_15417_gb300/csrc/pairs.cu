@@ -1,0 +1,1125 @@
+// pairs.cu -- narrow phase and collision-time search over candidate pairs.
+//
+// Paper Section 5 ("Time step size calculation"): for a candidate pair the
+// minimum triangle-pair distance is evaluated at given times; a contact is a
+// triangle pair within eps_i + eps_j (Definition of a contact point); the
+// collision time stamp is the first time the halos meet in the pair's
+// interval (case distinction; narrowing by K samples and bisection; the upper
+// bracket end as "widening").
+//
+// GPU design (one persistent CTA works on one pair at a time, pairs taken from
+// an atomic counter):
+//  * Triangle tiles of both particles are staged in shared memory by bulk
+//    copies (cp.async.bulk + mbarrier).  In FP32 mode particle A stays in its
+//    body frame (its float32 vertices are exact) and B is moved into A's frame
+//    with the relative pose, computed in FP64 and rounded once per time.
+//  * Culling: bounding spheres of groups of 32 consecutive triangles, then of
+//    triangles; only triangle pairs whose spheres come within the threshold
+//    reach the full distance.  The culling is conservative by construction
+//    (margins below), so it never changes a result.
+//  * Each warp owns a candidate list and evaluates it itself (no block-wide
+//    barrier in the inner loop).
+//  * FP32 distances carry an error bound E = ERR_REL32 * S, S = R_A + R_B +
+//    |x_B - x_A| (the coordinate scale in A's frame).  A decision d <= eps is
+//    taken in FP32 only when |d32 - eps| > E; otherwise the triangle pair is
+//    recomputed in binary64 with the fixed operation order of geom.cuh, in the
+//    world frame, from the same float32 vertices.  The closest pair (argmin)
+//    is chosen among all triangle pairs with d32 <= min d32 + 2E, recomputed
+//    in binary64, smallest (d^2, a, b).  Decisions and argmin are therefore
+//    the binary64 ones.
+//  * FP64 mode computes every distance in binary64 in the world frame.
+#include <cstdio>
+
+#include "internal.cuh"
+
+namespace dem {
+
+namespace {
+
+constexpr int NT = 256;
+constexpr int NW = NT / 32;
+constexpr int G = 32;        // triangles per group
+constexpr int WCAP = 256;    // per-warp candidate list capacity
+// FP32 error bound relative to the pair's coordinate scale (2^-14).  The
+// observed maximum of |d32 - d64| / S over the adversarial and workload cases
+// in the tests is below 2^-20.
+constexpr double ERR_REL32 = 6.103515625e-05;
+constexpr double ERR_REL64_LB = 9.094947017729282e-13;  // 2^-40: FP64 culling margin
+
+constexpr int MODE_NARROW = 0;
+constexpr int MODE_CTIME = 1;
+
+template <int PREC>
+struct Cfg;
+template <>
+struct Cfg<0> {
+  static constexpr int TT = 512;
+  using T = float;
+  using O = OpsF;
+};
+template <>
+struct Cfg<1> {
+  static constexpr int TT = 256;
+  using T = double;
+  using O = OpsD;
+};
+
+struct PairArgs {
+  int64_t n;
+  const double *st;
+  const int64_t *tri_off;
+  const float4 *tris;
+  int64_t n_tris;
+  const int32_t *pairs;
+  int64_t max_pairs;
+  const int64_t *n_pairs;
+  // narrow phase
+  const double *t_eval;
+  double *dmin, *pa, *pb;
+  int32_t *tri_ab;
+  uint8_t *flag;
+  float *dmin32;
+  int32_t *st_keys;
+  double *st_geom;
+  unsigned long long *st_count;
+  int64_t st_cap;
+  int64_t *pc;
+  // collision times
+  double *t_coll;
+  uint8_t *status;
+  int32_t *ct_ab;
+  int K;
+  double tol;
+  // bookkeeping
+  unsigned int *work;
+  uint32_t *err;
+  unsigned long long *stats;
+};
+
+template <int PREC>
+struct __align__(128) Smem {
+  using T = typename Cfg<PREC>::T;
+  static constexpr int TT = Cfg<PREC>::TT;
+  static constexpr int NG = TT / G;
+  float4 Ab[3][TT];                 // A tile, body frame (bulk copy target)
+  float4 Bb[3][TT];                 // B tile, body frame (bulk copy target)
+  T Ae[PREC ? 9 : 1][PREC ? TT : 1];  // A tile, evaluation frame (FP64 only)
+  T Be[9][TT];                      // B tile, evaluation frame [slot*3+coord][tri]
+  T SA[4][TT];                      // triangle spheres of A (cx, cy, cz, r)
+  T SB[4][TT];
+  T GA[4][NG];                      // group spheres
+  T GB[4][NG];
+  uint32_t gp[NG * NG];             // group pairs passing the group test
+  T gplb[NG * NG];                  // their lower bounds
+  uint32_t wl[NW][WCAP];            // per-warp candidate lists (a << 16 | b)
+  double RA[9], XA[3], RB[9], XB[3];
+  float Rr[9], tr[3];
+  double eps, ts, T_, Ed, Elb;
+  int64_t i, j, offA, offB;
+  int nA, nB, ngp, found, resA, resB, frmA, frmB, bad, abort;
+  unsigned long long bound;         // bits of a non-negative double
+  unsigned long long mbar;
+  double red_d[NW];
+  unsigned long long red_k[NW];
+  double mhat;
+  double best_d2;
+  unsigned long long best_key;
+  double best_pa[3], best_pb[3];
+  unsigned int work_item;
+  unsigned long long cnt[ST_N];
+};
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         unsigned long long *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait on the barrier phase; false if it ran out
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t phase) {
+  for (uint32_t it = 0; it < (1u << 22); ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long dbits(double x) {
+  return static_cast<unsigned long long>(__double_as_longlong(x));
+}
+__device__ __forceinline__ double bitsd(unsigned long long b) {
+  return __longlong_as_double(static_cast<long long>(b));
+}
+
+// ---------------------------------------------------------------- the CTA
+template <int PREC>
+struct Cta {
+  using T = typename Cfg<PREC>::T;
+  using O = typename Cfg<PREC>::O;
+  using GT = Geo<O>;
+  using GD = Geo<OpsD>;
+  using V = V3<T>;
+  static constexpr int TT = Cfg<PREC>::TT;
+  static constexpr int NG = TT / G;
+
+  Smem<PREC> &s;
+  const PairArgs &A;
+  int tid, w, lane;
+  uint32_t phase;
+  // per-evaluation warp state
+  T mw;                        // warp minimum of evaluated distances
+  double bd2;                  // lane best exact (d^2, key) and points
+  unsigned long long bkey;
+  double bpa[3], bpb[3];
+
+  __device__ Cta(Smem<PREC> &s_, const PairArgs &A_) : s(s_), A(A_) {
+    tid = threadIdx.x;
+    w = tid >> 5;
+    lane = tid & 31;
+    phase = 0;
+  }
+
+  __device__ void stat(int k, unsigned long long v) {
+    if (v) atomicAdd(&s.cnt[k], v);
+  }
+
+  __device__ int ntiles(int n) const { return (n + TT - 1) / TT; }
+
+  // --- tiles -------------------------------------------------------------
+  // Make body tiles ta of A and tb of B resident; false if a copy timed out.
+  __device__ bool load_tiles(int ta, int tb) {
+    const bool needA = s.resA != ta, needB = s.resB != tb;
+    __syncthreads();  // all reads of the previous tiles are done
+    if (!needA && !needB) return true;
+    const int na = min(TT, s.nA - ta * TT), nb = min(TT, s.nB - tb * TT);
+    if (tid == 0) {
+      s.resA = ta;
+      s.resB = tb;
+      s.frmA = needA ? -1 : s.frmA;
+      s.frmB = -1;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      uint32_t bytes = (needA ? 3u * 16u * na : 0u) + (needB ? 3u * 16u * nb : 0u);
+      mbar_expect_tx(&s.mbar, bytes);
+      if (needA)
+        for (int sl = 0; sl < 3; ++sl)
+          bulk_g2s(&s.Ab[sl][0], A.tris + sl * A.n_tris + s.offA + (int64_t)ta * TT, 16u * na, &s.mbar);
+      if (needB)
+        for (int sl = 0; sl < 3; ++sl)
+          bulk_g2s(&s.Bb[sl][0], A.tris + sl * A.n_tris + s.offB + (int64_t)tb * TT, 16u * nb, &s.mbar);
+    }
+    bool ok = mbar_wait(&s.mbar, phase);
+    ok = __syncthreads_and(ok) != 0;
+    phase ^= 1u;
+    if (!ok) {
+      if (tid == 0) {
+        set_err(A.err, ERR_TIMEOUT);
+        s.abort = 1;
+      }
+      mbar_wait(&s.mbar, phase ^ 1u);  // let the copies in flight land
+    }
+    __syncthreads();
+    return ok;
+  }
+
+  // triangle spheres (centroid, max vertex distance) of n triangles
+  __device__ void spheres(T (*S)[TT], int n, bool isA) {
+    for (int k = tid; k < n; k += NT) {
+      V v[3];
+      load_vtx(isA, k, v);
+      T third = T(1) / T(3);
+      T cx = (v[0].x + v[1].x + v[2].x) * third;
+      T cy = (v[0].y + v[1].y + v[2].y) * third;
+      T cz = (v[0].z + v[1].z + v[2].z) * third;
+      T r2 = T(0);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        T dx = v[q].x - cx, dy = v[q].y - cy, dz = v[q].z - cz;
+        T d = dx * dx + dy * dy + dz * dz;
+        r2 = d > r2 ? d : r2;
+      }
+      S[0][k] = cx;
+      S[1][k] = cy;
+      S[2][k] = cz;
+      S[3][k] = O::sqrt(r2);
+    }
+  }
+  // group spheres of n triangles: box centre of the triangle spheres, radius
+  // covering every triangle sphere
+  __device__ void groups(T (*S)[TT], T (*GS)[NG], int n) {
+    const int ng = (n + G - 1) / G;
+    for (int g = w; g < ng; g += NW) {
+      const int k = g * G + lane;
+      const bool v = k < n;
+      T cx = v ? S[0][k] : T(0), cy = v ? S[1][k] : T(0), cz = v ? S[2][k] : T(0), r = v ? S[3][k] : T(0);
+      const T big = O::inf();
+      T lox = warp_min(v ? cx - r : big), hix = warp_max(v ? cx + r : -big);
+      T loy = warp_min(v ? cy - r : big), hiy = warp_max(v ? cy + r : -big);
+      T loz = warp_min(v ? cz - r : big), hiz = warp_max(v ? cz + r : -big);
+      T gx = (lox + hix) * T(0.5), gy = (loy + hiy) * T(0.5), gz = (loz + hiz) * T(0.5);
+      T dx = cx - gx, dy = cy - gy, dz = cz - gz;
+      T gr = warp_max(v ? O::sqrt(dx * dx + dy * dy + dz * dz) + r : T(0));
+      if (lane == 0) {
+        GS[0][g] = gx;
+        GS[1][g] = gy;
+        GS[2][g] = gz;
+        GS[3][g] = gr;
+      }
+    }
+  }
+
+  // vertices of triangle k of the A or B tile in the evaluation frame
+  __device__ __forceinline__ void load_vtx(bool isA, int k, V v[3]) const {
+    if constexpr (PREC == 0) {
+      if (isA) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          float4 f = s.Ab[q][k];
+          v[q] = V{T(f.x), T(f.y), T(f.z)};
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) v[q] = V{s.Be[3 * q][k], s.Be[3 * q + 1][k], s.Be[3 * q + 2][k]};
+      }
+    } else {
+      if (isA) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) v[q] = V{s.Ae[3 * q][k], s.Ae[3 * q + 1][k], s.Ae[3 * q + 2][k]};
+      } else {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) v[q] = V{s.Be[3 * q][k], s.Be[3 * q + 1][k], s.Be[3 * q + 2][k]};
+      }
+    }
+  }
+
+  // evaluation-frame data for tiles (ta, tb) at the current time
+  __device__ void frames(int ta, int tb) {
+    const int na = min(TT, s.nA - ta * TT), nb = min(TT, s.nB - tb * TT);
+    const bool doA = s.frmA != ta, doB = s.frmB != tb;
+    if (!doA && !doB) return;
+    if constexpr (PREC == 1) {
+      if (doA)
+      for (int k = tid; k < na; k += NT)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          float4 f = s.Ab[q][k];
+          V3<double> p = to_world_exact(s.RA, s.XA, f.x, f.y, f.z);
+          s.Ae[3 * q][k] = T(p.x);
+          s.Ae[3 * q + 1][k] = T(p.y);
+          s.Ae[3 * q + 2][k] = T(p.z);
+        }
+    }
+    if (doB) {
+      for (int k = tid; k < nb; k += NT)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          float4 f = s.Bb[q][k];
+          if constexpr (PREC == 0) {
+            const float *R = s.Rr;
+            s.Be[3 * q][k] = T(fmaf(R[0], f.x, fmaf(R[1], f.y, fmaf(R[2], f.z, s.tr[0]))));
+            s.Be[3 * q + 1][k] = T(fmaf(R[3], f.x, fmaf(R[4], f.y, fmaf(R[5], f.z, s.tr[1]))));
+            s.Be[3 * q + 2][k] = T(fmaf(R[6], f.x, fmaf(R[7], f.y, fmaf(R[8], f.z, s.tr[2]))));
+          } else {
+            V3<double> p = to_world_exact(s.RB, s.XB, f.x, f.y, f.z);
+            s.Be[3 * q][k] = T(p.x);
+            s.Be[3 * q + 1][k] = T(p.y);
+            s.Be[3 * q + 2][k] = T(p.z);
+          }
+        }
+    }
+    __syncthreads();
+    if (doA) spheres(s.SA, na, true);
+    if (doB) spheres(s.SB, nb, false);
+    __syncthreads();
+    if (doA) groups(s.SA, s.GA, na);
+    if (doB) groups(s.SB, s.GB, nb);
+    __syncthreads();
+    if (tid == 0) {
+      s.frmA = ta;
+      s.frmB = tb;
+    }
+  }
+
+  // --- exact binary64 triangle pair (world frame, fixed operation order) --
+  __device__ double exact(int a, int b, V3<double> &pa, V3<double> &pb) const {
+    V3<double> X[3], Y[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      float4 f = s.Ab[q][a];
+      X[q] = to_world_exact(s.RA, s.XA, f.x, f.y, f.z);
+      float4 g = s.Bb[q][b];
+      Y[q] = to_world_exact(s.RB, s.XB, g.x, g.y, g.z);
+    }
+    return GD::tri_dist2(X, Y, pa, pb);
+  }
+
+  __device__ void world_of_A_frame(const V &p, double out[3]) const {
+    // FP32 points live in A's body frame: x_world = R_A p + X_A
+    const double x = p.x, y = p.y, z = p.z;
+    out[0] = s.RA[0] * x + s.RA[1] * y + s.RA[2] * z + s.XA[0];
+    out[1] = s.RA[3] * x + s.RA[4] * y + s.RA[5] * z + s.XA[1];
+    out[2] = s.RA[6] * x + s.RA[7] * y + s.RA[8] * z + s.XA[2];
+  }
+
+  // --- evaluate a warp's candidate list ------------------------------------
+  template <bool DECIDE, bool ARGMIN, bool CONTACTS>
+  __device__ void warp_eval(int cnt, int ta, int tb, int64_t pk, bool pass1) {
+    const T eps = T(s.eps);
+    const T Ed = T(s.Ed);
+    unsigned long long n32 = 0, n64 = 0, ncon = 0;
+    for (int e = 0; e < cnt; e += 32) {
+      const int k = e + lane;
+      const bool have = k < cnt;
+      const uint32_t ent = have ? s.wl[w][k] : 0u;
+      const int a = int(ent >> 16), b = int(ent & 0xffffu);
+      T d2 = O::inf();
+      V pa{}, pb{};
+      if (have) {
+        V X[3], Y[3];
+        load_vtx(true, a, X);
+        load_vtx(false, b, Y);
+        if (DECIDE && !ARGMIN && !CONTACTS) {
+          // features first; the crossing test only when they do not settle it
+          d2 = GT::tri_dist2_features(X, Y, pa, pb);
+          if (!(O::sqrt(d2) < eps - Ed)) {
+            V x;
+            bool hit = false;
+            for (int q = 0; q < 3 && !hit; ++q) hit = GT::seg_tri_cross(X[q], X[q == 2 ? 0 : q + 1], Y[0], Y[1], Y[2], x);
+            for (int q = 0; q < 3 && !hit; ++q) hit = GT::seg_tri_cross(Y[q], Y[q == 2 ? 0 : q + 1], X[0], X[1], X[2], x);
+            if (hit) d2 = T(0);
+          }
+        } else {
+          d2 = GT::tri_dist2(X, Y, pa, pb);
+        }
+        ++n32;
+      }
+      const T d = O::sqrt(d2);
+      const int ag = ta * TT + a, bg = tb * TT + b;
+      const unsigned long long key = (static_cast<unsigned long long>(ag) << 32) | static_cast<unsigned>(bg);
+      if (DECIDE) {
+        bool yes;
+        if (PREC == 0) {
+          yes = have && d < eps - Ed;
+          const bool band = have && !yes && d <= eps + Ed;
+          if (band) {
+            V3<double> qa, qb;
+            double e2 = exact(a, b, qa, qb);
+            ++n64;
+            yes = OpsD::sqrt(e2) <= s.eps;
+          }
+        } else {
+          yes = have && d <= eps;
+        }
+        if (__any_sync(0xffffffffu, yes) && lane == 0) s.found = 1;
+      }
+      if (ARGMIN || CONTACTS) {
+        // warp minimum of the FP32 (or FP64) distances seen so far
+        mw = fmin(mw, warp_min(have ? d : O::inf()));
+        bool con = false;
+        double gd = 0.0, ga3[3] = {0, 0, 0}, gb3[3] = {0, 0, 0};
+        if (PREC == 0) {
+          const bool band = CONTACTS && have && d >= eps - Ed && d <= eps + Ed;
+          const bool am = ARGMIN && have && d <= mw + T(2) * Ed;
+          double e2 = 0.0;
+          V3<double> qa{}, qb{};
+          if (band || am) {
+            e2 = exact(a, b, qa, qb);
+            ++n64;
+            if (am && (e2 < bd2 || (e2 == bd2 && key < bkey))) {
+              bd2 = e2;
+              bkey = key;
+              bpa[0] = qa.x; bpa[1] = qa.y; bpa[2] = qa.z;
+              bpb[0] = qb.x; bpb[1] = qb.y; bpb[2] = qb.z;
+            }
+          }
+          if (CONTACTS && have) {
+            if (band) {
+              gd = OpsD::sqrt(e2);
+              con = gd <= s.eps;
+              ga3[0] = qa.x; ga3[1] = qa.y; ga3[2] = qa.z;
+              gb3[0] = qb.x; gb3[1] = qb.y; gb3[2] = qb.z;
+            } else if (d < eps - Ed) {
+              con = true;
+              gd = double(d);
+              world_of_A_frame(pa, ga3);
+              world_of_A_frame(pb, gb3);
+            }
+          }
+        } else {
+          if (ARGMIN && have && (double(d2) < bd2 || (double(d2) == bd2 && key < bkey))) {
+            bd2 = double(d2);
+            bkey = key;
+            bpa[0] = pa.x; bpa[1] = pa.y; bpa[2] = pa.z;
+            bpb[0] = pb.x; bpb[1] = pb.y; bpb[2] = pb.z;
+          }
+          if (CONTACTS && have && d <= eps) {
+            con = true;
+            gd = double(d);
+            ga3[0] = pa.x; ga3[1] = pa.y; ga3[2] = pa.z;
+            gb3[0] = pb.x; gb3[1] = pb.y; gb3[2] = pb.z;
+          }
+        }
+        if (CONTACTS) {
+          const uint32_t m = __ballot_sync(0xffffffffu, con);
+          if (m) {
+            unsigned long long base = 0;
+            if (lane == 0) {
+              base = atomicAdd(A.st_count, (unsigned long long)__popc(m));
+              atomicAdd(reinterpret_cast<unsigned long long *>(&A.pc[pk]), (unsigned long long)__popc(m));
+            }
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (con) {
+              const unsigned long long slot = base + __popc(m & lanemask_lt());
+              if (slot < (unsigned long long)A.st_cap) {
+                A.st_keys[3 * slot] = int32_t(pk);
+                A.st_keys[3 * slot + 1] = ag;
+                A.st_keys[3 * slot + 2] = bg;
+                double *gg = A.st_geom + 7 * slot;
+                gg[0] = gd;
+                gg[1] = ga3[0]; gg[2] = ga3[1]; gg[3] = ga3[2];
+                gg[4] = gb3[0]; gg[5] = gb3[1]; gg[6] = gb3[2];
+              } else {
+                set_err(A.err, ERR_CAPACITY);
+              }
+            }
+            ncon += __popc(m);
+          }
+        }
+        if (ARGMIN && pass1 && lane == 0) {
+          // tighten the shared bound with this warp's minimum
+          const double nb = double(mw) + 3.0 * s.Ed + s.Elb;
+          atomicMin(&s.bound, dbits(nb));
+        }
+      }
+    }
+    // counters (lane sums)
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      n32 += __shfl_xor_sync(0xffffffffu, n32, o);
+      n64 += __shfl_xor_sync(0xffffffffu, n64, o);
+    }
+    if (lane == 0) {
+      stat(ST_FP32, n32);
+      stat(ST_FP64, n64);
+      stat(ST_CONTACTS, ncon);
+    }
+  }
+
+  // --- one pass over tile pair (ta, tb) -------------------------------------
+  // pass 0: triangle pairs with sphere bound LB <= th0;
+  // pass 1: th0 < LB <= bound (shared, shrinking).
+  template <bool DECIDE, bool ARGMIN, bool CONTACTS>
+  __device__ void scan_tiles(int ta, int tb, bool pass1, T th0, int64_t pk) {
+    const int na = min(TT, s.nA - ta * TT), nb = min(TT, s.nB - tb * TT);
+    const int nga = (na + G - 1) / G, ngb = (nb + G - 1) / G;
+    const T Elb = T(s.Elb);
+    if (tid == 0) s.ngp = 0;
+    __syncthreads();
+    // group pairs
+    {
+      const T gth = pass1 ? T(bitsd(s.bound)) + Elb : th0 + Elb;
+      for (int q = tid; q < nga * ngb; q += NT) {
+        const int ga = q / ngb, gb = q - ga * ngb;
+        const T dx = s.GA[0][ga] - s.GB[0][gb], dy = s.GA[1][ga] - s.GB[1][gb], dz = s.GA[2][ga] - s.GB[2][gb];
+        const T lb = O::sqrt(dx * dx + dy * dy + dz * dz) - s.GA[3][ga] - s.GB[3][gb];
+        if (lb <= gth) {
+          const int pos = atomicAdd(&s.ngp, 1);
+          s.gp[pos] = (uint32_t(ga) << 16) | uint32_t(gb);
+          s.gplb[pos] = lb;
+        }
+      }
+      if (tid == 0) stat(ST_GROUP, (unsigned long long)(nga * ngb));
+    }
+    __syncthreads();
+    // triangle pairs: warp w takes rows w, w+NW, ... of the surviving group pairs
+    const int rows = s.ngp * G;
+    int cnt = 0;
+    unsigned long long ntests = 0;
+    for (int idx = w; idx < rows; idx += NW) {
+      if (DECIDE) {
+        // one read per warp, broadcast: the exit is warp-uniform
+        int f = lane == 0 ? *(volatile int *)&s.found : 0;
+        if (__shfl_sync(0xffffffffu, f, 0)) break;
+      }
+      const int p = idx >> 5, r = idx & 31;
+      const uint32_t gpe = s.gp[p];
+      const int a = int(gpe >> 16) * G + r;
+      if (a >= na) continue;
+      if (pass1) {
+        unsigned long long bb = lane == 0 ? *(volatile unsigned long long *)&s.bound : 0ull;
+        bb = __shfl_sync(0xffffffffu, bb, 0);
+        if (s.gplb[p] > T(bitsd(bb)) + Elb) continue;
+      }
+      const int b = int(gpe & 0xffffu) * G + lane;
+      const bool valid = b < nb;
+      const T ax = s.SA[0][a], ay = s.SA[1][a], az = s.SA[2][a], ar = s.SA[3][a];
+      T dx = T(0), dy = T(0), dz = T(0), br = T(0);
+      if (valid) {
+        dx = ax - s.SB[0][b];
+        dy = ay - s.SB[1][b];
+        dz = az - s.SB[2][b];
+        br = s.SB[3][b];
+      }
+      const T d2c = dx * dx + dy * dy + dz * dz;
+      const T t0 = th0 + ar + br;
+      bool cand;
+      if (!pass1) {
+        cand = valid && d2c <= t0 * t0;
+      } else {
+        // every centroid pair bounds the minimum distance from above
+        const T rowmin = warp_min(valid ? d2c : O::inf());
+        if (lane == 0) {
+          const double ub = double(O::sqrt(rowmin)) + 2.0 * s.Elb + 4.0 * s.Ed;
+          atomicMin(&s.bound, dbits(ub));
+        }
+        __syncwarp();
+        const T bnd = T(bitsd(*(volatile unsigned long long *)&s.bound)) + Elb;
+        const T t1 = bnd + ar + br;
+        cand = valid && d2c <= t1 * t1 && !(d2c <= t0 * t0);
+      }
+      ntests += __popc(__ballot_sync(0xffffffffu, valid));
+      const uint32_t m = __ballot_sync(0xffffffffu, cand);
+      if (cand) s.wl[w][cnt + __popc(m & lanemask_lt())] = (uint32_t(a) << 16) | uint32_t(b);
+      cnt += __popc(m);
+      __syncwarp();
+      if (cnt > WCAP - 32) {
+        warp_eval<DECIDE, ARGMIN, CONTACTS>(cnt, ta, tb, pk, pass1);
+        cnt = 0;
+        __syncwarp();
+      }
+    }
+    if (cnt) warp_eval<DECIDE, ARGMIN, CONTACTS>(cnt, ta, tb, pk, pass1);
+    if (lane == 0) stat(ST_SPHERE, ntests);
+    __syncthreads();
+  }
+
+  // --- pose at t ------------------------------------------------------------
+  __device__ void set_time(double t) {
+    if (tid == 0) {
+      pose_exact(A.st, A.n, s.i, t, s.RA, s.XA);
+      pose_exact(A.st, A.n, s.j, t, s.RB, s.XB);
+      double d[3] = {s.XB[0] - s.XA[0], s.XB[1] - s.XA[1], s.XB[2] - s.XA[2]};
+      double tr[3];
+      for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c)
+          s.Rr[r * 3 + c] = float(s.RA[r] * s.RB[c] + s.RA[3 + r] * s.RB[3 + c] + s.RA[6 + r] * s.RB[6 + c]);
+        tr[r] = s.RA[r] * d[0] + s.RA[3 + r] * d[1] + s.RA[6 + r] * d[2];
+        s.tr[r] = float(tr[r]);
+      }
+      const double ri = A.st[16 * A.n + s.i], rj = A.st[16 * A.n + s.j];
+      if (PREC == 0) {
+        const double S = ri + rj + sqrt(tr[0] * tr[0] + tr[1] * tr[1] + tr[2] * tr[2]);
+        s.Ed = S * ERR_REL32;
+        s.Elb = s.Ed;
+        // FP32 A-frame data stay valid; B moves
+        s.frmB = -1;
+      } else {
+        const double S = ri + rj + sqrt(s.XA[0] * s.XA[0] + s.XA[1] * s.XA[1] + s.XA[2] * s.XA[2]) +
+                         sqrt(s.XB[0] * s.XB[0] + s.XB[1] * s.XB[1] + s.XB[2] * s.XB[2]);
+        s.Ed = 0.0;
+        s.Elb = S * ERR_REL64_LB;
+        s.frmA = -1;
+        s.frmB = -1;
+      }
+      s.found = 0;
+      s.bound = dbits(OpsD::inf());
+    }
+    __syncthreads();
+  }
+
+  // --- one evaluation of the pair at time t ---------------------------------
+  // DECIDE: returns whether some triangle pair is within eps (binary64).
+  // ARGMIN: leaves the exact closest pair in s.best_*, FP32 minimum in s.mhat.
+  template <bool DECIDE, bool ARGMIN, bool CONTACTS>
+  __device__ bool eval(double t, int64_t pk) {
+    set_time(t);
+    mw = O::inf();
+    bd2 = OpsD::inf();
+    bkey = ~0ull;
+    bpa[0] = bpa[1] = bpa[2] = 0.0;
+    bpb[0] = bpb[1] = bpb[2] = 0.0;
+    const int nta = ntiles(s.nA), ntb = ntiles(s.nB);
+    const T th0 = T(s.eps) + T(s.Elb);
+    bool stop = false;
+    for (int ta = 0; ta < nta && !stop; ++ta)
+      for (int tb = 0; tb < ntb && !stop; ++tb) {
+        if (!load_tiles(ta, tb)) return false;
+        frames(ta, tb);
+        scan_tiles<DECIDE, ARGMIN, CONTACTS>(ta, tb, false, th0, pk);
+        if (DECIDE && s.found) stop = true;
+      }
+    if (ARGMIN) {
+      // FP32 (FP64) minimum over the evaluated pairs
+      const double mh = block_min(double(mw));
+      const bool complete = mh + 3.0 * s.Ed + s.Elb <= double(th0);
+      if (!complete && nta > 0 && ntb > 0) {
+        if (tid == 0) s.bound = dbits(mh + 3.0 * s.Ed + s.Elb);  // inf if nothing seen
+        __syncthreads();
+        for (int ta = 0; ta < nta; ++ta)
+          for (int tb = 0; tb < ntb; ++tb) {
+            if (!load_tiles(ta, tb)) return false;
+            frames(ta, tb);
+            scan_tiles<false, true, false>(ta, tb, true, th0, pk);
+          }
+      }
+      const double mh2 = block_min(double(mw));
+      reduce_best();
+      if (tid == 0) s.mhat = mh2;
+      __syncthreads();
+    }
+    const bool f = DECIDE ? (*(volatile int *)&s.found != 0) : false;
+    __syncthreads();
+    return f;
+  }
+
+  __device__ double block_min(double v) {
+    v = warp_min(v);
+    __syncthreads();
+    if (lane == 0) s.red_d[w] = v;
+    __syncthreads();
+    double r = s.red_d[0];
+#pragma unroll
+    for (int q = 1; q < NW; ++q) r = fmin(r, s.red_d[q]);
+    __syncthreads();
+    return r;
+  }
+
+  // block-wide smallest (d^2, key) and its points into s.best_*
+  __device__ void reduce_best() {
+    double d = bd2;
+    unsigned long long k = bkey;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const double od = __shfl_xor_sync(0xffffffffu, d, o);
+      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, k, o);
+      if (od < d || (od == d && ok < k)) {
+        d = od;
+        k = ok;
+      }
+    }
+    __syncthreads();
+    if (lane == 0) {
+      s.red_d[w] = d;
+      s.red_k[w] = k;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double bd = s.red_d[0];
+      unsigned long long bk = s.red_k[0];
+      for (int q = 1; q < NW; ++q)
+        if (s.red_d[q] < bd || (s.red_d[q] == bd && s.red_k[q] < bk)) {
+          bd = s.red_d[q];
+          bk = s.red_k[q];
+        }
+      s.best_d2 = bd;
+      s.best_key = bk;
+      for (int q = 0; q < 3; ++q) s.best_pa[q] = s.best_pb[q] = 0.0;
+    }
+    __syncthreads();
+    if (bkey != ~0ull && bkey == s.best_key && bd2 == s.best_d2) {
+      for (int q = 0; q < 3; ++q) {
+        s.best_pa[q] = bpa[q];
+        s.best_pb[q] = bpb[q];
+      }
+    }
+    __syncthreads();
+  }
+
+  // --- per pair setup --------------------------------------------------------
+  __device__ bool setup_pair(int64_t k) {
+    if (tid == 0) {
+      const int64_t i = A.pairs[2 * k], j = A.pairs[2 * k + 1];
+      s.bad = 0;
+      if (i < 0 || j < 0 || i >= A.n || j >= A.n) {
+        set_err(A.err, ERR_INDEX);
+        s.bad = 1;
+        s.i = s.j = 0;
+        s.nA = s.nB = 0;
+      } else {
+        s.i = i;
+        s.j = j;
+        s.offA = A.tri_off[i];
+        s.offB = A.tri_off[j];
+        const int64_t nA = A.tri_off[i + 1] - s.offA, nB = A.tri_off[j + 1] - s.offB;
+        if (nA < 0 || nB < 0 || s.offA < 0 || s.offB < 0 || s.offA + nA > A.n_tris ||
+            s.offB + nB > A.n_tris || nA >= (1 << 24) || nB >= (1 << 24)) {
+          set_err(A.err, ERR_INDEX);
+          s.bad = 1;
+          s.nA = s.nB = 0;
+        } else {
+          s.nA = int(nA);
+          s.nB = int(nB);
+        }
+      }
+      const double *st = A.st;
+      const int64_t n = A.n;
+      s.eps = OpsD::add(st[15 * n + s.i], st[15 * n + s.j]);
+      const double ti = st[13 * n + s.i], tj = st[13 * n + s.j];
+      const double di = st[14 * n + s.i], dj = st[14 * n + s.j];
+      s.ts = ti < tj ? ti : tj;
+      s.T_ = di < dj ? di : dj;
+      s.resA = s.resB = -1;
+      s.frmA = s.frmB = -1;
+    }
+    __syncthreads();
+    return !s.bad;
+  }
+};
+
+__device__ __forceinline__ int64_t pair_count(const PairArgs &A) {
+  int64_t m = A.max_pairs;
+  if (A.n_pairs) {
+    const int64_t c = *A.n_pairs;
+    m = c < m ? c : m;
+  }
+  return m < 0 ? 0 : m;
+}
+
+template <int PREC, int MODE>
+__global__ void __launch_bounds__(NT, 2) pair_kernel(PairArgs A) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Smem<PREC> &s = *reinterpret_cast<Smem<PREC> *>(smem_raw);
+  Cta<PREC> c(s, A);
+  if (c.tid < ST_N) s.cnt[c.tid] = 0;
+  if (c.tid == 0) {
+    mbar_init(&s.mbar);
+    s.abort = 0;
+  }
+  __syncthreads();
+  const int64_t m = pair_count(A);
+  for (;;) {
+    if (c.tid == 0) s.work_item = atomicAdd(A.work, 1u);
+    __syncthreads();
+    const int64_t k = s.work_item;
+    const bool quit = s.abort != 0;
+    __syncthreads();
+    if (k >= m || quit) break;
+    const bool ok = c.setup_pair(k);
+    const double chk = double(s.nA) * double(s.nB);
+    if (MODE == MODE_NARROW) {
+      const double t = A.t_eval ? A.t_eval[k] : s.ts;
+      if (ok) c.template eval<false, true, true>(t, k);
+      if (c.tid == 0) {
+        const bool have = ok && s.best_key != ~0ull && s.nA > 0 && s.nB > 0;
+        const double d = have ? OpsD::sqrt(s.best_d2) : OpsD::inf();
+        A.dmin[k] = d;
+        for (int q = 0; q < 3; ++q) {
+          A.pa[3 * k + q] = have ? s.best_pa[q] : 0.0;
+          A.pb[3 * k + q] = have ? s.best_pb[q] : 0.0;
+        }
+        A.tri_ab[2 * k] = have ? int32_t(s.best_key >> 32) : -1;
+        A.tri_ab[2 * k + 1] = have ? int32_t(s.best_key & 0xffffffffu) : -1;
+        A.flag[k] = uint8_t(have && d <= s.eps);
+        if (A.dmin32) A.dmin32[k] = have ? float(s.mhat) : __int_as_float(0x7f800000);
+        atomicAdd(&s.cnt[ST_EVALS], 1ull);
+        atomicAdd(&s.cnt[ST_CHECKS], (unsigned long long)chk);
+        atomicAdd(&s.cnt[ST_PAIRS], 1ull);
+      }
+    } else {
+      // collision-time search (binary64, operations in the order of the
+      // definition, each rounded on its own)
+      using D = OpsD;
+      const double ts = s.ts, T = s.T_;
+      int evals = 0, bis = 0;
+      uint8_t status = 0;
+      double tc = D::add(ts, T);
+      int32_t ta = -1, tb = -1;
+      if (ok && s.nA > 0 && s.nB > 0) {
+        ++evals;
+        if (c.template eval<true, false, false>(ts, k)) {
+          status = 1;
+          c.template eval<false, true, false>(ts, k);
+          ta = int32_t(s.best_key >> 32);
+          tb = int32_t(s.best_key & 0xffffffffu);
+        } else {
+          bool fnd = false;
+          double lo = ts, hi = ts;
+          for (int q = 1; q <= A.K; ++q) {
+            const double tq = D::add(ts, D::div(D::mul(T, double(q)), double(A.K)));
+            ++evals;
+            if (c.template eval<true, false, false>(tq, k)) {
+              lo = D::add(ts, D::div(D::mul(T, double(q - 1)), double(A.K)));
+              hi = tq;
+              fnd = true;
+              break;
+            }
+          }
+          if (fnd) {
+            const double lim = D::mul(A.tol, T);
+            while (D::sub(hi, lo) > lim) {
+              const double mid = D::add(lo, D::mul(0.5, D::sub(hi, lo)));
+              ++evals;
+              ++bis;
+              if (c.template eval<true, false, false>(mid, k))
+                hi = mid;
+              else
+                lo = mid;
+            }
+            status = 2;
+            tc = hi;
+            c.template eval<false, true, false>(hi, k);
+            ta = int32_t(s.best_key >> 32);
+            tb = int32_t(s.best_key & 0xffffffffu);
+          }
+        }
+      }
+      if (c.tid == 0) {
+        A.t_coll[k] = tc;
+        A.status[k] = status;
+        A.ct_ab[2 * k] = ta;
+        A.ct_ab[2 * k + 1] = tb;
+        atomicAdd(&s.cnt[ST_EVALS], (unsigned long long)evals);
+        atomicAdd(&s.cnt[ST_CHECKS], (unsigned long long)(chk * evals));
+        atomicAdd(&s.cnt[ST_BISECT], (unsigned long long)bis);
+        atomicAdd(&s.cnt[ST_PAIRS], 1ull);
+      }
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (c.tid < ST_N && s.cnt[c.tid]) atomicAdd(&A.stats[c.tid], s.cnt[c.tid]);
+}
+
+// ------------------------------------------------------------- contact sort
+// Contacts of each pair are gathered from the staging area and sorted by
+// (a, b) in shared memory (bitonic), then written in order.
+constexpr int SORT_CAP = 4096;
+
+__global__ void contact_scatter(const int32_t *st_keys, const unsigned long long *st_count, int64_t st_cap,
+                                const int64_t *po, int32_t *pcur, int32_t *sidx, int64_t cap,
+                                uint32_t *err) {
+  const int64_t nst = min((int64_t)*st_count, st_cap);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nst;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t pk = st_keys[3 * e];
+    const int64_t slot = po[pk] + atomicAdd(&pcur[pk], 1);
+    if (slot < cap) sidx[slot] = int32_t(e);
+  }
+}
+
+__global__ void __launch_bounds__(256) contact_sort(const int32_t *st_keys, const double *st_geom,
+                                                   int64_t st_cap, const int64_t *pc, const int64_t *po,
+                                                   const int64_t *n_pairs, int64_t max_pairs,
+                                                   const int32_t *sidx, int32_t *out_keys,
+                                                   double *out_geom, int64_t cap, uint32_t *err) {
+  __shared__ unsigned long long key[SORT_CAP];
+  __shared__ int32_t val[SORT_CAP];
+  int64_t m = max_pairs;
+  if (n_pairs) m = min(m, *n_pairs);
+  for (int64_t pk = blockIdx.x; pk < m; pk += gridDim.x) {
+    const int64_t cnt = pc[pk], base = po[pk];
+    if (cnt == 0) continue;
+    if (base + cnt > cap) {
+      if (threadIdx.x == 0) set_err(err, ERR_CAPACITY);
+      continue;
+    }
+    if (cnt > SORT_CAP) {  // too many for the shared-memory sort: copy unsorted, flag
+      if (threadIdx.x == 0) set_err(err, ERR_CAPACITY);
+      for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const int e = sidx[base + q];
+        if (e < 0 || e >= st_cap) continue;
+        const int64_t o = base + q;
+        out_keys[3 * o] = int32_t(pk);
+        out_keys[3 * o + 1] = st_keys[3 * (int64_t)e + 1];
+        out_keys[3 * o + 2] = st_keys[3 * (int64_t)e + 2];
+        for (int c = 0; c < 7; ++c) out_geom[7 * o + c] = st_geom[7 * (int64_t)e + c];
+      }
+      __syncthreads();
+      continue;
+    }
+    int n2 = 1;
+    while (n2 < cnt) n2 <<= 1;
+    for (int q = threadIdx.x; q < n2; q += blockDim.x) {
+      const int e = q < cnt ? sidx[base + q] : -1;
+      if (e >= 0 && e < st_cap) {
+        key[q] = (static_cast<unsigned long long>(static_cast<uint32_t>(st_keys[3 * (int64_t)e + 1])) << 32) |
+                 static_cast<uint32_t>(st_keys[3 * (int64_t)e + 2]);
+        val[q] = e;
+      } else {
+        key[q] = ~0ull;
+        val[q] = -1;
+      }
+    }
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int q = threadIdx.x; q < n2; q += blockDim.x) {
+          const int l = q ^ j;
+          if (l > q) {
+            const bool up = (q & k) == 0;
+            const unsigned long long kq = key[q], kl = key[l];
+            if ((kq > kl) == up) {
+              key[q] = kl;
+              key[l] = kq;
+              const int32_t t = val[q];
+              val[q] = val[l];
+              val[l] = t;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+      const int e = val[q];
+      if (e < 0) continue;
+      const int64_t o = base + q;
+      out_keys[3 * o] = int32_t(pk);
+      out_keys[3 * o + 1] = st_keys[3 * e + 1];
+      out_keys[3 * o + 2] = st_keys[3 * e + 2];
+      for (int c = 0; c < 7; ++c) out_geom[7 * o + c] = st_geom[7 * (int64_t)e + c];
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void contact_total(const int64_t *total, const unsigned long long *st_count, int64_t st_cap,
+                              int64_t *n_contacts, uint32_t *err) {
+  const int64_t t = *total;
+  *n_contacts = t;
+  if ((int64_t)*st_count > st_cap) set_err(err, ERR_CAPACITY);
+}
+
+template <int PREC, int MODE>
+cudaError_t launch_pairs(const PairArgs &a, int num_sms, cudaStream_t s) {
+  const size_t smem = sizeof(Smem<PREC>);
+  cudaError_t e = cudaFuncSetAttribute(pair_kernel<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_kernel<PREC, MODE>, NT, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)num_sms * per_sm;
+  if (a.max_pairs < grid) grid = a.max_pairs > 0 ? a.max_pairs : 1;
+  pair_kernel<PREC, MODE><<<(unsigned)grid, NT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+PairArgs make_args(const dem_particles &P, const int32_t *pairs, int64_t max_pairs, const int64_t *n_pairs,
+                   Scratch &S) {
+  PairArgs a{};
+  a.n = P.n;
+  a.st = P.state;
+  a.tri_off = P.tri_off;
+  a.tris = reinterpret_cast<const float4 *>(P.tris);
+  a.n_tris = P.n_tris;
+  a.pairs = pairs;
+  a.max_pairs = max_pairs;
+  a.n_pairs = n_pairs;
+  a.work = S.work;
+  a.err = S.err;
+  a.stats = S.stats;
+  return a;
+}
+
+}  // namespace
+
+cudaError_t launch_narrow(int prec, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
+                          const int64_t *n_pairs, const double *t_eval, const dem_narrow_out &out,
+                          Scratch &S, int num_sms, cudaStream_t s) {
+  PairArgs a = make_args(P, pairs, max_pairs, n_pairs, S);
+  a.t_eval = t_eval;
+  a.dmin = out.dmin;
+  a.pa = out.pa;
+  a.pb = out.pb;
+  a.tri_ab = out.tri_ab;
+  a.flag = out.flag;
+  a.dmin32 = out.dmin32;
+  a.st_keys = S.st_keys;
+  a.st_geom = S.st_geom;
+  a.st_count = S.st_count;
+  a.st_cap = S.cap_contacts;
+  a.pc = S.pc;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(S.work, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(S.st_count, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+  if (max_pairs > 0) {
+    if ((e = cudaMemsetAsync(S.pc, 0, sizeof(int64_t) * max_pairs, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(S.pcur, 0, sizeof(int32_t) * max_pairs, s)) != cudaSuccess) return e;
+    e = prec == 0 ? launch_pairs<0, MODE_NARROW>(a, num_sms, s) : launch_pairs<1, MODE_NARROW>(a, num_sms, s);
+    if (e != cudaSuccess) return e;
+  }
+  // per-pair offsets, scatter, sort
+  int64_t *total = S.tmp;
+  if (max_pairs > 0) {
+    scan_exclusive_i64(S.pc, S.po, max_pairs, total, S.scan_part, s);
+  } else {
+    if ((e = cudaMemsetAsync(total, 0, sizeof(int64_t), s)) != cudaSuccess) return e;
+  }
+  if (max_pairs > 0) {
+    contact_scatter<<<num_sms * 4, 256, 0, s>>>(S.st_keys, S.st_count, S.cap_contacts, S.po, S.pcur, S.sidx,
+                                                out.contact_cap < S.cap_contacts ? out.contact_cap : S.cap_contacts,
+                                                S.err);
+    contact_sort<<<num_sms * 4, 256, 0, s>>>(S.st_keys, S.st_geom, S.cap_contacts, S.pc, S.po, n_pairs,
+                                             max_pairs, S.sidx,
+                                             out.contacts, out.contact_geom,
+                                             out.contact_cap < S.cap_contacts ? out.contact_cap : S.cap_contacts,
+                                             S.err);
+  }
+  contact_total<<<1, 1, 0, s>>>(total, S.st_count, S.cap_contacts, out.n_contacts, S.err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ctime(int prec, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
+                         const int64_t *n_pairs, int K, double tol, double *t_coll, uint8_t *status,
+                         int32_t *tri_ab, Scratch &S, int num_sms, cudaStream_t s) {
+  PairArgs a = make_args(P, pairs, max_pairs, n_pairs, S);
+  a.t_coll = t_coll;
+  a.status = status;
+  a.ct_ab = tri_ab;
+  a.K = K;
+  a.tol = tol;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(S.work, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
+  if (max_pairs <= 0) return cudaSuccess;
+  return prec == 0 ? launch_pairs<0, MODE_CTIME>(a, num_sms, s) : launch_pairs<1, MODE_CTIME>(a, num_sms, s);
+}
+
+}  // namespace dem

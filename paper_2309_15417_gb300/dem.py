@@ -1,0 +1,293 @@
+"""Thin Python binding of the C-ABI in include/dem.h (ctypes).
+
+Argument marshalling only: every step of the contact-detection path runs in
+the CUDA library ``libdem.so``.  Arrays are torch tensors on the CUDA device
+(torch provides device memory and streams); their data pointers are passed
+through unchanged.  There is no CPU fallback: if the library cannot be built
+or loaded, :func:`load` raises.
+
+Function names follow the C-ABI: :func:`dem_create`, :func:`dem_build_candidates`,
+:func:`dem_narrow_phase`, :func:`dem_collision_times`, :func:`dem_clusters`,
+:func:`dem_check`, :func:`dem_get_stats`.  :class:`Context` and
+:class:`Scene` wrap them for convenience (capacities, output allocation).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+DEM_NFIELDS = 17
+DEM_PREC_FP32_FIXUP = 0
+DEM_PREC_FP64 = 1
+
+STATUS = {0: "DEM_OK", -1: "DEM_ERR_ARG", -2: "DEM_ERR_CAPACITY", -3: "DEM_ERR_CUDA", -4: "DEM_ERR_INDEX",
+          -5: "DEM_ERR_TIMEOUT"}
+
+# every symbol include/dem.h declares
+EXPORTS = ["dem_create", "dem_destroy", "dem_last_error", "dem_build_candidates", "dem_narrow_phase",
+           "dem_collision_times", "dem_clusters", "dem_check", "dem_get_stats"]
+
+
+class DemError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class dem_config(C.Structure):
+    _fields_ = [("K", C.c_int32), ("bisect_tol", C.c_double), ("precision", C.c_int32),
+                ("reserved", C.c_int32), ("max_particles", C.c_int64), ("max_pairs", C.c_int64),
+                ("max_contacts", C.c_int64)]
+
+
+class dem_particles(C.Structure):
+    _fields_ = [("n", C.c_int64), ("state", C.c_void_p), ("is_static", C.c_void_p), ("tri_off", C.c_void_p),
+                ("tris", C.c_void_p), ("n_tris", C.c_int64)]
+
+
+class dem_narrow_out(C.Structure):
+    _fields_ = [("dmin", C.c_void_p), ("pa", C.c_void_p), ("pb", C.c_void_p), ("tri_ab", C.c_void_p),
+                ("flag", C.c_void_p), ("dmin32", C.c_void_p), ("contacts", C.c_void_p),
+                ("contact_geom", C.c_void_p), ("contact_cap", C.c_int64), ("n_contacts", C.c_void_p)]
+
+
+class dem_stats(C.Structure):
+    _fields_ = [("sphere_tests", C.c_int64), ("group_tests", C.c_int64), ("dist_fp32", C.c_int64),
+                ("dist_fp64", C.c_int64), ("pair_evals", C.c_int64), ("method_checks", C.c_int64),
+                ("bisect_steps", C.c_int64), ("contacts", C.c_int64), ("pairs_done", C.c_int64),
+                ("reserved", C.c_int64 * 7)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libdem.so (building it in-tree first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_needed else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library missing: {path}")
+        L = C.CDLL(path)
+        vp, i64 = C.c_void_p, C.c_int64
+        L.dem_create.argtypes = [C.POINTER(dem_config), C.POINTER(vp)]
+        L.dem_create.restype = C.c_int
+        L.dem_destroy.argtypes = [vp]
+        L.dem_destroy.restype = None
+        L.dem_last_error.argtypes = [vp]
+        L.dem_last_error.restype = C.c_char_p
+        L.dem_build_candidates.argtypes = [vp, C.POINTER(dem_particles), vp, i64, vp, vp]
+        L.dem_build_candidates.restype = C.c_int
+        L.dem_narrow_phase.argtypes = [vp, C.POINTER(dem_particles), vp, i64, vp, vp, C.POINTER(dem_narrow_out), vp]
+        L.dem_narrow_phase.restype = C.c_int
+        L.dem_collision_times.argtypes = [vp, C.POINTER(dem_particles), vp, i64, vp, vp, vp, vp, vp]
+        L.dem_collision_times.restype = C.c_int
+        L.dem_clusters.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp, vp]
+        L.dem_clusters.restype = C.c_int
+        L.dem_check.argtypes = [vp, vp]
+        L.dem_check.restype = C.c_int
+        L.dem_get_stats.argtypes = [vp, C.POINTER(dem_stats), C.c_int]
+        L.dem_get_stats.restype = C.c_int
+        _lib = L
+        return L
+
+
+# ------------------------------------------------------------------ helpers
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _cuda(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name}: expected a contiguous CUDA tensor of {dtype}")
+    return t
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _check(ctx, rc):
+    if rc != 0:
+        L = load()
+        raise DemError(rc, L.dem_last_error(ctx).decode() if ctx else "")
+
+
+# ------------------------------------------------------------------ C-ABI mirrors
+
+def dem_create(K=8, tol=1e-3, precision=DEM_PREC_FP32_FIXUP, max_particles=65536, max_pairs=1 << 20,
+               max_contacts=1 << 20):
+    L = load()
+    cfg = dem_config(K=K, bisect_tol=tol, precision=precision, reserved=0, max_particles=max_particles,
+                     max_pairs=max_pairs, max_contacts=max_contacts)
+    h = C.c_void_p()
+    rc = L.dem_create(C.byref(cfg), C.byref(h))
+    if rc != 0:
+        raise DemError(rc, "dem_create")
+    return h
+
+
+def dem_destroy(ctx):
+    load().dem_destroy(ctx)
+
+
+def dem_build_candidates(ctx, P: dem_particles, pairs, cap: int, n_pairs, stream=None):
+    _check(ctx, load().dem_build_candidates(ctx, C.byref(P), _ptr(pairs), int(cap), _ptr(n_pairs), _stream(stream)))
+
+
+def dem_narrow_phase(ctx, P: dem_particles, pairs, max_pairs: int, n_pairs, t_eval, out: dem_narrow_out,
+                     stream=None):
+    _check(ctx, load().dem_narrow_phase(ctx, C.byref(P), _ptr(pairs), int(max_pairs), _ptr(n_pairs),
+                                        _ptr(t_eval), C.byref(out), _stream(stream)))
+
+
+def dem_collision_times(ctx, P: dem_particles, pairs, max_pairs: int, n_pairs, t_coll, status, tri_ab,
+                        stream=None):
+    _check(ctx, load().dem_collision_times(ctx, C.byref(P), _ptr(pairs), int(max_pairs), _ptr(n_pairs),
+                                           _ptr(t_coll), _ptr(status), _ptr(tri_ab), _stream(stream)))
+
+
+def dem_clusters(ctx, n: int, edges, max_edges: int, n_edges, is_static, cluster_id, n_clusters, stream=None):
+    _check(ctx, load().dem_clusters(ctx, int(n), _ptr(edges), int(max_edges), _ptr(n_edges), _ptr(is_static),
+                                    _ptr(cluster_id), _ptr(n_clusters), _stream(stream)))
+
+
+def dem_check(ctx, stream=None):
+    _check(ctx, load().dem_check(ctx, _stream(stream)))
+
+
+def dem_get_stats(ctx, reset=False) -> dict:
+    st = dem_stats()
+    _check(ctx, load().dem_get_stats(ctx, C.byref(st), 1 if reset else 0))
+    return st.as_dict()
+
+
+# ------------------------------------------------------------------ convenience
+
+class Scene:
+    """Particle arrays resident on the device (the dem_particles of the C-ABI)."""
+
+    def __init__(self, state, is_static, tri_off, tris):
+        import torch
+        self.state = _cuda(state, torch.float64, "state")
+        self.is_static = _cuda(is_static, torch.uint8, "is_static")
+        self.tri_off = _cuda(tri_off, torch.int64, "tri_off")
+        self.tris = _cuda(tris, torch.float32, "tris")
+        self.n = int(self.state.shape[1])
+        self.n_tris = int(self.tris.shape[1])
+        self.P = dem_particles(n=self.n, state=self.state.data_ptr(), is_static=self.is_static.data_ptr(),
+                               tri_off=self.tri_off.data_ptr(), tris=self.tris.data_ptr(), n_tris=self.n_tris)
+
+    @classmethod
+    def from_workload(cls, w, device="cuda"):
+        import torch
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        return cls(t(w.state), t(w.is_static), t(w.tri_off), t(w.tris))
+
+
+class Context:
+    """Owns a dem_ctx and output buffers sized for its capacities."""
+
+    def __init__(self, K=8, tol=1e-3, precision=DEM_PREC_FP32_FIXUP, max_particles=65536, max_pairs=1 << 20,
+                 max_contacts=1 << 20, device="cuda"):
+        import torch
+        self.device = torch.device(device)
+        self.max_pairs = int(max_pairs)
+        self.max_contacts = int(max_contacts)
+        self.h = dem_create(K, tol, precision, max_particles, max_pairs, max_contacts)
+        z = lambda *s, dt: torch.zeros(*s, dtype=dt, device=self.device)
+        self.pairs = z(self.max_pairs, 2, dt=torch.int32)
+        self.n_pairs = z(1, dt=torch.int64)
+        self.dmin = z(self.max_pairs, dt=torch.float64)
+        self.pa = z(self.max_pairs, 3, dt=torch.float64)
+        self.pb = z(self.max_pairs, 3, dt=torch.float64)
+        self.tri_ab = z(self.max_pairs, 2, dt=torch.int32)
+        self.flag = z(self.max_pairs, dt=torch.uint8)
+        self.dmin32 = z(self.max_pairs, dt=torch.float32)
+        self.contacts = z(self.max_contacts, 3, dt=torch.int32)
+        self.contact_geom = z(self.max_contacts, 7, dt=torch.float64)
+        self.n_contacts = z(1, dt=torch.int64)
+        self.t_coll = z(self.max_pairs, dt=torch.float64)
+        self.status = z(self.max_pairs, dt=torch.uint8)
+        self.ct_ab = z(self.max_pairs, 2, dt=torch.int32)
+        self.n_clusters = z(1, dt=torch.int64)
+        self.cluster_id = None
+        self.out = dem_narrow_out(dmin=self.dmin.data_ptr(), pa=self.pa.data_ptr(), pb=self.pb.data_ptr(),
+                                  tri_ab=self.tri_ab.data_ptr(), flag=self.flag.data_ptr(),
+                                  dmin32=self.dmin32.data_ptr(), contacts=self.contacts.data_ptr(),
+                                  contact_geom=self.contact_geom.data_ptr(), contact_cap=self.max_contacts,
+                                  n_contacts=self.n_contacts.data_ptr())
+
+    def close(self):
+        if self.h:
+            dem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # one call each ------------------------------------------------------
+    def build_candidates(self, scene: Scene, stream=None):
+        dem_build_candidates(self.h, scene.P, self.pairs, self.max_pairs, self.n_pairs, stream)
+
+    def narrow_phase(self, scene: Scene, pairs=None, n_pairs=None, t_eval=None, stream=None):
+        """Default: the candidate pairs held by this context (device count)."""
+        if pairs is None:
+            pairs, m, cnt = self.pairs, self.max_pairs, self.n_pairs
+        else:
+            m, cnt = int(pairs.shape[0]), n_pairs
+        dem_narrow_phase(self.h, scene.P, pairs, m, cnt, t_eval, self.out, stream)
+
+    def collision_times(self, scene: Scene, pairs=None, n_pairs=None, stream=None):
+        if pairs is None:
+            pairs, m, cnt = self.pairs, self.max_pairs, self.n_pairs
+        else:
+            m, cnt = int(pairs.shape[0]), n_pairs
+        dem_collision_times(self.h, scene.P, pairs, m, cnt, self.t_coll, self.status, self.ct_ab, stream)
+
+    def clusters(self, scene: Scene, edges=None, n_edges=None, stream=None):
+        import torch
+        if self.cluster_id is None or self.cluster_id.numel() < scene.n:
+            self.cluster_id = torch.zeros(max(scene.n, 1), dtype=torch.int32, device=self.device)
+        if edges is None:
+            edges, m, cnt = self.pairs, self.max_pairs, self.n_pairs
+        else:
+            m, cnt = int(edges.shape[0]), n_edges
+        dem_clusters(self.h, scene.n, edges, m, cnt, scene.is_static, self.cluster_id, self.n_clusters, stream)
+
+    def step(self, scene: Scene, stream=None):
+        """One pass of the whole path: candidates, narrow phase at the pair
+        start, collision times, clusters of the candidate graph."""
+        self.build_candidates(scene, stream)
+        self.narrow_phase(scene, stream=stream)
+        self.collision_times(scene, stream=stream)
+        self.clusters(scene, stream=stream)
+
+    def check(self, stream=None):
+        dem_check(self.h, stream)
+
+    def stats(self, reset=False):
+        return dem_get_stats(self.h, reset)

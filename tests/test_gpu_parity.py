@@ -1,0 +1,365 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
+
+Bar (per output):
+  candidate pairs, contact flags, contact (pair, a, b) sets and order, closest
+  triangle pair (a, b), collision statuses and times, cluster ids: bit-exact;
+  closest-pair distance and points: bit-exact (they come from the binary64
+  recomputation in both precision modes);
+  contact-list geometry: bit-exact in FP64 mode, within 1e-5 * R in FP32 mode
+  (R = particle radius; a contact far from the halo boundary keeps its FP32
+  distance and points).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_15417_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+PRECS = [0, 1]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ctx(dem, w, prec, max_pairs=None, max_contacts=1 << 20):
+    return dem.Context(K=w.K, tol=w.tol, precision=prec, max_particles=max(w.n, 16),
+                       max_pairs=max_pairs or max(4096, 4 * w.n), max_contacts=max_contacts)
+
+
+def _pairs_tensor(pairs):
+    torch = _torch()
+    return torch.from_numpy(np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)).cuda()
+
+
+def gpu_candidates(dem, w, prec=0):
+    c = _ctx(dem, w, prec)
+    sc = dem.Scene.from_workload(w)
+    c.build_candidates(sc)
+    c.check()
+    m = int(c.n_pairs.item())
+    return c.pairs[:m].cpu().numpy()
+
+
+def gpu_narrow(dem, w, pairs, prec, t_eval=None):
+    torch = _torch()
+    c = _ctx(dem, w, prec, max_pairs=max(len(pairs), 1))
+    sc = dem.Scene.from_workload(w)
+    pt = _pairs_tensor(pairs)
+    te = None if t_eval is None else torch.from_numpy(np.ascontiguousarray(t_eval, np.float64)).cuda()
+    c.narrow_phase(sc, pairs=pt, n_pairs=None, t_eval=te)
+    c.check()
+    m = len(pairs)
+    nc = int(c.n_contacts.item())
+    return dict(dmin=c.dmin[:m].cpu().numpy(), pa=c.pa[:m].cpu().numpy(), pb=c.pb[:m].cpu().numpy(),
+                tri_ab=c.tri_ab[:m].cpu().numpy(), flag=c.flag[:m].cpu().numpy(),
+                dmin32=c.dmin32[:m].cpu().numpy(), contacts=c.contacts[:nc].cpu().numpy(),
+                geom=c.contact_geom[:nc].cpu().numpy(), stats=c.stats(reset=True))
+
+
+def gpu_ctime(dem, w, pairs, prec):
+    c = _ctx(dem, w, prec, max_pairs=max(len(pairs), 1))
+    sc = dem.Scene.from_workload(w)
+    pt = _pairs_tensor(pairs)
+    c.collision_times(sc, pairs=pt)
+    c.check()
+    m = len(pairs)
+    return dict(t_coll=c.t_coll[:m].cpu().numpy(), status=c.status[:m].cpu().numpy(),
+                tri_ab=c.ct_ab[:m].cpu().numpy(), stats=c.stats(reset=True))
+
+
+def _world_tri(w, p, t, a):
+    R, X = oracle.pose(w.state, int(p), float(t))
+    k = int(w.tri_off[p]) + int(a)
+    return np.stack([R @ w.tris[s, k, :3].astype(np.float64) + X for s in range(3)])
+
+
+def assert_contact_geometry(g_keys, g_geom, o_geom, w, pairs, t_eval, tol):
+    """FP32 contact geometry: the distance within tol; the closest points are
+    not unique for (near-)parallel triangles (paper Section 5, contact
+    points), so each point must lie on its triangle and |pa - pb| = d, within
+    tol."""
+    assert np.max(np.abs(g_geom[:, 0] - o_geom[:, 0]), initial=0.0) <= tol
+    for (k, a, b), gg in zip(g_keys, g_geom):
+        i, j = pairs[k]
+        t = t_eval[k] if t_eval is not None else min(w.state[W.F_TCUR, i], w.state[W.F_TCUR, j])
+        TA, TB = _world_tri(w, i, t, a), _world_tri(w, j, t, b)
+        da, _ = oracle.closest_pt_tri(gg[1:4], TA)
+        db, _ = oracle.closest_pt_tri(gg[4:7], TB)
+        assert np.sqrt(da) <= tol and np.sqrt(db) <= tol
+        assert abs(np.linalg.norm(gg[1:4] - gg[4:7]) - gg[0]) <= tol
+
+
+def assert_narrow_equal(g, o, w, pairs, prec, t_eval=None):
+    R = float(np.max(w.state[W.F_RADIUS]))
+    assert np.array_equal(g["flag"], o["flag"])
+    assert np.array_equal(g["tri_ab"], o["tri_ab"])
+    assert np.array_equal(g["dmin"], o["dmin"])
+    assert np.array_equal(g["pa"], o["pa"]) and np.array_equal(g["pb"], o["pb"])
+    assert np.array_equal(g["contacts"], o["contacts"])
+    if prec == 1:
+        assert np.array_equal(g["geom"], o["geom"])
+    else:
+        assert_contact_geometry(g["contacts"], g["geom"], o["geom"], w, pairs, t_eval, 1e-5 * R)
+    # raw FP32 minimum is close to the FP64 one
+    fin = np.isfinite(o["dmin"])
+    assert np.max(np.abs(g["dmin32"][fin] - o["dmin"][fin]), initial=0.0) <= 1e-5 * R
+
+
+# ----------------------------------------------------------------------------- broad phase
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_broad_phase_small(dem, seed):
+    w = W.small_icospheres(seed)
+    assert np.array_equal(gpu_candidates(dem, w), oracle.broad_phase(w))
+
+
+def test_broad_phase_dense_full_size(dem):
+    w = W.dense_packing(0)
+    g = gpu_candidates(dem, w)
+    o = oracle.broad_phase(w)
+    assert len(o) > 1000
+    assert np.array_equal(g, o)
+
+
+def test_broad_phase_uneven_radii(dem):
+    w = W.uneven_meshes(0, n=600, box=60.0)
+    assert np.array_equal(gpu_candidates(dem, w), oracle.broad_phase(w))
+
+
+def test_broad_phase_empty_and_static(dem):
+    w = W.small_icospheres(0, n=8)
+    w.state[W.F_X] += np.arange(8) * 100.0  # far apart: no pairs
+    assert len(gpu_candidates(dem, w)) == 0
+    w2 = W.small_icospheres(0)
+    w2.is_static[:2] = 1  # injected overlapping pair (0,1) becomes static-static
+    g = gpu_candidates(dem, w2)
+    assert np.array_equal(g, oracle.broad_phase(w2))
+    assert (0, 1) not in {tuple(p) for p in g}
+
+
+# ----------------------------------------------------------------------------- narrow phase
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("seed", [0, 1])
+def test_narrow_small_icospheres(dem, seed, prec):
+    w = W.small_icospheres(seed)
+    pairs = oracle.broad_phase(w)
+    g = gpu_narrow(dem, w, pairs, prec)
+    o = oracle.narrow_phase(w, pairs)
+    assert_narrow_equal(g, o, w, pairs, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_narrow_dense_subset(dem, prec):
+    w = W.dense_packing(3, nside=4)
+    pairs = oracle.broad_phase(w)
+    g = gpu_narrow(dem, w, pairs, prec)
+    o = oracle.narrow_phase(w, pairs)
+    assert (o["flag"] == 1).any() and (o["flag"] == 0).any() and (o["dmin"] == 0).any()
+    assert_narrow_equal(g, o, w, pairs, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_narrow_dense_full_size_sampled(dem, prec):
+    """1000 icospheres (320 triangles): the GPU runs every candidate pair; the
+    oracle checks a seeded sample of them one by one."""
+    w = W.dense_packing(0)
+    pairs = oracle.broad_phase(w)
+    g = gpu_narrow(dem, w, pairs, prec)
+    rng = np.random.default_rng(7)
+    idx = np.sort(rng.choice(len(pairs), 24, replace=False))
+    o = oracle.narrow_phase(w, pairs[idx])
+    for key in ("flag", "tri_ab", "dmin", "pa", "pb"):
+        assert np.array_equal(g[key][idx], o[key]), key
+    # contacts of the sampled pairs
+    gk = g["contacts"]
+    sel = np.isin(gk[:, 0], idx)
+    remap = {int(k): n for n, k in enumerate(idx)}
+    gsub = gk[sel].copy()
+    gsub[:, 0] = [remap[int(k)] for k in gsub[:, 0]]
+    assert np.array_equal(gsub, o["contacts"])
+    R = 1.0
+    if prec == 1:
+        assert np.array_equal(g["geom"][sel], o["geom"])
+    else:
+        assert_contact_geometry(gsub, g["geom"][sel], o["geom"], w, pairs[idx], None, 1e-5 * R)
+    # contact counts of all pairs are consistent with the sorted output
+    assert np.all(np.diff(gk[:, 0]) >= 0)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_narrow_uneven_meshes_multi_tile(dem, prec):
+    """Ragged sizes: 80/320/1280-triangle icospheres and 20-200-point hulls
+    (1280 > one shared-memory tile: several tiles per particle)."""
+    w = W.uneven_meshes(1, n=300, box=30.0)
+    pairs = oracle.broad_phase(w)
+    cnt = w.tri_counts()
+    big = pairs[(cnt[pairs[:, 0]] * cnt[pairs[:, 1]]) >= 1280 * 80]
+    rest = pairs[(cnt[pairs[:, 0]] * cnt[pairs[:, 1]]) < 1280 * 80]
+    sel = np.concatenate([big[:6], rest[:20]])
+    sel = sel[np.lexsort((sel[:, 1], sel[:, 0]))]
+    assert len(sel) >= 10
+    g = gpu_narrow(dem, w, sel, prec)
+    o = oracle.narrow_phase(w, sel)
+    assert_narrow_equal(g, o, w, sel, prec)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_narrow_time_eval_and_empty(dem, prec):
+    w = W.small_icospheres(0)
+    pairs = np.array([[0, 1], [2, 3], [4, 5], [2, 3]], np.int32)
+    te = np.array([0.0, 4.5e-4, 1e-3, 9e-4])
+    g = gpu_narrow(dem, w, pairs, prec, t_eval=te)
+    o = oracle.narrow_phase(w, pairs, t_eval=te)
+    assert_narrow_equal(g, o, w, pairs, prec, t_eval=te)
+    # zero pairs
+    g0 = gpu_narrow(dem, w, np.zeros((0, 2), np.int32), prec)
+    assert len(g0["contacts"]) == 0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_narrow_adversarial_triangles(dem, prec):
+    """One-triangle particles in near-degenerate configurations (near-parallel
+    edges, slivers, near-touching, near-intersecting)."""
+    rng = np.random.default_rng(11)
+    for trial in range(40):
+        A = rng.normal(0, 1, (3, 3))
+        B = A.copy()
+        kind = trial % 4
+        if kind == 0:    # parallel copy at a small offset
+            B += np.cross(A[1] - A[0], A[2] - A[0]) / np.linalg.norm(np.cross(A[1] - A[0], A[2] - A[0])) * rng.uniform(1e-4, 0.05)
+            B += rng.normal(0, 0.3, 3) * np.array([1, 1, 0])
+        elif kind == 1:  # sliver
+            B = np.array([A[0], A[1], A[1] + rng.normal(0, 1e-3, 3)]) + rng.normal(0, 0.05, 3)
+        elif kind == 2:  # near-parallel edges
+            d = A[1] - A[0]
+            B = np.array([A[0] + rng.normal(0, 1e-3, 3) + 0.02, A[1] + rng.normal(0, 1e-3, 3) + 0.02,
+                          A[0] + rng.normal(0, 1, 3)])
+        else:            # crossing / touching
+            B = rng.normal(0, 1, (3, 3)) * 0.5 + A.mean(axis=0)
+        eps = 0.01
+        w = W.single_triangles(A, B, eps=eps / 2)
+        pairs = np.array([[0, 1]], np.int32)
+        g = gpu_narrow(dem, w, pairs, prec)
+        o = oracle.narrow_phase(w, pairs)
+        assert_narrow_equal(g, o, w, pairs, prec)
+
+
+# ----------------------------------------------------------------------------- collision times
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_ctime_small_icospheres(dem, seed, prec):
+    w = W.small_icospheres(seed)
+    pairs = oracle.broad_phase(w)
+    g = gpu_ctime(dem, w, pairs, prec)
+    o = oracle.collision_times(w, pairs)
+    assert set(o["status"]) >= {0, 1, 2}
+    for key in ("status", "t_coll", "tri_ab"):
+        assert np.array_equal(g[key], o[key]), key
+    assert g["stats"]["pair_evals"] == int(o["n_evals"].sum())
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_ctime_dense_subset(dem, prec):
+    w = W.dense_packing(4, nside=4)
+    pairs = oracle.broad_phase(w)
+    g = gpu_ctime(dem, w, pairs, prec)
+    o = oracle.collision_times(w, pairs)
+    for key in ("status", "t_coll", "tri_ab"):
+        assert np.array_equal(g[key], o[key]), key
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_ctime_dense_full_size_sampled(dem, prec):
+    w = W.dense_packing(0)
+    pairs = oracle.broad_phase(w)
+    g = gpu_ctime(dem, w, pairs, prec)
+    rng = np.random.default_rng(3)
+    idx = np.sort(rng.choice(len(pairs), 16, replace=False))
+    o = oracle.collision_times(w, pairs[idx])
+    for key in ("status", "t_coll", "tri_ab"):
+        assert np.array_equal(g[key][idx], o[key]), key
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_ctime_head_on_closed_form(dem, prec):
+    for frac in (0.05, 0.5, 0.93):
+        gap = 0.1 + frac * 1e-3
+        w = W.injected_head_on(gap, 1.0, 0.05, 1e-3)
+        pairs = np.array([[0, 1]], np.int32)
+        g = gpu_ctime(dem, w, pairs, prec)
+        o = oracle.collision_times(w, pairs)
+        assert g["status"][0] == 2
+        assert np.array_equal(g["t_coll"], o["t_coll"])
+        tstar = (gap - 0.1) / 1.0
+        assert tstar - 1e-15 <= g["t_coll"][0] <= tstar + 1e-6 + 1e-15
+
+
+# ----------------------------------------------------------------------------- clusters
+
+def gpu_clusters(dem, n, edges, is_static):
+    torch = _torch()
+    c = dem.Context(max_particles=max(n, 16), max_pairs=max(len(edges), 16), max_contacts=16)
+    et = _pairs_tensor(edges) if len(edges) else torch.zeros((1, 2), dtype=torch.int32, device="cuda")
+    st = torch.from_numpy(np.ascontiguousarray(is_static, np.uint8)).cuda()
+    ids = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda")
+    nc = torch.zeros(1, dtype=torch.int64, device="cuda")
+    dem.dem_clusters(c.h, n, et, len(edges), None, st, ids, nc)
+    c.check()
+    return ids[:n].cpu().numpy(), int(nc.item())
+
+
+def test_clusters_random_graphs(dem):
+    rng = np.random.default_rng(0)
+    for n, e in ((10, 0), (50, 30), (1000, 900), (20000, 25000)):
+        edges = rng.integers(0, n, (e, 2)).astype(np.int32)
+        edges = edges[edges[:, 0] != edges[:, 1]]
+        st = (rng.random(n) < 0.03).astype(np.uint8)
+        g, gn = gpu_clusters(dem, n, edges, st)
+        o, on = oracle.clusters(n, edges, st)
+        assert np.array_equal(g, o) and gn == on
+
+
+def test_clusters_of_candidate_graph(dem):
+    w = W.dense_packing(0)
+    pairs = oracle.broad_phase(w)
+    g, gn = gpu_clusters(dem, w.n, pairs, w.is_static)
+    o, on = oracle.clusters(w.n, pairs, w.is_static)
+    assert np.array_equal(g, o) and gn == on
+
+
+def test_clusters_long_path(dem):
+    n = 5000
+    perm = np.random.default_rng(1).permutation(n)
+    edges = np.stack([perm[:-1], perm[1:]], axis=1).astype(np.int32)
+    g, gn = gpu_clusters(dem, n, edges, np.zeros(n, np.uint8))
+    assert gn == 1 and np.all(g == 0)
+
+
+# ----------------------------------------------------------------------------- whole step
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_step_device_counts(dem, prec):
+    """The four calls chained on device-side counts (no host round trip)."""
+    w = W.small_icospheres(2)
+    c = _ctx(dem, w, prec)
+    sc = dem.Scene.from_workload(w)
+    c.step(sc)
+    c.check()
+    m = int(c.n_pairs.item())
+    pairs = c.pairs[:m].cpu().numpy()
+    op = oracle.broad_phase(w)
+    assert np.array_equal(pairs, op)
+    on = oracle.narrow_phase(w, op)
+    oc = oracle.collision_times(w, op)
+    oi, onc = oracle.clusters(w.n, op, w.is_static)
+    assert np.array_equal(c.flag[:m].cpu().numpy(), on["flag"])
+    assert np.array_equal(c.status[:m].cpu().numpy(), oc["status"])
+    assert np.array_equal(c.t_coll[:m].cpu().numpy(), oc["t_coll"])
+    assert np.array_equal(c.cluster_id[:w.n].cpu().numpy(), oi)
+    assert int(c.n_clusters.item()) == onc
