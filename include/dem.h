@@ -138,7 +138,8 @@ typedef struct {
   int64_t bisect_steps;     /* bisection steps */
   int64_t contacts;         /* contacts found */
   int64_t pairs_done;       /* pairs processed */
-  int64_t reserved[7];
+  int64_t kernel_launches;  /* kernels launched by this context (host-side count) */
+  int64_t reserved[6];
 } dem_stats;
 
 /* Create a context: validates and copies *cfg, allocates scratch for the

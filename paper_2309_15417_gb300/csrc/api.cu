@@ -203,9 +203,11 @@ dem_status dem_get_stats(dem_ctx *c, dem_stats *out, int reset) {
   std::memset(out, 0, sizeof(*out));
   int64_t *o = reinterpret_cast<int64_t *>(out);
   for (int q = 0; q < dem::ST_N && q < (int)(sizeof(dem_stats) / sizeof(int64_t)); ++q) o[q] = (int64_t)v[q];
+  out->kernel_launches = c->S.launches;
   if (reset) {
     e = cudaMemset(c->S.stats, 0, sizeof(v));
     if (e != cudaSuccess) return cuda_fail(c, e, "get_stats: reset");
+    c->S.launches = 0;
   }
   return DEM_OK;
 }

@@ -152,13 +152,14 @@ cudaError_t launch_broad(const dem_particles &P, int32_t *pairs, int64_t cap, in
   if ((e = cudaMemsetAsync(S.bucket_cur, 0, sizeof(int32_t) * S.table_size, s)) != cudaSuccess) return e;
   k_prep<<<grid, tb, 0, s>>>(n, P.state, S.sph, S.rho_max);
   k_count<<<grid, tb, 0, s>>>(n, S.sph, S.rho_max, mask, S.cell, S.bucket_cnt);
-  scan_exclusive_i32_to_i64(S.bucket_cnt, S.bucket_start, S.table_size, S.scan_part, s);
+  S.launches += 2 + scan_exclusive_i32_to_i64(S.bucket_cnt, S.bucket_start, S.table_size, S.scan_part, s);
   k_scatter<<<grid, tb, 0, s>>>(n, S.cell, S.bucket_start, S.bucket_cur, S.bucket_ids);
   k_pairs<false><<<grid, tb, 0, s>>>(n, S.sph, S.cell, P.is_static, S.bucket_cnt, S.bucket_start, S.bucket_ids,
                                      mask, S.pcnt, nullptr, nullptr, 0, nullptr, S.err);
-  scan_exclusive_i64(S.pcnt, S.poff, n, n_pairs, S.scan_part, s);
+  S.launches += 2 + scan_exclusive_i64(S.pcnt, S.poff, n, n_pairs, S.scan_part, s);
   k_pairs<true><<<grid, tb, 0, s>>>(n, S.sph, S.cell, P.is_static, S.bucket_cnt, S.bucket_start, S.bucket_ids,
                                     mask, nullptr, S.poff, pairs, cap, n_pairs, S.err);
+  S.launches += 1;
   return cudaGetLastError();
 }
 

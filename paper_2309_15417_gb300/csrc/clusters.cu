@@ -96,7 +96,9 @@ cudaError_t launch_clusters(int64_t n, const int32_t *edges, int64_t max_edges, 
   if (max_edges > 0) {
     const unsigned ge = (unsigned)((max_edges + tb - 1) / tb);
     k_cc_hook<<<ge, tb, 0, s>>>(n, edges, max_edges, n_edges, id, S.err);
+    S.launches += 1;
   }
+  S.launches += 3;
   k_cc_final<<<g, tb, 0, s>>>(n, id, reinterpret_cast<unsigned long long *>(n_clusters));
   k_cc_flatten<<<g, tb, 0, s>>>(n, id);
   return cudaGetLastError();

@@ -33,6 +33,7 @@ struct __align__(32) Sphere4 {
 };
 
 struct Scratch {
+  int64_t launches = 0;           // host-side count of kernel launches issued
   // common
   uint32_t *err;                  // [1]
   unsigned long long *stats;      // [ST_N]
@@ -69,10 +70,11 @@ constexpr int64_t SCAN_PART_CAP = 4096;        // partial sums (=> up to 8M elem
 
 // exclusive scan of n int64 values (in may alias out); total written to
 // *total if non-null.  Grid-wide, no inter-block waits.
-void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total,
-                        int64_t *part, cudaStream_t s);
-void scan_exclusive_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *part,
-                               cudaStream_t s);
+// return the number of kernels launched
+int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total,
+                       int64_t *part, cudaStream_t s);
+int scan_exclusive_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *part,
+                              cudaStream_t s);
 
 // launchers
 cudaError_t launch_broad(const dem_particles &P, int32_t *pairs, int64_t cap, int64_t *n_pairs,

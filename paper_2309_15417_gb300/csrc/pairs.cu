@@ -1029,13 +1029,17 @@ __global__ void contact_total(const int64_t *total, const unsigned long long *st
 template <int PREC, int MODE>
 cudaError_t launch_pairs(const PairArgs &a, int num_sms, cudaStream_t s) {
   const size_t smem = sizeof(Smem<PREC>);
-  cudaError_t e = cudaFuncSetAttribute(pair_kernel<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_kernel<PREC, MODE>, NT, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
+  // attribute and occupancy once per process (kept out of graph captures)
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(pair_kernel<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int q = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, pair_kernel<PREC, MODE>, NT, smem);
+    if (e != cudaSuccess) return e;
+    per_sm = q < 1 ? 1 : q;
+  }
   int64_t grid = (int64_t)num_sms * per_sm;
   if (a.max_pairs < grid) grid = a.max_pairs > 0 ? a.max_pairs : 1;
   pair_kernel<PREC, MODE><<<(unsigned)grid, NT, smem, s>>>(a);
@@ -1085,11 +1089,12 @@ cudaError_t launch_narrow(int prec, const dem_particles &P, const int32_t *pairs
     if ((e = cudaMemsetAsync(S.pcur, 0, sizeof(int32_t) * max_pairs, s)) != cudaSuccess) return e;
     e = prec == 0 ? launch_pairs<0, MODE_NARROW>(a, num_sms, s) : launch_pairs<1, MODE_NARROW>(a, num_sms, s);
     if (e != cudaSuccess) return e;
+    S.launches += 1;
   }
   // per-pair offsets, scatter, sort
   int64_t *total = S.tmp;
   if (max_pairs > 0) {
-    scan_exclusive_i64(S.pc, S.po, max_pairs, total, S.scan_part, s);
+    S.launches += scan_exclusive_i64(S.pc, S.po, max_pairs, total, S.scan_part, s);
   } else {
     if ((e = cudaMemsetAsync(total, 0, sizeof(int64_t), s)) != cudaSuccess) return e;
   }
@@ -1102,8 +1107,10 @@ cudaError_t launch_narrow(int prec, const dem_particles &P, const int32_t *pairs
                                              out.contacts, out.contact_geom,
                                              out.contact_cap < S.cap_contacts ? out.contact_cap : S.cap_contacts,
                                              S.err);
+    S.launches += 2;
   }
   contact_total<<<1, 1, 0, s>>>(total, S.st_count, S.cap_contacts, out.n_contacts, S.err);
+  S.launches += 1;
   return cudaGetLastError();
 }
 
@@ -1119,6 +1126,7 @@ cudaError_t launch_ctime(int prec, const dem_particles &P, const int32_t *pairs,
   cudaError_t e;
   if ((e = cudaMemsetAsync(S.work, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
   if (max_pairs <= 0) return cudaSuccess;
+  S.launches += 1;
   return prec == 0 ? launch_pairs<0, MODE_CTIME>(a, num_sms, s) : launch_pairs<1, MODE_CTIME>(a, num_sms, s);
 }
 

@@ -108,26 +108,27 @@ __global__ void __launch_bounds__(ST) k_apply(const TI *in, int64_t *out, int64_
 }
 
 template <class TI>
-void scan_impl(const TI *in, int64_t *out, int64_t n, int64_t *total, int64_t *part, cudaStream_t s) {
+int scan_impl(const TI *in, int64_t *out, int64_t n, int64_t *total, int64_t *part, cudaStream_t s) {
   if (n <= 0) {
     if (total) cudaMemsetAsync(total, 0, sizeof(int64_t), s);
-    return;
+    return 0;
   }
   const int64_t nb = (n + SCAN_BLOCK - 1) / SCAN_BLOCK;  // callers keep nb <= SCAN_PART_CAP
   k_block_sums<TI><<<(unsigned)nb, ST, 0, s>>>(in, n, part);
   k_scan_parts<<<1, 1024, 0, s>>>(part, nb, total);
   k_apply<TI><<<(unsigned)nb, ST, 0, s>>>(in, out, n, part);
+  return 3;
 }
 
 }  // namespace
 
-void scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total, int64_t *part,
-                        cudaStream_t s) {
-  scan_impl<int64_t>(in, out, n, total, part, s);
+int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *total, int64_t *part,
+                       cudaStream_t s) {
+  return scan_impl<int64_t>(in, out, n, total, part, s);
 }
 
-void scan_exclusive_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *part, cudaStream_t s) {
-  scan_impl<int32_t>(in, out, n, nullptr, part, s);
+int scan_exclusive_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *part, cudaStream_t s) {
+  return scan_impl<int32_t>(in, out, n, nullptr, part, s);
 }
 
 }  // namespace dem
