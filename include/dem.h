@@ -204,6 +204,25 @@ dem_status dem_clusters(dem_ctx *ctx, int64_t n, const int32_t *edges, int64_t m
                         const int64_t *n_edges, const uint8_t *is_static, int32_t *cluster_id,
                         int64_t *n_clusters, void *stream);
 
+/* Candidate pairs without any device allocation (no context needed).  The
+ * paper has no counterpart: this is for callers that cannot allocate device
+ * memory when they need candidates -- e.g. an application whose device memory
+ * pool belongs to another framework, or a real-time loop in which an
+ * allocation could block or fail.  Same predicate, output and order as
+ * dem_build_candidates.  Scratch lives in a fixed device array inside the
+ * library, sized for at most DEM_NOALLOC_MAX_PARTICLES particles (about
+ * 1.7 MB, held on every GPU that loads the library until the process exits);
+ * larger inputs return DEM_ERR_CAPACITY without launching anything.  No
+ * cudaMalloc / cudaFree is called.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device
+ * current): make that first call before any stream capture.  All calls share
+ * the array and it keeps the last call's contents; each call clears what must
+ * start at zero, and calls that overlap on the GPU race, so serialise them.
+ * Capacity overflow shows as *n_pairs > cap (only cap pairs are written). */
+#define DEM_NOALLOC_MAX_PARTICLES 16384
+dem_status dem_build_candidates_noalloc(const dem_particles *P, int32_t *pairs, int64_t cap,
+                                        int64_t *n_pairs, void *stream);
+
 /* Synchronise `stream`, return (and clear) the sticky device error as a
  * status (DEM_OK if none). */
 dem_status dem_check(dem_ctx *ctx, void *stream);

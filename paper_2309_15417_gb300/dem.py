@@ -30,7 +30,8 @@ STATUS = {0: "DEM_OK", -1: "DEM_ERR_ARG", -2: "DEM_ERR_CAPACITY", -3: "DEM_ERR_C
 
 # every symbol include/dem.h declares
 EXPORTS = ["dem_create", "dem_destroy", "dem_last_error", "dem_build_candidates", "dem_narrow_phase",
-           "dem_collision_times", "dem_clusters", "dem_check", "dem_get_stats"]
+           "dem_collision_times", "dem_clusters", "dem_check", "dem_get_stats", "dem_build_candidates_noalloc"]
+DEM_NOALLOC_MAX_PARTICLES = 16384
 
 
 class DemError(RuntimeError):
@@ -103,6 +104,8 @@ def load(build_if_needed: bool = True):
         L.dem_check.restype = C.c_int
         L.dem_get_stats.argtypes = [vp, C.POINTER(dem_stats), C.c_int]
         L.dem_get_stats.restype = C.c_int
+        L.dem_build_candidates_noalloc.argtypes = [C.POINTER(dem_particles), vp, i64, vp, vp]
+        L.dem_build_candidates_noalloc.restype = C.c_int
         _lib = L
         return L
 
@@ -170,6 +173,13 @@ def dem_collision_times(ctx, P: dem_particles, pairs, max_pairs: int, n_pairs, t
 def dem_clusters(ctx, n: int, edges, max_edges: int, n_edges, is_static, cluster_id, n_clusters, stream=None):
     _check(ctx, load().dem_clusters(ctx, int(n), _ptr(edges), int(max_edges), _ptr(n_edges), _ptr(is_static),
                                     _ptr(cluster_id), _ptr(n_clusters), _stream(stream)))
+
+
+def dem_build_candidates_noalloc(P: dem_particles, pairs, cap: int, n_pairs, stream=None) -> int:
+    """Candidate pairs with the library's fixed scratch (no device allocation;
+    for callers that cannot allocate).  Returns the C status code."""
+    return int(load().dem_build_candidates_noalloc(C.byref(P), _ptr(pairs), int(cap), _ptr(n_pairs),
+                                                   _stream(stream)))
 
 
 def dem_check(ctx, stream=None):
