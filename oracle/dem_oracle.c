@@ -54,8 +54,9 @@ static void st(double *p, vec3 v) { p[0] = v.x; p[1] = v.y; p[2] = v.z; }
  *   dq = (cos(phi), sin(phi)/phi * (h/2) * w),  phi = |w| h / 2.
  *
  * cos(phi) and sin(phi)/phi are evaluated from their Taylor series in
- * z = phi^2 = |w|^2 h^2 / 4 (Horner form, 10 terms, exact integer
- * denominators (2k-1)2k and 2k(2k+1)); no square root, no library
+ * z = phi^2 = |w|^2 h^2 / 4 (Horner form, 10 terms; the factors are the
+ * binary64 reciprocals 1/((2k-1)2k) and 1/(2k(2k+1)), each the correctly
+ * rounded quotient of 1 by an exact integer); no square root, no library
  * trigonometry.  Truncation error < 1e-17 for phi <= 1.5. */
 #define POSE_TERMS 10
 
@@ -67,8 +68,10 @@ void demo_pose(const double *state, int64_t n, int64_t p, double t, double R[9],
   double z = (w2 * (h * h)) * 0.25;
   double c = 1.0, sn = 1.0;
   for (int k = POSE_TERMS; k >= 1; --k) {
-    c = 1.0 - (z / (double)((2 * k - 1) * (2 * k))) * c;
-    sn = 1.0 - (z / (double)((2 * k) * (2 * k + 1))) * sn;
+    const double rc = 1.0 / (double)((2 * k - 1) * (2 * k));
+    const double rs = 1.0 / (double)((2 * k) * (2 * k + 1));
+    c = 1.0 - (z * rc) * c;
+    sn = 1.0 - (z * rs) * sn;
   }
   double g = (h * 0.5) * sn;
   /* dq = (c, g w) */

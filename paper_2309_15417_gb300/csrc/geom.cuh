@@ -240,14 +240,23 @@ struct Geo {
 // (paper Section 2.1).  h = t - t_cur, X = x + v h, q(t) = dq (x) q0 with
 // dq = (cos phi, (sin phi / phi) (h/2) w), phi = |w| h / 2.  cos phi and
 // sin phi / phi come from their Taylor series in z = phi^2 = (|w|^2 h^2) / 4,
-// Horner form with 10 terms and exact integer denominators (2k-1)2k and
-// 2k(2k+1), k = 10..1 (no square root, no library trigonometry; truncation
-// error below 1e-17 for phi <= 1.5).  R is the rotation matrix of q(t),
+// Horner form with 10 terms, k = 10..1, factors rc[k] = 1/((2k-1)2k) and
+// rs[k] = 1/(2k(2k+1)), each the correctly rounded binary64 quotient (see
+// pose_reciprocals); no square root, no library trigonometry; truncation
+// error below 1e-17 for phi <= 1.5.  R is the rotation matrix of q(t),
 // row-major.
 constexpr int POSE_TERMS = 10;
 
+// rc[k], rs[k] for k = 1..POSE_TERMS (index 0 unused)
+__device__ __forceinline__ void pose_reciprocals(double *rc, double *rs) {
+  for (int k = 1; k <= POSE_TERMS; ++k) {
+    rc[k] = OpsD::div(1.0, (double)((2 * k - 1) * (2 * k)));
+    rs[k] = OpsD::div(1.0, (double)((2 * k) * (2 * k + 1)));
+  }
+}
+
 __device__ __forceinline__ void pose_exact(const double *st, int64_t n, int64_t p, double t,
-                                           double R[9], double X[3]) {
+                                           const double *rc, const double *rs, double R[9], double X[3]) {
   using O = OpsD;
   const double h = O::sub(t, st[13 * n + p]);
   const double wx = st[10 * n + p], wy = st[11 * n + p], wz = st[12 * n + p];
@@ -256,8 +265,8 @@ __device__ __forceinline__ void pose_exact(const double *st, int64_t n, int64_t 
   double c = 1.0, sn = 1.0;
 #pragma unroll
   for (int k = POSE_TERMS; k >= 1; --k) {
-    c = O::sub(1.0, O::mul(O::div(z, (double)((2 * k - 1) * (2 * k))), c));
-    sn = O::sub(1.0, O::mul(O::div(z, (double)((2 * k) * (2 * k + 1))), sn));
+    c = O::sub(1.0, O::mul(O::mul(z, rc[k]), c));
+    sn = O::sub(1.0, O::mul(O::mul(z, rs[k]), sn));
   }
   const double g = O::mul(O::mul(h, 0.5), sn);
   const double pw = c, px = O::mul(g, wx), py = O::mul(g, wy), pz = O::mul(g, wz);

@@ -39,11 +39,14 @@ namespace {
 constexpr int NT = 256;
 constexpr int NW = NT / 32;
 constexpr int G = 32;        // triangles per group
+constexpr int H = 8;         // triangles per subgroup
 constexpr int WCAP = 256;    // per-warp candidate list capacity
-// FP32 error bound relative to the pair's coordinate scale (2^-14).  The
-// observed maximum of |d32 - d64| / S over the adversarial and workload cases
-// in the tests is below 2^-20.
-constexpr double ERR_REL32 = 6.103515625e-05;
+constexpr int XQCAP = 64;    // per-warp binary64 queue capacity
+constexpr int ACAP = 512;    // closest-pair candidates per evaluation
+// FP32 error band relative to the pair's coordinate scale S: 2^-17 = 128
+// units of float32 rounding.  The measured maximum of |d32 - d64| / S over
+// the workload and the adversarial cases of the tests is below 2^-22.
+constexpr double ERR_REL32 = 7.62939453125e-06;
 constexpr double ERR_REL64_LB = 9.094947017729282e-13;  // 2^-40: FP64 culling margin
 
 constexpr int MODE_NARROW = 0;
@@ -100,24 +103,31 @@ template <int PREC>
 struct __align__(128) Smem {
   using T = typename Cfg<PREC>::T;
   static constexpr int TT = Cfg<PREC>::TT;
-  static constexpr int NG = TT / G;
-  float4 Ab[3][TT];                 // A tile, body frame (bulk copy target)
-  float4 Bb[3][TT];                 // B tile, body frame (bulk copy target)
+  static constexpr int NG = TT / G;   // groups of 32 triangles
+  static constexpr int NH = TT / H;   // subgroups of 8 triangles
+  float4 Ab[3][TT];                   // A tile, body frame (bulk copy target)
+  float4 Bb[3][TT];                   // B tile, body frame (bulk copy target)
   T Ae[PREC ? 9 : 1][PREC ? TT : 1];  // A tile, evaluation frame (FP64 only)
-  T Be[9][TT];                      // B tile, evaluation frame [slot*3+coord][tri]
-  T SA[4][TT];                      // triangle spheres of A (cx, cy, cz, r)
+  T Be[9][TT];                        // B tile, evaluation frame [slot*3+coord][tri]
+  T SA[4][TT];                        // triangle spheres of A (cx, cy, cz, r)
   T SB[4][TT];
-  T GA[4][NG];                      // group spheres
+  T GA[4][NG];                        // group spheres
   T GB[4][NG];
-  uint32_t gp[NG * NG];             // group pairs passing the group test
-  T gplb[NG * NG];                  // their lower bounds
-  uint32_t wl[NW][WCAP];            // per-warp candidate lists (a << 16 | b)
+  T HA[4][NH];                        // subgroup spheres
+  T HB[4][NH];
+  uint32_t gp[NG * NG];               // group pairs passing the group test
+  float gplb[NG * NG];                // their lower bounds (rounded down)
+  uint32_t wl[NW][WCAP];              // per-warp candidate lists (a << 16 | b)
+  uint32_t xq[NW][XQCAP];             // per-warp binary64 queue (why << 28 | a << 14 | b)
+  unsigned long long ac_key[ACAP];    // closest-pair candidates (global a << 32 | b)
+  float ac_d[ACAP];                   // their FP32 distances
+  double rc[POSE_TERMS + 1], rs[POSE_TERMS + 1];
   double RA[9], XA[3], RB[9], XB[3];
   float Rr[9], tr[3];
   double eps, ts, T_, Ed, Elb;
   int64_t i, j, offA, offB;
-  int nA, nB, ngp, found, resA, resB, frmA, frmB, bad, abort;
-  unsigned long long bound;         // bits of a non-negative double
+  int nA, nB, ngp, found, resA, resB, frmA, frmB, bad, abort, nac;
+  unsigned long long bound;           // bits of a non-negative double
   unsigned long long mbar;
   double red_d[NW];
   unsigned long long red_k[NW];
@@ -181,14 +191,21 @@ __device__ __forceinline__ double warp_min(double v) {
   for (int o = 16; o; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+// min / max over aligned segments of `width` lanes
+template <class T>
+__device__ __forceinline__ T seg_min(T v, int width) {
+  for (int o = width >> 1; o; o >>= 1) {
+    const T u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u < v ? u : v;
+  }
   return v;
 }
-__device__ __forceinline__ double warp_max(double v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+template <class T>
+__device__ __forceinline__ T seg_max(T v, int width) {
+  for (int o = width >> 1; o; o >>= 1) {
+    const T u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
   return v;
 }
 
@@ -198,6 +215,11 @@ __device__ __forceinline__ unsigned long long dbits(double x) {
 __device__ __forceinline__ double bitsd(unsigned long long b) {
   return __longlong_as_double(static_cast<long long>(b));
 }
+// float not above x
+__device__ __forceinline__ float down_f(float x) { return x; }
+__device__ __forceinline__ float down_f(double x) { return __double2float_rd(x); }
+
+constexpr uint32_t WHY_DEC = 1u, WHY_CON = 2u, WHY_ARG = 4u;
 
 // ---------------------------------------------------------------- the CTA
 template <int PREC>
@@ -209,22 +231,27 @@ struct Cta {
   using V = V3<T>;
   static constexpr int TT = Cfg<PREC>::TT;
   static constexpr int NG = TT / G;
+  static constexpr int NH = TT / H;
 
   Smem<PREC> &s;
   const PairArgs &A;
   int tid, w, lane;
   uint32_t phase;
   // per-evaluation warp state
-  T mw;                        // warp minimum of evaluated distances
-  double bd2;                  // lane best exact (d^2, key) and points
+  T mw;                        // warp minimum of the evaluated distances
+  double bd2;                  // lane best exact (d^2, key) and its points
   unsigned long long bkey;
   double bpa[3], bpb[3];
+  double wbd2;                 // warp best (uniform), for pruning candidates
+  unsigned long long wbkey;
+  int qn;                      // entries in this warp's binary64 queue
 
   __device__ Cta(Smem<PREC> &s_, const PairArgs &A_) : s(s_), A(A_) {
     tid = threadIdx.x;
     w = tid >> 5;
     lane = tid & 31;
     phase = 0;
+    qn = 0;
   }
 
   __device__ void stat(int k, unsigned long long v) {
@@ -291,26 +318,37 @@ struct Cta {
       S[3][k] = O::sqrt(r2);
     }
   }
-  // group spheres of n triangles: box centre of the triangle spheres, radius
-  // covering every triangle sphere
-  __device__ void groups(T (*S)[TT], T (*GS)[NG], int n) {
+  // group (32 triangles) and subgroup (8 triangles) spheres: box centre of
+  // the triangle spheres, radius covering every triangle sphere
+  __device__ void groups(T (*S)[TT], T (*GS)[NG], T (*HS)[NH], int n) {
     const int ng = (n + G - 1) / G;
+    const T big = O::inf();
     for (int g = w; g < ng; g += NW) {
       const int k = g * G + lane;
       const bool v = k < n;
-      T cx = v ? S[0][k] : T(0), cy = v ? S[1][k] : T(0), cz = v ? S[2][k] : T(0), r = v ? S[3][k] : T(0);
-      const T big = O::inf();
-      T lox = warp_min(v ? cx - r : big), hix = warp_max(v ? cx + r : -big);
-      T loy = warp_min(v ? cy - r : big), hiy = warp_max(v ? cy + r : -big);
-      T loz = warp_min(v ? cz - r : big), hiz = warp_max(v ? cz + r : -big);
-      T gx = (lox + hix) * T(0.5), gy = (loy + hiy) * T(0.5), gz = (loz + hiz) * T(0.5);
-      T dx = cx - gx, dy = cy - gy, dz = cz - gz;
-      T gr = warp_max(v ? O::sqrt(dx * dx + dy * dy + dz * dz) + r : T(0));
-      if (lane == 0) {
-        GS[0][g] = gx;
-        GS[1][g] = gy;
-        GS[2][g] = gz;
-        GS[3][g] = gr;
+      const T cx = v ? S[0][k] : T(0), cy = v ? S[1][k] : T(0), cz = v ? S[2][k] : T(0), r = v ? S[3][k] : T(0);
+#pragma unroll
+      for (int lvl = 0; lvl < 2; ++lvl) {
+        const int wd = lvl == 0 ? G : H;
+        const T lox = seg_min(v ? cx - r : big, wd), hix = seg_max(v ? cx + r : -big, wd);
+        const T loy = seg_min(v ? cy - r : big, wd), hiy = seg_max(v ? cy + r : -big, wd);
+        const T loz = seg_min(v ? cz - r : big, wd), hiz = seg_max(v ? cz + r : -big, wd);
+        const T gx = (lox + hix) * T(0.5), gy = (loy + hiy) * T(0.5), gz = (loz + hiz) * T(0.5);
+        const T dx = cx - gx, dy = cy - gy, dz = cz - gz;
+        const T gr = seg_max(v ? O::sqrt(dx * dx + dy * dy + dz * dz) + r : T(0), wd);
+        if (lvl == 0 && lane == 0) {
+          GS[0][g] = gx;
+          GS[1][g] = gy;
+          GS[2][g] = gz;
+          GS[3][g] = gr;
+        }
+        if (lvl == 1 && (lane & (H - 1)) == 0) {
+          const int h = g * (G / H) + (lane / H);
+          HS[0][h] = gx;
+          HS[1][h] = gy;
+          HS[2][h] = gz;
+          HS[3][h] = gr;
+        }
       }
     }
   }
@@ -346,15 +384,15 @@ struct Cta {
     if (!doA && !doB) return;
     if constexpr (PREC == 1) {
       if (doA)
-      for (int k = tid; k < na; k += NT)
+        for (int k = tid; k < na; k += NT)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          float4 f = s.Ab[q][k];
-          V3<double> p = to_world_exact(s.RA, s.XA, f.x, f.y, f.z);
-          s.Ae[3 * q][k] = T(p.x);
-          s.Ae[3 * q + 1][k] = T(p.y);
-          s.Ae[3 * q + 2][k] = T(p.z);
-        }
+          for (int q = 0; q < 3; ++q) {
+            float4 f = s.Ab[q][k];
+            V3<double> p = to_world_exact(s.RA, s.XA, f.x, f.y, f.z);
+            s.Ae[3 * q][k] = T(p.x);
+            s.Ae[3 * q + 1][k] = T(p.y);
+            s.Ae[3 * q + 2][k] = T(p.z);
+          }
     }
     if (doB) {
       for (int k = tid; k < nb; k += NT)
@@ -378,8 +416,8 @@ struct Cta {
     if (doA) spheres(s.SA, na, true);
     if (doB) spheres(s.SB, nb, false);
     __syncthreads();
-    if (doA) groups(s.SA, s.GA, na);
-    if (doB) groups(s.SB, s.GB, nb);
+    if (doA) groups(s.SA, s.GA, s.HA, na);
+    if (doB) groups(s.SB, s.GB, s.HB, nb);
     __syncthreads();
     if (tid == 0) {
       s.frmA = ta;
@@ -388,13 +426,27 @@ struct Cta {
   }
 
   // --- exact binary64 triangle pair (world frame, fixed operation order) --
-  __device__ double exact(int a, int b, V3<double> &pa, V3<double> &pb) const {
+  __device__ __noinline__ double exact(int a, int b, V3<double> &pa, V3<double> &pb) const {
     V3<double> X[3], Y[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       float4 f = s.Ab[q][a];
       X[q] = to_world_exact(s.RA, s.XA, f.x, f.y, f.z);
       float4 g = s.Bb[q][b];
+      Y[q] = to_world_exact(s.RB, s.XB, g.x, g.y, g.z);
+    }
+    return GD::tri_dist2(X, Y, pa, pb);
+  }
+
+  // the same, for triangles a, b (indices within the particles) read from
+  // global memory: used when the tiles holding them are no longer resident
+  __device__ __noinline__ double exact_global(int a, int b, V3<double> &pa, V3<double> &pb) const {
+    V3<double> X[3], Y[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float4 f = A.tris[q * A.n_tris + s.offA + a];
+      X[q] = to_world_exact(s.RA, s.XA, f.x, f.y, f.z);
+      const float4 g = A.tris[q * A.n_tris + s.offB + b];
       Y[q] = to_world_exact(s.RB, s.XB, g.x, g.y, g.z);
     }
     return GD::tri_dist2(X, Y, pa, pb);
@@ -408,12 +460,110 @@ struct Cta {
     out[2] = s.RA[6] * x + s.RA[7] * y + s.RA[8] * z + s.XA[2];
   }
 
+  __device__ __forceinline__ unsigned long long key_of(int a, int b, int ta, int tb) const {
+    return (static_cast<unsigned long long>(ta * TT + a) << 32) | static_cast<unsigned>(tb * TT + b);
+  }
+
+  // write a warp's contacts (lanes with con) to the staging area
+  __device__ void put_contacts(bool con, int64_t pk, int ag, int bg, double gd, const double *ga3,
+                               const double *gb3) {
+    const uint32_t m = __ballot_sync(0xffffffffu, con);
+    if (!m) return;
+    unsigned long long base = 0;
+    if (lane == 0) {
+      base = atomicAdd(A.st_count, (unsigned long long)__popc(m));
+      atomicAdd(reinterpret_cast<unsigned long long *>(&A.pc[pk]), (unsigned long long)__popc(m));
+      atomicAdd(&s.cnt[ST_CONTACTS], (unsigned long long)__popc(m));
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (con) {
+      const unsigned long long slot = base + __popc(m & lanemask_lt());
+      if (slot < (unsigned long long)A.st_cap) {
+        A.st_keys[3 * slot] = int32_t(pk);
+        A.st_keys[3 * slot + 1] = ag;
+        A.st_keys[3 * slot + 2] = bg;
+        double *gg = A.st_geom + 7 * slot;
+        gg[0] = gd;
+        gg[1] = ga3[0]; gg[2] = ga3[1]; gg[3] = ga3[2];
+        gg[4] = gb3[0]; gg[5] = gb3[1]; gg[6] = gb3[2];
+      } else {
+        set_err(A.err, ERR_CAPACITY);
+      }
+    }
+  }
+
+  __device__ void update_best(double d2, unsigned long long key, const V3<double> &pa, const V3<double> &pb) {
+    if (d2 < bd2 || (d2 == bd2 && key < bkey)) {
+      bd2 = d2;
+      bkey = key;
+      bpa[0] = pa.x; bpa[1] = pa.y; bpa[2] = pa.z;
+      bpb[0] = pb.x; bpb[1] = pb.y; bpb[2] = pb.z;
+    }
+  }
+
+  // warp-wide best (d^2, key) into the uniform wbd2 / wbkey
+  __device__ void warp_best() {
+    double d = bd2;
+    unsigned long long k = bkey;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const double od = __shfl_xor_sync(0xffffffffu, d, o);
+      const unsigned long long ok = __shfl_xor_sync(0xffffffffu, k, o);
+      if (od < d || (od == d && ok < k)) {
+        d = od;
+        k = ok;
+      }
+    }
+    wbd2 = d;
+    wbkey = k;
+  }
+
+  // --- the warp's binary64 queue: full-lane passes ---------------------------
+  template <bool DECIDE, bool ARGMIN, bool CONTACTS>
+  __device__ void flush_queue(int ta, int tb, int64_t pk) {
+    unsigned long long n64 = 0;
+    for (int q0 = 0; q0 < qn; q0 += 32) {
+      const int k = q0 + lane;
+      const bool have = k < qn;
+      const uint32_t ent = have ? s.xq[w][k] : 0u;
+      const uint32_t why = ent >> 28;
+      const int a = int((ent >> 14) & 0x3fffu), b = int(ent & 0x3fffu);
+      const unsigned long long key = key_of(a, b, ta, tb);
+      // an argmin-only candidate that cannot beat a zero-distance best is skipped
+      const bool skip = why == WHY_ARG && wbd2 == 0.0 && key > wbkey;
+      double e2 = OpsD::inf();
+      V3<double> qa{}, qb{};
+      if (have && !skip) {
+        e2 = exact(a, b, qa, qb);
+        ++n64;
+      }
+      const double de = OpsD::sqrt(e2);
+      if (DECIDE) {
+        const bool yes = have && (why & WHY_DEC) && de <= s.eps;
+        if (__any_sync(0xffffffffu, yes) && lane == 0) s.found = 1;
+      }
+      if (CONTACTS) {
+        const bool con = have && (why & WHY_CON) && de <= s.eps;
+        const double ga3[3] = {qa.x, qa.y, qa.z}, gb3[3] = {qb.x, qb.y, qb.z};
+        put_contacts(con, pk, ta * TT + a, tb * TT + b, de, ga3, gb3);
+      }
+      if (ARGMIN) {
+        if (have && !skip && (why & WHY_ARG)) update_best(e2, key, qa, qb);
+        warp_best();
+      }
+    }
+    qn = 0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) n64 += __shfl_xor_sync(0xffffffffu, n64, o);
+    if (lane == 0) stat(ST_FP64, n64);
+  }
+
   // --- evaluate a warp's candidate list ------------------------------------
   template <bool DECIDE, bool ARGMIN, bool CONTACTS>
   __device__ void warp_eval(int cnt, int ta, int tb, int64_t pk, bool pass1) {
     const T eps = T(s.eps);
     const T Ed = T(s.Ed);
-    unsigned long long n32 = 0, n64 = 0, ncon = 0;
+    unsigned long long n32 = 0;
     for (int e = 0; e < cnt; e += 32) {
       const int k = e + lane;
       const bool have = k < cnt;
@@ -431,8 +581,10 @@ struct Cta {
           if (!(O::sqrt(d2) < eps - Ed)) {
             V x;
             bool hit = false;
-            for (int q = 0; q < 3 && !hit; ++q) hit = GT::seg_tri_cross(X[q], X[q == 2 ? 0 : q + 1], Y[0], Y[1], Y[2], x);
-            for (int q = 0; q < 3 && !hit; ++q) hit = GT::seg_tri_cross(Y[q], Y[q == 2 ? 0 : q + 1], X[0], X[1], X[2], x);
+            for (int q = 0; q < 3 && !hit; ++q)
+              hit = GT::seg_tri_cross(X[q], X[q == 2 ? 0 : q + 1], Y[0], Y[1], Y[2], x);
+            for (int q = 0; q < 3 && !hit; ++q)
+              hit = GT::seg_tri_cross(Y[q], Y[q == 2 ? 0 : q + 1], X[0], X[1], X[2], x);
             if (hit) d2 = T(0);
           }
         } else {
@@ -441,120 +593,116 @@ struct Cta {
         ++n32;
       }
       const T d = O::sqrt(d2);
-      const int ag = ta * TT + a, bg = tb * TT + b;
-      const unsigned long long key = (static_cast<unsigned long long>(ag) << 32) | static_cast<unsigned>(bg);
-      if (DECIDE) {
-        bool yes;
-        if (PREC == 0) {
-          yes = have && d < eps - Ed;
-          const bool band = have && !yes && d <= eps + Ed;
-          if (band) {
-            V3<double> qa, qb;
-            double e2 = exact(a, b, qa, qb);
-            ++n64;
-            yes = OpsD::sqrt(e2) <= s.eps;
-          }
-        } else {
-          yes = have && d <= eps;
+      const unsigned long long key = key_of(a, b, ta, tb);
+      if constexpr (PREC == 0) {
+        uint32_t why = 0;
+        bool yes = false, con = false;
+        if (DECIDE && have) {
+          yes = d < eps - Ed;
+          if (!yes && d <= eps + Ed) why |= WHY_DEC;
         }
-        if (__any_sync(0xffffffffu, yes) && lane == 0) s.found = 1;
-      }
-      if (ARGMIN || CONTACTS) {
-        // warp minimum of the FP32 (or FP64) distances seen so far
-        mw = fmin(mw, warp_min(have ? d : O::inf()));
-        bool con = false;
-        double gd = 0.0, ga3[3] = {0, 0, 0}, gb3[3] = {0, 0, 0};
-        if (PREC == 0) {
-          const bool band = CONTACTS && have && d >= eps - Ed && d <= eps + Ed;
-          const bool am = ARGMIN && have && d <= mw + T(2) * Ed;
-          double e2 = 0.0;
-          V3<double> qa{}, qb{};
-          if (band || am) {
-            e2 = exact(a, b, qa, qb);
-            ++n64;
-            if (am && (e2 < bd2 || (e2 == bd2 && key < bkey))) {
-              bd2 = e2;
-              bkey = key;
-              bpa[0] = qa.x; bpa[1] = qa.y; bpa[2] = qa.z;
-              bpb[0] = qb.x; bpb[1] = qb.y; bpb[2] = qb.z;
+        if (CONTACTS && have) {
+          con = d < eps - Ed;
+          if (!con && d <= eps + Ed) why |= WHY_CON;
+        }
+        if (ARGMIN) {
+          mw = fmin(mw, warp_min(have ? d : O::inf()));
+          const bool am = have && d <= mw + T(2) * Ed;
+          const uint32_t mm = __ballot_sync(0xffffffffu, am);
+          if (mm) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&s.nac, __popc(mm));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            const int pos = base + __popc(mm & lanemask_lt());
+            if (base + __popc(mm) <= ACAP) {
+              if (am) {
+                s.ac_key[pos] = key;
+                s.ac_d[pos] = float(d);
+              }
+            } else {
+              // list full: mark the reserved slots empty, recompute through the queue
+              if (am && pos < ACAP) s.ac_key[pos] = ~0ull;
+              if (am) why |= WHY_ARG;
             }
           }
-          if (CONTACTS && have) {
-            if (band) {
-              gd = OpsD::sqrt(e2);
-              con = gd <= s.eps;
-              ga3[0] = qa.x; ga3[1] = qa.y; ga3[2] = qa.z;
-              gb3[0] = qb.x; gb3[1] = qb.y; gb3[2] = qb.z;
-            } else if (d < eps - Ed) {
-              con = true;
-              gd = double(d);
-              world_of_A_frame(pa, ga3);
-              world_of_A_frame(pb, gb3);
-            }
+        }
+        if (DECIDE && __any_sync(0xffffffffu, yes) && lane == 0) s.found = 1;
+        if (CONTACTS) {
+          double ga3[3], gb3[3];
+          if (con) {
+            world_of_A_frame(pa, ga3);
+            world_of_A_frame(pb, gb3);
           }
-        } else {
-          if (ARGMIN && have && (double(d2) < bd2 || (double(d2) == bd2 && key < bkey))) {
-            bd2 = double(d2);
-            bkey = key;
-            bpa[0] = pa.x; bpa[1] = pa.y; bpa[2] = pa.z;
-            bpb[0] = pb.x; bpb[1] = pb.y; bpb[2] = pb.z;
-          }
-          if (CONTACTS && have && d <= eps) {
-            con = true;
-            gd = double(d);
-            ga3[0] = pa.x; ga3[1] = pa.y; ga3[2] = pa.z;
-            gb3[0] = pb.x; gb3[1] = pb.y; gb3[2] = pb.z;
-          }
+          put_contacts(con, pk, ta * TT + a, tb * TT + b, double(d), ga3, gb3);
+        }
+        // queue the binary64 recomputations
+        const uint32_t m = __ballot_sync(0xffffffffu, why != 0);
+        if (m) {
+          if (why) s.xq[w][qn + __popc(m & lanemask_lt())] = (why << 28) | (uint32_t(a) << 14) | uint32_t(b);
+          qn += __popc(m);
+          __syncwarp();
+          if (qn > XQCAP - 32) flush_queue<DECIDE, ARGMIN, CONTACTS>(ta, tb, pk);
+        }
+      } else {
+        if (DECIDE) {
+          const bool yes = have && d <= eps;
+          if (__any_sync(0xffffffffu, yes) && lane == 0) s.found = 1;
+        }
+        if (ARGMIN) {
+          mw = fmin(mw, warp_min(have ? d : O::inf()));
+          if (have) update_best(double(d2), key, V3<double>{pa.x, pa.y, pa.z}, V3<double>{pb.x, pb.y, pb.z});
         }
         if (CONTACTS) {
-          const uint32_t m = __ballot_sync(0xffffffffu, con);
-          if (m) {
-            unsigned long long base = 0;
-            if (lane == 0) {
-              base = atomicAdd(A.st_count, (unsigned long long)__popc(m));
-              atomicAdd(reinterpret_cast<unsigned long long *>(&A.pc[pk]), (unsigned long long)__popc(m));
-            }
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (con) {
-              const unsigned long long slot = base + __popc(m & lanemask_lt());
-              if (slot < (unsigned long long)A.st_cap) {
-                A.st_keys[3 * slot] = int32_t(pk);
-                A.st_keys[3 * slot + 1] = ag;
-                A.st_keys[3 * slot + 2] = bg;
-                double *gg = A.st_geom + 7 * slot;
-                gg[0] = gd;
-                gg[1] = ga3[0]; gg[2] = ga3[1]; gg[3] = ga3[2];
-                gg[4] = gb3[0]; gg[5] = gb3[1]; gg[6] = gb3[2];
-              } else {
-                set_err(A.err, ERR_CAPACITY);
-              }
-            }
-            ncon += __popc(m);
-          }
-        }
-        if (ARGMIN && pass1 && lane == 0) {
-          // tighten the shared bound with this warp's minimum
-          const double nb = double(mw) + 3.0 * s.Ed + s.Elb;
-          atomicMin(&s.bound, dbits(nb));
+          const bool con = have && d <= eps;
+          const double ga3[3] = {pa.x, pa.y, pa.z}, gb3[3] = {pb.x, pb.y, pb.z};
+          put_contacts(con, pk, ta * TT + a, tb * TT + b, double(d), ga3, gb3);
         }
       }
+      if (ARGMIN && pass1 && lane == 0) {
+        // tighten the shared bound with this warp's minimum
+        const double nb = double(mw) + 3.0 * s.Ed + s.Elb;
+        atomicMin(&s.bound, dbits(nb));
+      }
     }
-    // counters (lane sums)
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      n32 += __shfl_xor_sync(0xffffffffu, n32, o);
-      n64 += __shfl_xor_sync(0xffffffffu, n64, o);
+    for (int o = 16; o; o >>= 1) n32 += __shfl_xor_sync(0xffffffffu, n32, o);
+    if (lane == 0) stat(ST_FP32, n32);
+  }
+
+  // block-wide sort of the group-pair list by lower bound (bitonic)
+  __device__ void sort_groups() {
+    const int n = s.ngp;
+    int n2 = 1;
+    while (n2 < n) n2 <<= 1;
+    for (int q = n + tid; q < n2; q += NT) {
+      s.gplb[q] = __int_as_float(0x7f800000);
+      s.gp[q] = 0u;
     }
-    if (lane == 0) {
-      stat(ST_FP32, n32);
-      stat(ST_FP64, n64);
-      stat(ST_CONTACTS, ncon);
-    }
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int q = tid; q < n2; q += NT) {
+          const int l = q ^ j;
+          if (l > q) {
+            const bool up = (q & k) == 0;
+            const float kq = s.gplb[q], kl = s.gplb[l];
+            if ((kq > kl) == up) {
+              s.gplb[q] = kl;
+              s.gplb[l] = kq;
+              const uint32_t t = s.gp[q];
+              s.gp[q] = s.gp[l];
+              s.gp[l] = t;
+            }
+          }
+        }
+        __syncthreads();
+      }
   }
 
   // --- one pass over tile pair (ta, tb) -------------------------------------
   // pass 0: triangle pairs with sphere bound LB <= th0;
-  // pass 1: th0 < LB <= bound (shared, shrinking).
+  // pass 1: th0 < LB <= bound (shared, shrinking), group pairs in order of
+  // their lower bounds.
   template <bool DECIDE, bool ARGMIN, bool CONTACTS>
   __device__ void scan_tiles(int ta, int tb, bool pass1, T th0, int64_t pk) {
     const int na = min(TT, s.nA - ta * TT), nb = min(TT, s.nB - tb * TT);
@@ -562,7 +710,7 @@ struct Cta {
     const T Elb = T(s.Elb);
     if (tid == 0) s.ngp = 0;
     __syncthreads();
-    // group pairs
+    // level 1: group pairs (32 x 32 triangles)
     {
       const T gth = pass1 ? T(bitsd(s.bound)) + Elb : th0 + Elb;
       for (int q = tid; q < nga * ngb; q += NT) {
@@ -572,90 +720,123 @@ struct Cta {
         if (lb <= gth) {
           const int pos = atomicAdd(&s.ngp, 1);
           s.gp[pos] = (uint32_t(ga) << 16) | uint32_t(gb);
-          s.gplb[pos] = lb;
+          s.gplb[pos] = down_f(lb);
         }
       }
       if (tid == 0) stat(ST_GROUP, (unsigned long long)(nga * ngb));
     }
     __syncthreads();
-    // triangle pairs: warp w takes rows w, w+NW, ... of the surviving group pairs
-    const int rows = s.ngp * G;
+    if (pass1) sort_groups();
+    // levels 2 and 3: warp w takes group pairs w, w + NW, ...; inside a group
+    // pair the 16 subgroup pairs (8 x 8 triangles) are tested by lanes 0..15,
+    // then each passing subgroup pair is two rows of 4 x 8 triangle pairs
+    const int ngp = s.ngp;
     int cnt = 0;
-    unsigned long long ntests = 0;
-    for (int idx = w; idx < rows; idx += NW) {
+    unsigned long long ntests = 0, nsub = 0;
+    for (int p = w; p < ngp; p += NW) {
       if (DECIDE) {
-        // one read per warp, broadcast: the exit is warp-uniform
-        int f = lane == 0 ? *(volatile int *)&s.found : 0;
+        const int f = lane == 0 ? *(volatile int *)&s.found : 0;
         if (__shfl_sync(0xffffffffu, f, 0)) break;
       }
-      const int p = idx >> 5, r = idx & 31;
-      const uint32_t gpe = s.gp[p];
-      const int a = int(gpe >> 16) * G + r;
-      if (a >= na) continue;
+      T bnd = T(0);
       if (pass1) {
         unsigned long long bb = lane == 0 ? *(volatile unsigned long long *)&s.bound : 0ull;
         bb = __shfl_sync(0xffffffffu, bb, 0);
-        if (s.gplb[p] > T(bitsd(bb)) + Elb) continue;
+        bnd = T(bitsd(bb));
+        if (double(s.gplb[p]) > double(bnd) + double(Elb)) continue;  // sorted: later ones fail too
       }
-      const int b = int(gpe & 0xffffu) * G + lane;
-      const bool valid = b < nb;
-      const T ax = s.SA[0][a], ay = s.SA[1][a], az = s.SA[2][a], ar = s.SA[3][a];
-      T dx = T(0), dy = T(0), dz = T(0), br = T(0);
-      if (valid) {
-        dx = ax - s.SB[0][b];
-        dy = ay - s.SB[1][b];
-        dz = az - s.SB[2][b];
-        br = s.SB[3][b];
+      const uint32_t gpe = s.gp[p];
+      const int ga = int(gpe >> 16), gb = int(gpe & 0xffffu);
+      // level 2
+      const int ha = ga * (G / H) + ((lane >> 2) & 3), hb = gb * (G / H) + (lane & 3);
+      bool subok = lane < 16 && ha * H < na && hb * H < nb;
+      nsub += __popc(__ballot_sync(0xffffffffu, subok));
+      if (subok) {
+        const T dx = s.HA[0][ha] - s.HB[0][hb], dy = s.HA[1][ha] - s.HB[1][hb], dz = s.HA[2][ha] - s.HB[2][hb];
+        const T lb = O::sqrt(dx * dx + dy * dy + dz * dz) - s.HA[3][ha] - s.HB[3][hb];
+        subok = lb <= (pass1 ? bnd : th0) + Elb;
       }
-      const T d2c = dx * dx + dy * dy + dz * dz;
-      const T t0 = th0 + ar + br;
-      bool cand;
-      if (!pass1) {
-        cand = valid && d2c <= t0 * t0;
-      } else {
-        // every centroid pair bounds the minimum distance from above
-        const T rowmin = warp_min(valid ? d2c : O::inf());
-        if (lane == 0) {
-          const double ub = double(O::sqrt(rowmin)) + 2.0 * s.Elb + 4.0 * s.Ed;
-          atomicMin(&s.bound, dbits(ub));
+      uint32_t m2 = __ballot_sync(0xffffffffu, subok);
+      while (m2) {
+        const int sidx = __ffs(m2) - 1;
+        m2 &= m2 - 1;
+        const int sa = ga * (G / H) + (sidx >> 2), sb = gb * (G / H) + (sidx & 3);
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          const int a = sa * H + h * 4 + (lane >> 3);
+          const int b = sb * H + (lane & 7);
+          const bool valid = a < na && b < nb;
+          T dx = T(0), dy = T(0), dz = T(0), ar = T(0), br = T(0);
+          if (valid) {
+            dx = s.SA[0][a] - s.SB[0][b];
+            dy = s.SA[1][a] - s.SB[1][b];
+            dz = s.SA[2][a] - s.SB[2][b];
+            ar = s.SA[3][a];
+            br = s.SB[3][b];
+          }
+          const T d2c = dx * dx + dy * dy + dz * dz;
+          const T t0 = th0 + ar + br;
+          bool cand;
+          if (!pass1) {
+            cand = valid && d2c <= t0 * t0;
+          } else {
+            // every centroid pair bounds the minimum distance from above
+            const T rowmin = warp_min(valid ? d2c : O::inf());
+            if (lane == 0) {
+              const double ub = double(O::sqrt(rowmin)) + 2.0 * s.Elb + 4.0 * s.Ed;
+              atomicMin(&s.bound, dbits(ub));
+            }
+            __syncwarp();
+            const T bn = T(bitsd(*(volatile unsigned long long *)&s.bound)) + Elb;
+            const T t1 = bn + ar + br;
+            cand = valid && d2c <= t1 * t1 && !(d2c <= t0 * t0);
+          }
+          ntests += __popc(__ballot_sync(0xffffffffu, valid));
+          const uint32_t m = __ballot_sync(0xffffffffu, cand);
+          if (cand) s.wl[w][cnt + __popc(m & lanemask_lt())] = (uint32_t(a) << 16) | uint32_t(b);
+          cnt += __popc(m);
+          __syncwarp();
+          if (cnt > WCAP - 32) {
+            warp_eval<DECIDE, ARGMIN, CONTACTS>(cnt, ta, tb, pk, pass1);
+            cnt = 0;
+            __syncwarp();
+          }
         }
-        __syncwarp();
-        const T bnd = T(bitsd(*(volatile unsigned long long *)&s.bound)) + Elb;
-        const T t1 = bnd + ar + br;
-        cand = valid && d2c <= t1 * t1 && !(d2c <= t0 * t0);
-      }
-      ntests += __popc(__ballot_sync(0xffffffffu, valid));
-      const uint32_t m = __ballot_sync(0xffffffffu, cand);
-      if (cand) s.wl[w][cnt + __popc(m & lanemask_lt())] = (uint32_t(a) << 16) | uint32_t(b);
-      cnt += __popc(m);
-      __syncwarp();
-      if (cnt > WCAP - 32) {
-        warp_eval<DECIDE, ARGMIN, CONTACTS>(cnt, ta, tb, pk, pass1);
-        cnt = 0;
-        __syncwarp();
       }
     }
     if (cnt) warp_eval<DECIDE, ARGMIN, CONTACTS>(cnt, ta, tb, pk, pass1);
-    if (lane == 0) stat(ST_SPHERE, ntests);
+    if (PREC == 0 && qn) flush_queue<DECIDE, ARGMIN, CONTACTS>(ta, tb, pk);
+    if (lane == 0) {
+      stat(ST_SPHERE, ntests);
+      stat(ST_GROUP, nsub);
+    }
     __syncthreads();
   }
 
   // --- pose at t ------------------------------------------------------------
   __device__ void set_time(double t) {
+    // the two binary64 poses by lanes 0 and 1 of one warp (one FP64 pass)
+    if (tid < 2) {
+      const int64_t p = tid == 0 ? s.i : s.j;
+      pose_exact(A.st, A.n, p, t, s.rc, s.rs, tid == 0 ? s.RA : s.RB, tid == 0 ? s.XA : s.XB);
+    }
+    __syncthreads();
     if (tid == 0) {
-      pose_exact(A.st, A.n, s.i, t, s.RA, s.XA);
-      pose_exact(A.st, A.n, s.j, t, s.RB, s.XB);
-      double d[3] = {s.XB[0] - s.XA[0], s.XB[1] - s.XA[1], s.XB[2] - s.XA[2]};
-      double tr[3];
+      // relative pose of B in A's frame in FP32 (its error is inside the band)
+      const float d[3] = {float(s.XB[0] - s.XA[0]), float(s.XB[1] - s.XA[1]), float(s.XB[2] - s.XA[2])};
+      float ra[9], rb[9], tr[3];
+      for (int q = 0; q < 9; ++q) {
+        ra[q] = float(s.RA[q]);
+        rb[q] = float(s.RB[q]);
+      }
       for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c)
-          s.Rr[r * 3 + c] = float(s.RA[r] * s.RB[c] + s.RA[3 + r] * s.RB[3 + c] + s.RA[6 + r] * s.RB[6 + c]);
-        tr[r] = s.RA[r] * d[0] + s.RA[3 + r] * d[1] + s.RA[6 + r] * d[2];
-        s.tr[r] = float(tr[r]);
+        for (int c = 0; c < 3; ++c) s.Rr[r * 3 + c] = ra[r] * rb[c] + ra[3 + r] * rb[3 + c] + ra[6 + r] * rb[6 + c];
+        tr[r] = ra[r] * d[0] + ra[3 + r] * d[1] + ra[6 + r] * d[2];
+        s.tr[r] = tr[r];
       }
       const double ri = A.st[16 * A.n + s.i], rj = A.st[16 * A.n + s.j];
       if (PREC == 0) {
-        const double S = ri + rj + sqrt(tr[0] * tr[0] + tr[1] * tr[1] + tr[2] * tr[2]);
+        const double S = ri + rj + sqrtf(tr[0] * tr[0] + tr[1] * tr[1] + tr[2] * tr[2]);
         s.Ed = S * ERR_REL32;
         s.Elb = s.Ed;
         // FP32 A-frame data stay valid; B moves
@@ -669,6 +850,7 @@ struct Cta {
         s.frmB = -1;
       }
       s.found = 0;
+      s.nac = 0;
       s.bound = dbits(OpsD::inf());
     }
     __syncthreads();
@@ -683,6 +865,9 @@ struct Cta {
     mw = O::inf();
     bd2 = OpsD::inf();
     bkey = ~0ull;
+    wbd2 = OpsD::inf();
+    wbkey = ~0ull;
+    qn = 0;
     bpa[0] = bpa[1] = bpa[2] = 0.0;
     bpb[0] = bpb[1] = bpb[2] = 0.0;
     const int nta = ntiles(s.nA), ntb = ntiles(s.nB);
@@ -710,6 +895,7 @@ struct Cta {
           }
       }
       const double mh2 = block_min(double(mw));
+      if (PREC == 0) argmin_list(mh2);
       reduce_best();
       if (tid == 0) s.mhat = mh2;
       __syncthreads();
@@ -717,6 +903,56 @@ struct Cta {
     const bool f = DECIDE ? (*(volatile int *)&s.found != 0) : false;
     __syncthreads();
     return f;
+  }
+
+  // Closest pair among the collected candidates: those with d32 <= min + 2E,
+  // recomputed in binary64 in (a, b) order by warp 0, 32 at a time; once a
+  // zero distance is found no later (larger) key can win.
+  __device__ void argmin_list(double mh) {
+    const int n = min(s.nac, ACAP);
+    const float thr = float(mh + 2.0 * s.Ed);
+    for (int q = tid; q < n; q += NT)
+      if (s.ac_key[q] != ~0ull && s.ac_d[q] > thr) s.ac_key[q] = ~0ull;
+    int n2 = 1;
+    while (n2 < n) n2 <<= 1;
+    for (int q = n + tid; q < n2; q += NT) s.ac_key[q] = ~0ull;
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int q = tid; q < n2; q += NT) {
+          const int l = q ^ j;
+          if (l > q) {
+            const bool up = (q & k) == 0;
+            const unsigned long long kq = s.ac_key[q], kl = s.ac_key[l];
+            if ((kq > kl) == up) {
+              s.ac_key[q] = kl;
+              s.ac_key[l] = kq;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    if (w == 0) {
+      unsigned long long n64 = 0;
+      warp_best();
+      for (int q0 = 0; q0 < n; q0 += 32) {
+        const unsigned long long key = q0 + lane < n ? s.ac_key[q0 + lane] : ~0ull;
+        const bool go = key != ~0ull && !(wbd2 == 0.0 && key > wbkey);
+        if (!__any_sync(0xffffffffu, go)) break;
+        if (go) {
+          V3<double> qa, qb;
+          const double e2 = exact_global(int(key >> 32), int(key & 0xffffffffu), qa, qb);
+          update_best(e2, key, qa, qb);
+          ++n64;
+        }
+        warp_best();
+        if (wbd2 == 0.0) break;
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) n64 += __shfl_xor_sync(0xffffffffu, n64, o);
+      if (lane == 0) stat(ST_FP64, n64);
+    }
+    __syncthreads();
   }
 
   __device__ double block_min(double v) {
@@ -831,6 +1067,7 @@ __global__ void __launch_bounds__(NT, 2) pair_kernel(PairArgs A) {
   if (c.tid == 0) {
     mbar_init(&s.mbar);
     s.abort = 0;
+    pose_reciprocals(s.rc, s.rs);
   }
   __syncthreads();
   const int64_t m = pair_count(A);

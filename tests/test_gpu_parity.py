@@ -363,3 +363,67 @@ def test_full_step_device_counts(dem, prec):
     assert np.array_equal(c.t_coll[:m].cpu().numpy(), oc["t_coll"])
     assert np.array_equal(c.cluster_id[:w.n].cpu().numpy(), oi)
     assert int(c.n_clusters.item()) == onc
+
+
+def _adversarial_batch(n_pairs, seed):
+    """Many one-triangle particle pairs in near-degenerate configurations,
+    each pair far from the others, with random rigid poses."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(seed)
+    meshes, pos, quat = [], [], []
+    for k in range(n_pairs):
+        scale = 10.0 ** rng.uniform(-2, 1.5)
+        A = rng.normal(0, 1, (3, 3))
+        kind = k % 6
+        if kind == 0:    # parallel copy at a small offset
+            n = np.cross(A[1] - A[0], A[2] - A[0])
+            B = A + n / np.linalg.norm(n) * rng.uniform(1e-6, 0.05) + rng.normal(0, 0.3, 3) * [1, 1, 0]
+        elif kind == 1:  # sliver
+            B = np.array([A[0], A[1], A[1] + rng.normal(0, 1e-4, 3)]) + rng.normal(0, 0.05, 3)
+        elif kind == 2:  # near-parallel edges
+            B = np.array([A[0] + rng.normal(0, 1e-4, 3) + 0.02, A[1] + rng.normal(0, 1e-4, 3) + 0.02,
+                          A[0] + rng.normal(0, 1, 3)])
+        elif kind == 3:  # crossing or touching
+            B = rng.normal(0, 1, (3, 3)) * 0.5 + A.mean(axis=0)
+        elif kind == 4:  # vertex almost on the face
+            c = A.mean(axis=0)
+            n = np.cross(A[1] - A[0], A[2] - A[0])
+            n /= np.linalg.norm(n)
+            B = np.array([c + n * rng.uniform(-1e-5, 1e-5), c + n + rng.normal(0, 0.3, 3),
+                          c + n + rng.normal(0, 0.3, 3)])
+        else:            # generic, near
+            B = rng.normal(0, 1, (3, 3)) + rng.normal(0, 0.5, 3)
+        A, B = A * scale, B * scale
+        q = Rotation.random(random_state=rng).as_quat()  # x y z w
+        far = rng.normal(0, 50.0, 3)
+        for T in (A, B):
+            meshes.append(T.astype(np.float32).reshape(1, 3, 3))
+            pos.append(far)
+            quat.append([q[3], q[0], q[1], q[2]])
+    n = len(meshes)
+    w = W._assemble("adversarial", meshes, list(range(n)), pos, np.zeros((n, 3)), quat, np.zeros((n, 3)),
+                    0.0, 1e-3, 0.0)
+    # halo of each pair near its own distance scale: contact decisions land near the band
+    pairs = np.array([(2 * k, 2 * k + 1) for k in range(n_pairs)], np.int32)
+    return w, pairs
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_fp32_error_band_adversarial(dem, seed):
+    """The raw FP32 pair minimum stays within 1/16 of the FP32 band
+    E = 2^-17 * S (S = R_A + R_B + |x_B - x_A|) of the binary64 value, and every
+    decision still matches binary64."""
+    w, pairs = _adversarial_batch(600, seed)
+    o = oracle.narrow_phase(w, pairs)
+    # halos at a fraction of each pair's distance, so the FP32 band is hit
+    eps = np.zeros(w.n)
+    eps[pairs[:, 0]] = eps[pairs[:, 1]] = 0.5 * o["dmin"] * (1 + np.random.default_rng(seed).normal(0, 1e-7, len(pairs)))
+    w.state[W.F_EPS] = eps
+    o = oracle.narrow_phase(w, pairs)
+    g = gpu_narrow(dem, w, pairs, 0)
+    assert_narrow_equal(g, o, w, pairs, 0)
+    R = w.state[W.F_RADIUS]
+    X = w.state[W.F_X:W.F_Z + 1]
+    S = R[pairs[:, 0]] + R[pairs[:, 1]] + np.linalg.norm(X[:, pairs[:, 1]] - X[:, pairs[:, 0]], axis=0)
+    rel = np.abs(g["dmin32"].astype(np.float64) - o["dmin"]) / S
+    assert rel.max() <= 2.0 ** -21, rel.max()
