@@ -43,6 +43,9 @@ constexpr int H = 8;         // triangles per subgroup
 constexpr int WCAP = 256;    // per-warp candidate list capacity
 constexpr int XQCAP = 64;    // per-warp binary64 queue capacity
 constexpr int ACAP = 512;    // closest-pair candidates per evaluation
+constexpr int WFLUSH = 64;   // a warp evaluates its candidate list at this size
+constexpr int QWARP = 12;    // binary64 queues up to this size run one triangle pair per warp
+constexpr int GRID_MAX = 16; // sample times whose poses are computed up front
 // FP32 error band relative to the pair's coordinate scale S: 2^-17 = 128
 // units of float32 rounding.  The measured maximum of |d32 - d64| / S over
 // the workload and the adversarial cases of the tests is below 2^-22.
@@ -126,7 +129,8 @@ struct __align__(128) Smem {
   float Rr[9], tr[3];
   double eps, ts, T_, Ed, Elb;
   int64_t i, j, offA, offB;
-  int nA, nB, ngp, found, resA, resB, frmA, frmB, bad, abort, nac;
+  int nA, nB, ngp, gpnext, found, resA, resB, frmA, frmB, bad, abort, nac, ngrid;
+  double gR[GRID_MAX][2][9], gX[GRID_MAX][2][3];  // poses at the sample times
   unsigned long long bound;           // bits of a non-negative double
   unsigned long long mbar;
   double red_d[NW];
@@ -452,6 +456,114 @@ struct Cta {
     return GD::tri_dist2(X, Y, pa, pb);
   }
 
+  // The same binary64 triangle distance with one warp per triangle pair.
+  // Lanes 0..5 run the six edge-triangle crossing tests in binary64.  Lanes
+  // 8..13 (vertex-triangle) and 16..24 (edge-edge) first compute their
+  // feature distance in FP32 (A's frame); only features whose FP32 distance
+  // is within 2E of the smallest one are then recomputed in binary64: every
+  // feature that can attain the binary64 minimum is among them, so the
+  // minimum and its first attaining feature (sequential order, strict "<")
+  // are those of Geo<OpsD>::tri_dist2.  a, b index triangles within
+  // particles i, j.  Every lane returns the result.
+  __device__ __noinline__ double exact_warp(int a, int b, V3<double> &pa, V3<double> &pb) const {
+    using GF = Geo<OpsF>;
+    V3<double> v{0.0, 0.0, 0.0};
+    V3<float> vf{0.f, 0.f, 0.f};
+    if (lane < 6) {
+      const int q = lane < 3 ? lane : lane - 3;
+      const float4 f = lane < 3 ? A.tris[q * A.n_tris + s.offA + a] : A.tris[q * A.n_tris + s.offB + b];
+      if (lane < 3) {
+        v = to_world_exact(s.RA, s.XA, f.x, f.y, f.z);
+        vf = V3<float>{f.x, f.y, f.z};
+      } else {
+        v = to_world_exact(s.RB, s.XB, f.x, f.y, f.z);
+        const float *R = s.Rr;
+        vf = V3<float>{fmaf(R[0], f.x, fmaf(R[1], f.y, fmaf(R[2], f.z, s.tr[0]))),
+                       fmaf(R[3], f.x, fmaf(R[4], f.y, fmaf(R[5], f.z, s.tr[1]))),
+                       fmaf(R[6], f.x, fmaf(R[7], f.y, fmaf(R[8], f.z, s.tr[2])))};
+      }
+    }
+    V3<double> X[3], Y[3];
+    V3<float> Xf[3], Yf[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      X[q] = V3<double>{__shfl_sync(0xffffffffu, v.x, q), __shfl_sync(0xffffffffu, v.y, q),
+                        __shfl_sync(0xffffffffu, v.z, q)};
+      Y[q] = V3<double>{__shfl_sync(0xffffffffu, v.x, q + 3), __shfl_sync(0xffffffffu, v.y, q + 3),
+                        __shfl_sync(0xffffffffu, v.z, q + 3)};
+      Xf[q] = V3<float>{__shfl_sync(0xffffffffu, vf.x, q), __shfl_sync(0xffffffffu, vf.y, q),
+                        __shfl_sync(0xffffffffu, vf.z, q)};
+      Yf[q] = V3<float>{__shfl_sync(0xffffffffu, vf.x, q + 3), __shfl_sync(0xffffffffu, vf.y, q + 3),
+                        __shfl_sync(0xffffffffu, vf.z, q + 3)};
+    }
+    const bool fvt = lane >= 8 && lane < 14, fee = lane >= 16 && lane < 25;
+    const int ord = lane < 11 ? lane - 8 : (lane < 14 ? lane - 8 : lane - 10);
+    const int vi = lane < 11 ? lane - 8 : lane - 11;       // vertex index of a VT lane
+    const int ei = (lane - 16) / 3, ej = (lane - 16) % 3;  // edge indices of an EE lane
+    // binary64 crossing tests
+    bool hit = false;
+    V3<double> p1{0.0, 0.0, 0.0}, p2{0.0, 0.0, 0.0};
+    if (lane < 3) {
+      hit = GD::seg_tri_cross(X[lane], X[lane == 2 ? 0 : lane + 1], Y[0], Y[1], Y[2], p1);
+    } else if (lane < 6) {
+      const int j = lane - 3;
+      hit = GD::seg_tri_cross(Y[j], Y[j == 2 ? 0 : j + 1], X[0], X[1], X[2], p1);
+    }
+    // FP32 feature distances
+    float df = OpsF::inf();
+    {
+      V3<float> q1, q2;
+      if (fvt) {
+        df = lane < 11 ? GF::closest_pt_tri(Xf[vi], Yf[0], Yf[1], Yf[2], q1)
+                       : GF::closest_pt_tri(Yf[vi], Xf[0], Xf[1], Xf[2], q1);
+      } else if (fee) {
+        df = GF::seg_seg(Xf[ei], Xf[ei == 2 ? 0 : ei + 1], Yf[ej], Yf[ej == 2 ? 0 : ej + 1], q1, q2);
+      }
+      df = OpsF::sqrt(df);
+    }
+    const uint32_t hm = __ballot_sync(0xffffffffu, hit) & 0x3fu;
+    if (hm) {
+      const int src = __ffs(hm) - 1;
+      pa = V3<double>{__shfl_sync(0xffffffffu, p1.x, src), __shfl_sync(0xffffffffu, p1.y, src),
+                      __shfl_sync(0xffffffffu, p1.z, src)};
+      pb = pa;
+      return 0.0;
+    }
+    const float m32 = warp_min(df);
+    const bool need = (fvt || fee) && df <= m32 + 2.0f * float(s.Ed);
+    double d2 = OpsD::inf();
+    if (need) {
+      if (fvt) {
+        if (lane < 11) {
+          d2 = GD::closest_pt_tri(X[vi], Y[0], Y[1], Y[2], p2);
+          p1 = X[vi];
+        } else {
+          d2 = GD::closest_pt_tri(Y[vi], X[0], X[1], X[2], p1);
+          p2 = Y[vi];
+        }
+      } else {
+        d2 = GD::seg_seg(X[ei], X[ei == 2 ? 0 : ei + 1], Y[ej], Y[ej == 2 ? 0 : ej + 1], p1, p2);
+      }
+    }
+    double bd = d2;
+    int bo = need ? ord : 99;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+      const int oo = __shfl_xor_sync(0xffffffffu, bo, o);
+      if (od < bd || (od == bd && oo < bo)) {
+        bd = od;
+        bo = oo;
+      }
+    }
+    const int src = bo < 3 ? 8 + bo : (bo < 6 ? 11 + (bo - 3) : 16 + (bo - 6));
+    pa = V3<double>{__shfl_sync(0xffffffffu, p1.x, src), __shfl_sync(0xffffffffu, p1.y, src),
+                    __shfl_sync(0xffffffffu, p1.z, src)};
+    pb = V3<double>{__shfl_sync(0xffffffffu, p2.x, src), __shfl_sync(0xffffffffu, p2.y, src),
+                    __shfl_sync(0xffffffffu, p2.z, src)};
+    return bd;
+  }
+
   __device__ void world_of_A_frame(const V &p, double out[3]) const {
     // FP32 points live in A's body frame: x_world = R_A p + X_A
     const double x = p.x, y = p.y, z = p.z;
@@ -522,6 +634,38 @@ struct Cta {
   template <bool DECIDE, bool ARGMIN, bool CONTACTS>
   __device__ void flush_queue(int ta, int tb, int64_t pk) {
     unsigned long long n64 = 0;
+    if (qn <= QWARP) {
+      // few entries: one triangle pair at a time, lanes over its features
+      for (int q = 0; q < qn; ++q) {
+        const uint32_t ent = s.xq[w][q];
+        const uint32_t why = ent >> 28;
+        const int a = int((ent >> 14) & 0x3fffu), b = int(ent & 0x3fffu);
+        const unsigned long long key = key_of(a, b, ta, tb);
+        if (why == WHY_ARG && wbd2 == 0.0 && key > wbkey) continue;
+        if (DECIDE && !ARGMIN && !CONTACTS) {
+          // one read per warp, broadcast: the exit is warp-uniform
+          const int f = lane == 0 ? *(volatile int *)&s.found : 0;
+          if (__shfl_sync(0xffffffffu, f, 0)) break;
+        }
+        V3<double> qa, qb;
+        const double e2 = exact_warp(ta * TT + a, tb * TT + b, qa, qb);
+        ++n64;
+        const double de = OpsD::sqrt(e2);
+        if (DECIDE && (why & WHY_DEC) && de <= s.eps && lane == 0) s.found = 1;
+        if (CONTACTS) {
+          const bool con = lane == 0 && (why & WHY_CON) && de <= s.eps;
+          const double ga3[3] = {qa.x, qa.y, qa.z}, gb3[3] = {qb.x, qb.y, qb.z};
+          put_contacts(con, pk, ta * TT + a, tb * TT + b, de, ga3, gb3);
+        }
+        if (ARGMIN && (why & WHY_ARG)) {
+          update_best(e2, key, qa, qb);
+          warp_best();
+        }
+      }
+      qn = 0;
+      if (lane == 0) stat(ST_FP64, n64);
+      return;
+    }
     for (int q0 = 0; q0 < qn; q0 += 32) {
       const int k = q0 + lane;
       const bool have = k < qn;
@@ -708,7 +852,10 @@ struct Cta {
     const int na = min(TT, s.nA - ta * TT), nb = min(TT, s.nB - tb * TT);
     const int nga = (na + G - 1) / G, ngb = (nb + G - 1) / G;
     const T Elb = T(s.Elb);
-    if (tid == 0) s.ngp = 0;
+    if (tid == 0) {
+      s.ngp = 0;
+      s.gpnext = 0;
+    }
     __syncthreads();
     // level 1: group pairs (32 x 32 triangles)
     {
@@ -733,17 +880,22 @@ struct Cta {
     const int ngp = s.ngp;
     int cnt = 0;
     unsigned long long ntests = 0, nsub = 0;
-    for (int p = w; p < ngp; p += NW) {
-      if (DECIDE) {
-        const int f = lane == 0 ? *(volatile int *)&s.found : 0;
-        if (__shfl_sync(0xffffffffu, f, 0)) break;
+    for (;;) {
+      // group pairs are handed out one at a time (balanced across warps)
+      int p = 0, f = 0;
+      if (lane == 0) {
+        p = atomicAdd(&s.gpnext, 1);
+        if (DECIDE && !ARGMIN) f = *(volatile int *)&s.found;
       }
+      p = __shfl_sync(0xffffffffu, p, 0);
+      f = __shfl_sync(0xffffffffu, f, 0);
+      if (p >= ngp || f) break;
       T bnd = T(0);
       if (pass1) {
         unsigned long long bb = lane == 0 ? *(volatile unsigned long long *)&s.bound : 0ull;
         bb = __shfl_sync(0xffffffffu, bb, 0);
         bnd = T(bitsd(bb));
-        if (double(s.gplb[p]) > double(bnd) + double(Elb)) continue;  // sorted: later ones fail too
+        if (double(s.gplb[p]) > double(bnd) + double(Elb)) break;  // sorted: later ones fail too
       }
       const uint32_t gpe = s.gp[p];
       const int ga = int(gpe >> 16), gb = int(gpe & 0xffffu);
@@ -796,7 +948,7 @@ struct Cta {
           if (cand) s.wl[w][cnt + __popc(m & lanemask_lt())] = (uint32_t(a) << 16) | uint32_t(b);
           cnt += __popc(m);
           __syncwarp();
-          if (cnt > WCAP - 32) {
+          if (cnt >= WFLUSH) {
             warp_eval<DECIDE, ARGMIN, CONTACTS>(cnt, ta, tb, pk, pass1);
             cnt = 0;
             __syncwarp();
@@ -814,9 +966,33 @@ struct Cta {
   }
 
   // --- pose at t ------------------------------------------------------------
-  __device__ void set_time(double t) {
-    // the two binary64 poses by lanes 0 and 1 of one warp (one FP64 pass)
-    if (tid < 2) {
+  // Poses at the pair's sample times t_q = ts + (T q) / K, q = 0..K, all
+  // computed in one parallel pass (lane 2q: particle i, lane 2q+1: j).
+  __device__ void pose_grid(int K) {
+    const int ng = K + 1 <= GRID_MAX ? K + 1 : 0;
+    if (w == 0 && lane < 2 * ng) {
+      using D = OpsD;
+      const int q = lane >> 1, side = lane & 1;
+      const double tq = q == 0 ? s.ts : D::add(s.ts, D::div(D::mul(s.T_, double(q)), double(K)));
+      pose_exact(A.st, A.n, side == 0 ? s.i : s.j, tq, s.rc, s.rs, s.gR[q][side], s.gX[q][side]);
+    }
+    if (tid == 0) s.ngrid = ng;
+    __syncthreads();
+  }
+
+  // pose at t; kidx >= 0: t is sample time kidx of the pose grid
+  __device__ void set_time(double t, int kidx = -1) {
+    if (kidx >= 0 && kidx < s.ngrid) {
+      if (tid < 24) {
+        const int side = tid / 12, e = tid % 12;
+        double *R = side == 0 ? s.RA : s.RB, *X = side == 0 ? s.XA : s.XB;
+        if (e < 9)
+          R[e] = s.gR[kidx][side][e];
+        else
+          X[e - 9] = s.gX[kidx][side][e - 9];
+      }
+    } else if (tid < 2) {
+      // the two binary64 poses by lanes 0 and 1 of one warp (one FP64 pass)
       const int64_t p = tid == 0 ? s.i : s.j;
       pose_exact(A.st, A.n, p, t, s.rc, s.rs, tid == 0 ? s.RA : s.RB, tid == 0 ? s.XA : s.XB);
     }
@@ -859,9 +1035,11 @@ struct Cta {
   // --- one evaluation of the pair at time t ---------------------------------
   // DECIDE: returns whether some triangle pair is within eps (binary64).
   // ARGMIN: leaves the exact closest pair in s.best_*, FP32 minimum in s.mhat.
+  // DECIDE and ARGMIN together: the decision, and the closest pair only when
+  // the decision is true.
   template <bool DECIDE, bool ARGMIN, bool CONTACTS>
-  __device__ bool eval(double t, int64_t pk) {
-    set_time(t);
+  __device__ bool eval(double t, int64_t pk, int kidx = -1) {
+    set_time(t, kidx);
     mw = O::inf();
     bd2 = OpsD::inf();
     bkey = ~0ull;
@@ -878,8 +1056,13 @@ struct Cta {
         if (!load_tiles(ta, tb)) return false;
         frames(ta, tb);
         scan_tiles<DECIDE, ARGMIN, CONTACTS>(ta, tb, false, th0, pk);
-        if (DECIDE && s.found) stop = true;
+        if (DECIDE && !ARGMIN && s.found) stop = true;
       }
+    if (DECIDE && ARGMIN) {
+      const bool f = *(volatile int *)&s.found != 0;
+      __syncthreads();
+      if (!f) return false;
+    }
     if (ARGMIN) {
       // FP32 (FP64) minimum over the evaluated pairs
       const double mh = block_min(double(mw));
@@ -905,53 +1088,78 @@ struct Cta {
     return f;
   }
 
-  // Closest pair among the collected candidates: those with d32 <= min + 2E,
-  // recomputed in binary64 in (a, b) order by warp 0, 32 at a time; once a
-  // zero distance is found no later (larger) key can win.
+  // Closest pair among the collected candidates: those with d32 <= min + 2E
+  // (compacted by warp 0), sorted by (a, b), recomputed in binary64 one
+  // candidate per warp per round; once a round finds a zero distance no later
+  // (larger) key can win.
   __device__ void argmin_list(double mh) {
-    const int n = min(s.nac, ACAP);
+    const int n0 = min(s.nac, ACAP);
     const float thr = float(mh + 2.0 * s.Ed);
-    for (int q = tid; q < n; q += NT)
-      if (s.ac_key[q] != ~0ull && s.ac_d[q] > thr) s.ac_key[q] = ~0ull;
+    if (w == 0) {
+      int m = 0;
+      for (int q0 = 0; q0 < n0; q0 += 32) {
+        const int q = q0 + lane;
+        const unsigned long long key = q < n0 ? s.ac_key[q] : ~0ull;
+        const bool keep = q < n0 && key != ~0ull && s.ac_d[q] <= thr;
+        const uint32_t mk = __ballot_sync(0xffffffffu, keep);
+        __syncwarp();
+        if (keep) s.ac_key[m + __popc(mk & lanemask_lt())] = key;
+        m += __popc(mk);
+        __syncwarp();
+      }
+      if (lane == 0) s.nac = m;
+    }
+    __syncthreads();
+    const int n = s.nac;
     int n2 = 1;
     while (n2 < n) n2 <<= 1;
-    for (int q = n + tid; q < n2; q += NT) s.ac_key[q] = ~0ull;
-    __syncthreads();
-    for (int k = 2; k <= n2; k <<= 1)
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        for (int q = tid; q < n2; q += NT) {
-          const int l = q ^ j;
-          if (l > q) {
-            const bool up = (q & k) == 0;
-            const unsigned long long kq = s.ac_key[q], kl = s.ac_key[l];
-            if ((kq > kl) == up) {
-              s.ac_key[q] = kl;
-              s.ac_key[l] = kq;
+    if (n2 <= 32) {
+      if (w == 0) {
+        // one candidate per lane, bitonic sort in registers
+        unsigned long long key = lane < n ? s.ac_key[lane] : ~0ull;
+        for (int k = 2; k <= 32; k <<= 1)
+          for (int j = k >> 1; j > 0; j >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, key, j);
+            const bool lower = (lane & j) == 0, up = (lane & k) == 0;
+            key = (lower == up) ? (key < o ? key : o) : (key > o ? key : o);
+          }
+        if (lane < n) s.ac_key[lane] = key;
+      }
+      __syncthreads();
+    } else {
+      for (int q = n + tid; q < n2; q += NT) s.ac_key[q] = ~0ull;
+      __syncthreads();
+      for (int k = 2; k <= n2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          for (int q = tid; q < n2; q += NT) {
+            const int l = q ^ j;
+            if (l > q) {
+              const bool up = (q & k) == 0;
+              const unsigned long long kq = s.ac_key[q], kl = s.ac_key[l];
+              if ((kq > kl) == up) {
+                s.ac_key[q] = kl;
+                s.ac_key[l] = kq;
+              }
             }
           }
+          __syncthreads();
         }
-        __syncthreads();
-      }
-    if (w == 0) {
-      unsigned long long n64 = 0;
-      warp_best();
-      for (int q0 = 0; q0 < n; q0 += 32) {
-        const unsigned long long key = q0 + lane < n ? s.ac_key[q0 + lane] : ~0ull;
-        const bool go = key != ~0ull && !(wbd2 == 0.0 && key > wbkey);
-        if (!__any_sync(0xffffffffu, go)) break;
-        if (go) {
-          V3<double> qa, qb;
-          const double e2 = exact_global(int(key >> 32), int(key & 0xffffffffu), qa, qb);
-          update_best(e2, key, qa, qb);
-          ++n64;
-        }
-        warp_best();
-        if (wbd2 == 0.0) break;
-      }
-#pragma unroll
-      for (int o = 16; o; o >>= 1) n64 += __shfl_xor_sync(0xffffffffu, n64, o);
-      if (lane == 0) stat(ST_FP64, n64);
     }
+    unsigned long long n64 = 0;
+    for (int r0 = 0; r0 < n; r0 += NW) {
+      const int q = r0 + w;
+      const unsigned long long key = q < n ? s.ac_key[q] : ~0ull;
+      double e2 = OpsD::inf();
+      if (key != ~0ull) {
+        V3<double> qa, qb;
+        e2 = exact_warp(int(key >> 32), int(key & 0xffffffffu), qa, qb);
+        update_best(e2, key, qa, qb);
+        ++n64;
+      }
+      // stop after a round that found a zero distance
+      if (__syncthreads_or(key != ~0ull && e2 == 0.0)) break;
+    }
+    if (lane == 0) stat(ST_FP64, n64);
     __syncthreads();
   }
 
@@ -1110,9 +1318,9 @@ __global__ void __launch_bounds__(NT, 2) pair_kernel(PairArgs A) {
       int32_t ta = -1, tb = -1;
       if (ok && s.nA > 0 && s.nB > 0) {
         ++evals;
-        if (c.template eval<true, false, false>(ts, k)) {
+        c.pose_grid(A.K);
+        if (c.template eval<true, true, false>(ts, k, 0)) {
           status = 1;
-          c.template eval<false, true, false>(ts, k);
           ta = int32_t(s.best_key >> 32);
           tb = int32_t(s.best_key & 0xffffffffu);
         } else {
@@ -1121,7 +1329,7 @@ __global__ void __launch_bounds__(NT, 2) pair_kernel(PairArgs A) {
           for (int q = 1; q <= A.K; ++q) {
             const double tq = D::add(ts, D::div(D::mul(T, double(q)), double(A.K)));
             ++evals;
-            if (c.template eval<true, false, false>(tq, k)) {
+            if (c.template eval<true, false, false>(tq, k, q)) {
               lo = D::add(ts, D::div(D::mul(T, double(q - 1)), double(A.K)));
               hi = tq;
               fnd = true;
