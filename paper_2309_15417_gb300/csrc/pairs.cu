@@ -36,11 +36,9 @@ namespace dem {
 
 namespace {
 
-constexpr int NT = 256;
-constexpr int NW = NT / 32;
 constexpr int G = 32;        // triangles per group
 constexpr int H = 8;         // triangles per subgroup
-constexpr int WCAP = 256;    // per-warp candidate list capacity
+constexpr int WCAP = 96;     // per-warp candidate list capacity
 constexpr int XQCAP = 64;    // per-warp binary64 queue capacity
 constexpr int ACAP = 512;    // closest-pair candidates per evaluation
 constexpr int WFLUSH = 64;   // a warp evaluates its candidate list at this size
@@ -55,17 +53,25 @@ constexpr double ERR_REL64_LB = 9.094947017729282e-13;  // 2^-40: FP64 culling m
 constexpr int MODE_NARROW = 0;
 constexpr int MODE_CTIME = 1;
 
+constexpr int pow2_at_least(int v) { return v <= 1 ? 1 : 2 * pow2_at_least((v + 1) / 2); }
+
 template <int PREC>
 struct Cfg;
+// FP32: 4 warps per CTA, 4 CTAs per SM (about 52 KB of shared memory each);
+// FP64: 8 warps per CTA, 2 CTAs per SM.  A tile holds 320 triangles.
 template <>
 struct Cfg<0> {
-  static constexpr int TT = 512;
+  static constexpr int TT = 320;
+  static constexpr int NT = 128;
+  static constexpr int MINB = 4;
   using T = float;
   using O = OpsF;
 };
 template <>
 struct Cfg<1> {
-  static constexpr int TT = 256;
+  static constexpr int TT = 320;
+  static constexpr int NT = 256;
+  static constexpr int MINB = 2;
   using T = double;
   using O = OpsD;
 };
@@ -106,10 +112,12 @@ template <int PREC>
 struct __align__(128) Smem {
   using T = typename Cfg<PREC>::T;
   static constexpr int TT = Cfg<PREC>::TT;
+  static constexpr int NT = Cfg<PREC>::NT;
+  static constexpr int NW = NT / 32;
   static constexpr int NG = TT / G;   // groups of 32 triangles
   static constexpr int NH = TT / H;   // subgroups of 8 triangles
+  static constexpr int GPCAP = pow2_at_least(NG * NG);  // the sort pads to a power of two
   float4 Ab[3][TT];                   // A tile, body frame (bulk copy target)
-  float4 Bb[3][TT];                   // B tile, body frame (bulk copy target)
   T Ae[PREC ? 9 : 1][PREC ? TT : 1];  // A tile, evaluation frame (FP64 only)
   T Be[9][TT];                        // B tile, evaluation frame [slot*3+coord][tri]
   T SA[4][TT];                        // triangle spheres of A (cx, cy, cz, r)
@@ -118,8 +126,8 @@ struct __align__(128) Smem {
   T GB[4][NG];
   T HA[4][NH];                        // subgroup spheres
   T HB[4][NH];
-  uint32_t gp[NG * NG];               // group pairs passing the group test
-  float gplb[NG * NG];                // their lower bounds (rounded down)
+  uint32_t gp[GPCAP];                 // group pairs passing the group test
+  float gplb[GPCAP];                  // their lower bounds (rounded down)
   uint32_t wl[NW][WCAP];              // per-warp candidate lists (a << 16 | b)
   uint32_t xq[NW][XQCAP];             // per-warp binary64 queue (why << 28 | a << 14 | b)
   unsigned long long ac_key[ACAP];    // closest-pair candidates (global a << 32 | b)
@@ -130,6 +138,7 @@ struct __align__(128) Smem {
   double eps, ts, T_, Ed, Elb;
   int64_t i, j, offA, offB;
   int nA, nB, ngp, gpnext, found, resA, resB, frmA, frmB, bad, abort, nac, ngrid;
+  int wcnt[NW];
   double gR[GRID_MAX][2][9], gX[GRID_MAX][2][3];  // poses at the sample times
   unsigned long long bound;           // bits of a non-negative double
   unsigned long long mbar;
@@ -234,6 +243,8 @@ struct Cta {
   using GD = Geo<OpsD>;
   using V = V3<T>;
   static constexpr int TT = Cfg<PREC>::TT;
+  static constexpr int NT = Cfg<PREC>::NT;
+  static constexpr int NW = NT / 32;
   static constexpr int NG = TT / G;
   static constexpr int NH = TT / H;
 
@@ -265,26 +276,27 @@ struct Cta {
   __device__ int ntiles(int n) const { return (n + TT - 1) / TT; }
 
   // --- tiles -------------------------------------------------------------
-  // Make body tiles ta of A and tb of B resident; false if a copy timed out.
+  // Make body tile ta of A resident (B is read from global memory when its
+  // frame is built); false if the copy timed out.
   __device__ bool load_tiles(int ta, int tb) {
-    const bool needA = s.resA != ta, needB = s.resB != tb;
-    __syncthreads();  // all reads of the previous tiles are done
-    if (!needA && !needB) return true;
-    const int na = min(TT, s.nA - ta * TT), nb = min(TT, s.nB - tb * TT);
+    const bool needA = s.resA != ta;
+    __syncthreads();  // all reads of the previous tile are done
+    if (tid == 0 && s.resB != tb) {
+      s.resB = tb;
+      s.frmB = -1;
+    }
+    if (!needA) {
+      __syncthreads();
+      return true;
+    }
+    const int na = min(TT, s.nA - ta * TT);
     if (tid == 0) {
       s.resA = ta;
-      s.resB = tb;
-      s.frmA = needA ? -1 : s.frmA;
-      s.frmB = -1;
+      s.frmA = -1;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      uint32_t bytes = (needA ? 3u * 16u * na : 0u) + (needB ? 3u * 16u * nb : 0u);
-      mbar_expect_tx(&s.mbar, bytes);
-      if (needA)
-        for (int sl = 0; sl < 3; ++sl)
-          bulk_g2s(&s.Ab[sl][0], A.tris + sl * A.n_tris + s.offA + (int64_t)ta * TT, 16u * na, &s.mbar);
-      if (needB)
-        for (int sl = 0; sl < 3; ++sl)
-          bulk_g2s(&s.Bb[sl][0], A.tris + sl * A.n_tris + s.offB + (int64_t)tb * TT, 16u * nb, &s.mbar);
+      mbar_expect_tx(&s.mbar, 3u * 16u * na);
+      for (int sl = 0; sl < 3; ++sl)
+        bulk_g2s(&s.Ab[sl][0], A.tris + sl * A.n_tris + s.offA + (int64_t)ta * TT, 16u * na, &s.mbar);
     }
     bool ok = mbar_wait(&s.mbar, phase);
     ok = __syncthreads_and(ok) != 0;
@@ -294,7 +306,7 @@ struct Cta {
         set_err(A.err, ERR_TIMEOUT);
         s.abort = 1;
       }
-      mbar_wait(&s.mbar, phase ^ 1u);  // let the copies in flight land
+      mbar_wait(&s.mbar, phase ^ 1u);  // let the copy in flight land
     }
     __syncthreads();
     return ok;
@@ -402,7 +414,7 @@ struct Cta {
       for (int k = tid; k < nb; k += NT)
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-          float4 f = s.Bb[q][k];
+          const float4 f = A.tris[q * A.n_tris + s.offB + tb * TT + k];
           if constexpr (PREC == 0) {
             const float *R = s.Rr;
             s.Be[3 * q][k] = T(fmaf(R[0], f.x, fmaf(R[1], f.y, fmaf(R[2], f.z, s.tr[0]))));
@@ -430,20 +442,7 @@ struct Cta {
   }
 
   // --- exact binary64 triangle pair (world frame, fixed operation order) --
-  __device__ __noinline__ double exact(int a, int b, V3<double> &pa, V3<double> &pb) const {
-    V3<double> X[3], Y[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      float4 f = s.Ab[q][a];
-      X[q] = to_world_exact(s.RA, s.XA, f.x, f.y, f.z);
-      float4 g = s.Bb[q][b];
-      Y[q] = to_world_exact(s.RB, s.XB, g.x, g.y, g.z);
-    }
-    return GD::tri_dist2(X, Y, pa, pb);
-  }
-
-  // the same, for triangles a, b (indices within the particles) read from
-  // global memory: used when the tiles holding them are no longer resident
+  // triangles a, b (indices within particles i, j), read from global memory
   __device__ __noinline__ double exact_global(int a, int b, V3<double> &pa, V3<double> &pb) const {
     V3<double> X[3], Y[3];
 #pragma unroll
@@ -678,7 +677,7 @@ struct Cta {
       double e2 = OpsD::inf();
       V3<double> qa{}, qb{};
       if (have && !skip) {
-        e2 = exact(a, b, qa, qb);
+        e2 = exact_global(ta * TT + a, tb * TT + b, qa, qb);
         ++n64;
       }
       const double de = OpsD::sqrt(e2);
@@ -704,14 +703,14 @@ struct Cta {
 
   // --- evaluate a warp's candidate list ------------------------------------
   template <bool DECIDE, bool ARGMIN, bool CONTACTS>
-  __device__ void warp_eval(int cnt, int ta, int tb, int64_t pk, bool pass1) {
+  __device__ void warp_eval(const uint32_t *list, int cnt, int ta, int tb, int64_t pk, bool pass1) {
     const T eps = T(s.eps);
     const T Ed = T(s.Ed);
     unsigned long long n32 = 0;
     for (int e = 0; e < cnt; e += 32) {
       const int k = e + lane;
       const bool have = k < cnt;
-      const uint32_t ent = have ? s.wl[w][k] : 0u;
+      const uint32_t ent = have ? list[k] : 0u;
       const int a = int(ent >> 16), b = int(ent & 0xffffu);
       T d2 = O::inf();
       V pa{}, pb{};
@@ -949,14 +948,40 @@ struct Cta {
           cnt += __popc(m);
           __syncwarp();
           if (cnt >= WFLUSH) {
-            warp_eval<DECIDE, ARGMIN, CONTACTS>(cnt, ta, tb, pk, pass1);
+            warp_eval<DECIDE, ARGMIN, CONTACTS>(s.wl[w], cnt, ta, tb, pk, pass1);
             cnt = 0;
             __syncwarp();
           }
         }
       }
     }
-    if (cnt) warp_eval<DECIDE, ARGMIN, CONTACTS>(cnt, ta, tb, pk, pass1);
+    // the leftover lists of all warps, evaluated together in rounds of 32
+    {
+      uint32_t e0 = lane < cnt ? s.wl[w][lane] : 0u;
+      uint32_t e1 = lane + 32 < cnt ? s.wl[w][lane + 32] : 0u;
+      uint32_t e2 = lane + 64 < cnt ? s.wl[w][lane + 64] : 0u;
+      if (lane == 0) s.wcnt[w] = cnt;
+      __syncthreads();
+      int start = 0, tot = 0;
+#pragma unroll
+      for (int q = 0; q < NW; ++q) {
+        start = q == w ? tot : start;
+        tot += s.wcnt[q];
+      }
+      uint32_t *flat = &s.wl[0][0];
+      __syncthreads();
+      if (lane < cnt) flat[start + lane] = e0;
+      if (lane + 32 < cnt) flat[start + lane + 32] = e1;
+      if (lane + 64 < cnt) flat[start + lane + 64] = e2;
+      __syncthreads();
+      for (int r = w; r * 32 < tot; r += NW) {
+        if (DECIDE && !ARGMIN) {
+          const int f = lane == 0 ? *(volatile int *)&s.found : 0;
+          if (__shfl_sync(0xffffffffu, f, 0)) break;
+        }
+        warp_eval<DECIDE, ARGMIN, CONTACTS>(flat + r * 32, min(32, tot - r * 32), ta, tb, pk, pass1);
+      }
+    }
     if (PREC == 0 && qn) flush_queue<DECIDE, ARGMIN, CONTACTS>(ta, tb, pk);
     if (lane == 0) {
       stat(ST_SPHERE, ntests);
@@ -1267,7 +1292,7 @@ __device__ __forceinline__ int64_t pair_count(const PairArgs &A) {
 }
 
 template <int PREC, int MODE>
-__global__ void __launch_bounds__(NT, 2) pair_kernel(PairArgs A) {
+__global__ void __launch_bounds__(Cfg<PREC>::NT, Cfg<PREC>::MINB) pair_kernel(PairArgs A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Smem<PREC> &s = *reinterpret_cast<Smem<PREC> *>(smem_raw);
   Cta<PREC> c(s, A);
@@ -1481,13 +1506,13 @@ cudaError_t launch_pairs(const PairArgs &a, int num_sms, cudaStream_t s) {
                                          (int)smem);
     if (e != cudaSuccess) return e;
     int q = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, pair_kernel<PREC, MODE>, NT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&q, pair_kernel<PREC, MODE>, Cfg<PREC>::NT, smem);
     if (e != cudaSuccess) return e;
     per_sm = q < 1 ? 1 : q;
   }
   int64_t grid = (int64_t)num_sms * per_sm;
   if (a.max_pairs < grid) grid = a.max_pairs > 0 ? a.max_pairs : 1;
-  pair_kernel<PREC, MODE><<<(unsigned)grid, NT, smem, s>>>(a);
+  pair_kernel<PREC, MODE><<<(unsigned)grid, Cfg<PREC>::NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
