@@ -44,6 +44,7 @@ constexpr int ACAP = 512;    // closest-pair candidates per evaluation
 constexpr int WFLUSH = 64;   // a warp evaluates its candidate list at this size
 constexpr int QWARP = 12;    // binary64 queues up to this size run one triangle pair per warp
 constexpr int GRID_MAX = 16; // sample times whose poses are computed up front
+constexpr int ILCAP = 512;   // triangle pairs of the pair-interval candidate list
 // FP32 error band relative to the pair's coordinate scale S: 2^-17 = 128
 // units of float32 rounding.  The measured maximum of |d32 - d64| / S over
 // the workload and the adversarial cases of the tests is below 2^-22.
@@ -139,6 +140,9 @@ struct __align__(128) Smem {
   int64_t i, j, offA, offB;
   int nA, nB, ngp, gpnext, found, resA, resB, frmA, frmB, bad, abort, nac, ngrid;
   int wcnt[NW];
+  uint32_t il[ILCAP];                 // pair-interval candidates (a << 16 | b)
+  int nil, ilover, ilcol;
+  double delta;                       // bound on the change of any distance over the interval
   double gR[GRID_MAX][2][9], gX[GRID_MAX][2][3];  // poses at the sample times
   unsigned long long bound;           // bits of a non-negative double
   unsigned long long mbar;
@@ -712,6 +716,21 @@ struct Cta {
       const bool have = k < cnt;
       const uint32_t ent = have ? list[k] : 0u;
       const int a = int(ent >> 16), b = int(ent & 0xffffu);
+      if (s.ilcol) {
+        // remember the candidate for the rest of the pair interval
+        const uint32_t m = __ballot_sync(0xffffffffu, have);
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&s.nil, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (have) {
+          const int pos = base + __popc(m & lanemask_lt());
+          const int ag = ta * TT + a, bg = tb * TT + b;
+          if (pos < ILCAP && ag < 65536 && bg < 65536)
+            s.il[pos] = (uint32_t(ag) << 16) | uint32_t(bg);
+          else
+            s.ilover = 1;
+        }
+      }
       T d2 = O::inf();
       V pa{}, pb{};
       if (have) {
@@ -1062,8 +1081,10 @@ struct Cta {
   // ARGMIN: leaves the exact closest pair in s.best_*, FP32 minimum in s.mhat.
   // DECIDE and ARGMIN together: the decision, and the closest pair only when
   // the decision is true.
+  // extra > 0: candidates up to eps + extra, all remembered in the interval
+  // list (see decide_list).
   template <bool DECIDE, bool ARGMIN, bool CONTACTS>
-  __device__ bool eval(double t, int64_t pk, int kidx = -1) {
+  __device__ bool eval(double t, int64_t pk, int kidx = -1, double extra = 0.0) {
     set_time(t, kidx);
     mw = O::inf();
     bd2 = OpsD::inf();
@@ -1074,7 +1095,13 @@ struct Cta {
     bpa[0] = bpa[1] = bpa[2] = 0.0;
     bpb[0] = bpb[1] = bpb[2] = 0.0;
     const int nta = ntiles(s.nA), ntb = ntiles(s.nB);
-    const T th0 = T(s.eps) + T(s.Elb);
+    const T th0 = T(s.eps) + T(s.Elb) + T(extra);
+    if (tid == 0) {
+      s.nil = 0;
+      s.ilover = 0;
+      s.ilcol = extra > 0.0 ? 1 : 0;
+    }
+    __syncthreads();
     bool stop = false;
     for (int ta = 0; ta < nta && !stop; ++ta)
       for (int tb = 0; tb < ntb && !stop; ++tb) {
@@ -1083,6 +1110,7 @@ struct Cta {
         scan_tiles<DECIDE, ARGMIN, CONTACTS>(ta, tb, false, th0, pk);
         if (DECIDE && !ARGMIN && s.found) stop = true;
       }
+    if (tid == 0) s.ilcol = 0;
     if (DECIDE && ARGMIN) {
       const bool f = *(volatile int *)&s.found != 0;
       __syncthreads();
@@ -1186,6 +1214,83 @@ struct Cta {
     }
     if (lane == 0) stat(ST_FP64, n64);
     __syncthreads();
+  }
+
+  // Decision f(t) <= eps on the pair-interval list: every triangle pair that
+  // can come within eps anywhere in [ts, ts + T] is on it (its sphere bound
+  // at ts was within eps + delta, delta bounding how much any distance can
+  // change over the interval), so the list decides exactly like the full scan.
+  __device__ bool decide_list(double t, int kidx) {
+    set_time(t, kidx);
+    const int n = s.nil;
+    const T eps = T(s.eps), Ed = T(s.Ed);
+    bool yes_any = false;
+    unsigned long long n32 = 0, n64 = 0;
+    for (int r0 = w * 32; r0 < n; r0 += NT) {
+      const int k = r0 + lane;
+      const bool have = k < n;
+      const uint32_t ent = have ? s.il[k] : 0u;
+      const int ag = int(ent >> 16), bg = int(ent & 0xffffu);
+      T d = O::inf();
+      if (have) {
+        V X[3], Y[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const float4 f = A.tris[q * A.n_tris + s.offA + ag];
+          const float4 g = A.tris[q * A.n_tris + s.offB + bg];
+          if constexpr (PREC == 0) {
+            X[q] = V{f.x, f.y, f.z};
+            const float *R = s.Rr;
+            Y[q] = V{fmaf(R[0], g.x, fmaf(R[1], g.y, fmaf(R[2], g.z, s.tr[0]))),
+                     fmaf(R[3], g.x, fmaf(R[4], g.y, fmaf(R[5], g.z, s.tr[1]))),
+                     fmaf(R[6], g.x, fmaf(R[7], g.y, fmaf(R[8], g.z, s.tr[2])))};
+          } else {
+            const V3<double> x = to_world_exact(s.RA, s.XA, f.x, f.y, f.z);
+            const V3<double> y = to_world_exact(s.RB, s.XB, g.x, g.y, g.z);
+            X[q] = V{T(x.x), T(x.y), T(x.z)};
+            Y[q] = V{T(y.x), T(y.y), T(y.z)};
+          }
+        }
+        V pa, pb;
+        T d2 = GT::tri_dist2_features(X, Y, pa, pb);
+        if (!(O::sqrt(d2) < eps - Ed)) {
+          V x;
+          bool hit = false;
+          for (int q = 0; q < 3 && !hit; ++q)
+            hit = GT::seg_tri_cross(X[q], X[q == 2 ? 0 : q + 1], Y[0], Y[1], Y[2], x);
+          for (int q = 0; q < 3 && !hit; ++q)
+            hit = GT::seg_tri_cross(Y[q], Y[q == 2 ? 0 : q + 1], X[0], X[1], X[2], x);
+          if (hit) d2 = T(0);
+        }
+        d = O::sqrt(d2);
+        ++n32;
+      }
+      bool yes = have && (PREC == 0 ? d < eps - Ed : d <= eps);
+      if (__any_sync(0xffffffffu, yes)) {
+        yes_any = true;
+        break;
+      }
+      if constexpr (PREC == 0) {
+        // the FP32 band: binary64, one triangle pair per warp
+        uint32_t bm = __ballot_sync(0xffffffffu, have && d <= eps + Ed);
+        while (bm && !yes_any) {
+          const int src = __ffs(bm) - 1;
+          bm &= bm - 1;
+          V3<double> qa, qb;
+          const double e2 = exact_warp(__shfl_sync(0xffffffffu, ag, src), __shfl_sync(0xffffffffu, bg, src), qa, qb);
+          ++n64;
+          if (OpsD::sqrt(e2) <= s.eps) yes_any = true;
+        }
+        if (yes_any) break;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) n32 += __shfl_xor_sync(0xffffffffu, n32, o);
+    if (lane == 0) {
+      stat(ST_FP32, n32);
+      stat(ST_FP64, n64);
+    }
+    return __syncthreads_or(yes_any) != 0;
   }
 
   __device__ double block_min(double v) {
@@ -1344,7 +1449,24 @@ __global__ void __launch_bounds__(Cfg<PREC>::NT, Cfg<PREC>::MINB) pair_kernel(Pa
       if (ok && s.nA > 0 && s.nB > 0) {
         ++evals;
         c.pose_grid(A.K);
-        if (c.template eval<true, true, false>(ts, k, 0)) {
+        if (c.tid == 0) {
+          // bound on the change of any triangle-pair distance over [ts, ts+T]:
+          // each vertex moves at most (|v| + |w| R) per unit time
+          const double *st = A.st;
+          const int64_t n = A.n;
+          double m = 0.0;
+          for (int side = 0; side < 2; ++side) {
+            const int64_t p = side == 0 ? s.i : s.j;
+            const double v = sqrt(st[3 * n + p] * st[3 * n + p] + st[4 * n + p] * st[4 * n + p] +
+                                  st[5 * n + p] * st[5 * n + p]);
+            const double om = sqrt(st[10 * n + p] * st[10 * n + p] + st[11 * n + p] * st[11 * n + p] +
+                                   st[12 * n + p] * st[12 * n + p]);
+            m += v + om * st[16 * n + p];
+          }
+          s.delta = m * T * (1.0 + 1e-9) + 1e-300;
+        }
+        __syncthreads();
+        if (c.template eval<true, true, false>(ts, k, 0, s.delta)) {
           status = 1;
           ta = int32_t(s.best_key >> 32);
           tb = int32_t(s.best_key & 0xffffffffu);
@@ -1354,7 +1476,8 @@ __global__ void __launch_bounds__(Cfg<PREC>::NT, Cfg<PREC>::MINB) pair_kernel(Pa
           for (int q = 1; q <= A.K; ++q) {
             const double tq = D::add(ts, D::div(D::mul(T, double(q)), double(A.K)));
             ++evals;
-            if (c.template eval<true, false, false>(tq, k, q)) {
+            const bool useL = s.ilover == 0;
+            if (useL ? c.decide_list(tq, q) : c.template eval<true, false, false>(tq, k, q)) {
               lo = D::add(ts, D::div(D::mul(T, double(q - 1)), double(A.K)));
               hi = tq;
               fnd = true;
@@ -1367,7 +1490,8 @@ __global__ void __launch_bounds__(Cfg<PREC>::NT, Cfg<PREC>::MINB) pair_kernel(Pa
               const double mid = D::add(lo, D::mul(0.5, D::sub(hi, lo)));
               ++evals;
               ++bis;
-              if (c.template eval<true, false, false>(mid, k))
+              const bool useL = s.ilover == 0;
+              if (useL ? c.decide_list(mid, -1) : c.template eval<true, false, false>(mid, k))
                 hi = mid;
               else
                 lo = mid;
