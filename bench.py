@@ -182,12 +182,43 @@ def gpu_arm(args, rank, world, local):
                                   max_contacts=1 << 20, device=dev)
 
     def measure(prec, steps, warmup, detail):
+        """Stage split from direct calls (CUDA events between the calls), then
+        the timed steps as replays of the step captured in a CUDA graph."""
         ctx = mk(prec)
         for _ in range(warmup):
             run_step(ctx, sc)
         ctx.check()
         ctx.stats(reset=True)
-        E = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+        # stage split: direct calls
+        nsplit = max(3, min(steps, 10))
+        E = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(nsplit)]
+        for k in range(nsplit):
+            flush.fill_(float(k))
+            e = E[k]
+            e[0].record()
+            run_step(ctx, sc, ev=(e[1], e[2], e[3]))
+            e[4].record()
+        torch.cuda.synchronize()
+        ct_ms = [e[2].elapsed_time(e[3]) for e in E]
+        nw_ms = [e[1].elapsed_time(e[2]) for e in E]
+        direct_ms = [e[0].elapsed_time(e[4]) for e in E]
+        # the whole step as one CUDA graph
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            run_step(ctx, sc)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        l0 = ctx.stats()["kernel_launches"]
+        with torch.cuda.graph(g):
+            run_step(ctx, sc)
+        launches_step = ctx.stats()["kernel_launches"] - l0
+        g.replay()
+        torch.cuda.synchronize()
+        ctx.check()
+        ctx.stats(reset=True)
+        G = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -197,10 +228,9 @@ def gpu_arm(args, rank, world, local):
         t0 = time.perf_counter()
         for k in range(steps):
             flush.fill_(float(k))  # L2 flush between steps, outside the timed events
-            e = E[k]
-            e[0].record()
-            run_step(ctx, sc, ev=(e[1], e[2], e[3]))
-            e[4].record()
+            G[k][0].record()
+            g.replay()
+            G[k][1].record()
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         if world > 1:
@@ -208,10 +238,10 @@ def gpu_arm(args, rank, world, local):
         clocks = clk.stop() if clk else None
         ctx.check()
         st = ctx.stats(reset=True)
-        step_ms = [e[0].elapsed_time(e[4]) for e in E]
-        ct_ms = [e[2].elapsed_time(e[3]) for e in E]
-        nw_ms = [e[1].elapsed_time(e[2]) for e in E]
-        return ctx, dict(step_ms=step_ms, ct_ms=ct_ms, nw_ms=nw_ms, stats=st, wall=wall, clocks=clocks)
+        st["kernel_launches"] = launches_step * steps
+        step_ms = [e[0].elapsed_time(e[1]) for e in G]
+        return ctx, dict(step_ms=step_ms, ct_ms=ct_ms, nw_ms=nw_ms, stats=st, wall=wall, clocks=clocks,
+                         direct_ms=direct_ms, graph=g)
 
     ctx32, r32 = measure(dem.DEM_PREC_FP32_FIXUP, args.steps, args.warmup, True)
     K = args.steps
@@ -259,10 +289,11 @@ def gpu_arm(args, rank, world, local):
         ctx64.close()
 
     # end to end through the public API from pinned host buffers
-    e2e = e2e_arm(dem, w, ctx32, dev, max(3, min(K, 10)))
+    e2e = e2e_arm(dem, w, ctx32, sc, max(3, min(K, 10)), r32["graph"])
 
     res = dict(value_local=checks_step * K, time_local=t_total, particles=w.n, K=K, n_pairs=n_pairs,
                ms=float(np.mean(r32["step_ms"])), ct_ms=ct_ms, nw_ms=float(np.mean(r32["nw_ms"])),
+               direct_ms=float(np.mean(r32["direct_ms"])),
                achieved=achieved, ct_flops=ct_flops, st_ct=st_ct, clocks=r32["clocks"], wall=r32["wall"],
                launches=r32["stats"]["kernel_launches"], fp32_err=fp32_err, fp64=fp64, e2e=e2e,
                checks_step=checks_step, stats_step={k: v / K for k, v in r32["stats"].items()})
@@ -270,11 +301,13 @@ def gpu_arm(args, rank, world, local):
     return res
 
 
-def e2e_arm(dem, w, ctx, dev, steps):
+def e2e_arm(dem, w, ctx, sc, steps, graph):
+    """Through the public API from pinned host buffers: host-to-device copies
+    of the particle data into the scene the step graph was captured on, the
+    step, device-to-host copies of every output."""
     import torch
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     h_state, h_static, h_off, h_tris = pin(w.state), pin(w.is_static), pin(w.tri_off), pin(w.tris)
-    sc = dem.Scene.from_workload(w, device=dev)
     h_out = {}
     bi = sum(t.numel() * t.element_size() for t in (h_state, h_static, h_off, h_tris))
     times, bo = [], 0
@@ -285,7 +318,7 @@ def e2e_arm(dem, w, ctx, dev, steps):
         sc.is_static.copy_(h_static, non_blocking=True)
         sc.tri_off.copy_(h_off, non_blocking=True)
         sc.tris.copy_(h_tris, non_blocking=True)
-        run_step(ctx, sc)
+        graph.replay()
         m = int(ctx.n_pairs.item())
         nc = min(int(ctx.n_contacts.item()), ctx.max_contacts)
         outs = [ctx.pairs[:m], ctx.flag[:m], ctx.dmin[:m], ctx.tri_ab[:m], ctx.t_coll[:m], ctx.status[:m],
@@ -300,6 +333,7 @@ def e2e_arm(dem, w, ctx, dev, steps):
     ctx.check()
     st = ctx.stats(reset=True)
     checks = st["method_checks"] / (steps + 2)
+    h_out.clear()
     return {"value": checks / float(np.mean(times)), "unit": UNIT, "h2d_bytes_per_step": int(bi),
             "d2h_bytes_per_step": int(bo), "ms_per_step": 1e3 * float(np.mean(times))}
 
@@ -399,7 +433,9 @@ def main():
                            "l2": "flushed (512 MB write) between timed steps", "parallelism": f"replicas x{world}"},
                 "particle_steps_per_s": world * r["particles"] * K / tmax,
                 "checks_per_step": r["checks_step"],
-                "stage_ms": {"narrow": r["nw_ms"], "collision_times": r["ct_ms"]},
+                "stage_ms": {"narrow": r["nw_ms"], "collision_times": r["ct_ms"],
+                             "step_without_graph": r["direct_ms"]},
+                "cuda_graph": "timed steps are replays of the four-call step captured in one CUDA graph",
                 "roofline": roof, "cpu_baseline": cpu, "e2e": r["e2e"], "clocks": r["clocks"],
                 "gpu_launches": int(r["launches"]), "fp64_form": r["fp64"], "fp32_error": r["fp32_err"],
                 "counters_per_step": r["stats_step"]}

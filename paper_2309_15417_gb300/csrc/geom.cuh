@@ -35,8 +35,12 @@ struct OpsF {
   static __device__ __forceinline__ float add(float a, float b) { return a + b; }
   static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
   static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
-  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
-  static __device__ __forceinline__ float sqrt(float a) { return __fsqrt_rn(a); }
+  // hardware-approximate quotient and square root (a few ulp): the FP32
+  // results only have to stay inside the caller's error band
+  static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  static __device__ __forceinline__ float sqrt(float a) {
+    return a > 1e-30f ? a * rsqrtf(a) : __fsqrt_rn(a);  // tiny and denormal inputs: exact path
+  }
   static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
 };
 

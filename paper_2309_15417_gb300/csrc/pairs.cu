@@ -1199,8 +1199,10 @@ struct Cta {
         }
     }
     unsigned long long n64 = 0;
-    for (int r0 = 0; r0 < n; r0 += NW) {
-      const int q = r0 + w;
+    // round 0: the smallest key alone (it settles most intersecting pairs);
+    // then NW candidates per round
+    for (int r0 = 0; r0 < n; r0 = (r0 == 0 ? 1 : r0 + NW)) {
+      const int q = r0 == 0 ? (w == 0 ? 0 : n) : r0 + w;
       const unsigned long long key = q < n ? s.ac_key[q] : ~0ull;
       double e2 = OpsD::inf();
       if (key != ~0ull) {

@@ -427,3 +427,32 @@ def test_fp32_error_band_adversarial(dem, seed):
     S = R[pairs[:, 0]] + R[pairs[:, 1]] + np.linalg.norm(X[:, pairs[:, 1]] - X[:, pairs[:, 0]], axis=0)
     rel = np.abs(g["dmin32"].astype(np.float64) - o["dmin"]) / S
     assert rel.max() <= 2.0 ** -21, rel.max()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_step_in_cuda_graph_matches_direct_calls(dem, prec):
+    """The four calls captured in one CUDA graph (device-side counts keep the
+    graph static) give the same outputs as direct calls."""
+    import torch
+    w = W.dense_packing(5, nside=5)
+    sc = dem.Scene.from_workload(w)
+    c1, c2 = _ctx(dem, w, prec), _ctx(dem, w, prec)
+    c1.step(sc)
+    c1.check()
+    c2.step(sc)  # warm-up outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        c2.step(sc)
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    c2.check()
+    m = int(c1.n_pairs.item())
+    assert m == int(c2.n_pairs.item()) and m > 0
+    for name in ("pairs", "dmin", "pa", "pb", "tri_ab", "flag", "t_coll", "status", "ct_ab"):
+        assert torch.equal(getattr(c1, name)[:m], getattr(c2, name)[:m]), name
+    nc = int(c1.n_contacts.item())
+    assert nc == int(c2.n_contacts.item())
+    assert torch.equal(c1.contacts[:nc], c2.contacts[:nc])
+    assert torch.equal(c1.cluster_id[:w.n], c2.cluster_id[:w.n])
