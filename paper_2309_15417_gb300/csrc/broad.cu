@@ -11,9 +11,9 @@
 // table (counting sort of particles into buckets).  Overlapping spheres lie in
 // the same or adjacent cells, so scanning the 27 neighbour cells finds every
 // candidate; the binary64 predicate then decides, so the set equals the
-// brute-force set.  Per particle the candidates are counted, offsets are
-// scanned, and each particle writes its partners sorted by j: the output is in
-// (i, j) order without a global sort.
+// brute-force set.  Per particle (one warp, lanes over the 27 cells) the
+// candidates are counted, offsets are scanned, and each particle writes its
+// partners sorted by j: the output is in (i, j) order without a global sort.
 #include "internal.cuh"
 
 namespace dem {
@@ -82,49 +82,79 @@ __global__ void k_scatter(int64_t n, const int4 *cell, const int64_t *bstart, in
   }
 }
 
+// One warp per particle i: lane c < 27 scans neighbour cell c; counts are
+// combined with a warp prefix sum.  WRITE: the partners are written at the
+// particle's offset and sorted by j (bitonic in registers for up to 32).
 template <bool WRITE>
 __global__ void k_pairs(int64_t n, const Sphere4 *sph, const int4 *cell, const uint8_t *is_static,
                         const int32_t *bcnt, const int64_t *bstart, const int32_t *ids, uint32_t mask,
                         int64_t *pcnt, const int64_t *poff, int32_t *pairs, int64_t cap,
                         const int64_t *n_pairs, uint32_t *err) {
   if (WRITE && blockIdx.x == 0 && threadIdx.x == 0 && *n_pairs > cap) set_err(err, ERR_CAPACITY);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; i < n; i += nwarp) {
     const Sphere4 si = sph[i];
     const int4 ci = cell[i];
     const bool sti = is_static && is_static[i];
-    int64_t c = 0;
-    const int64_t o = WRITE ? poff[i] : 0;
-    for (int dz = -1; dz <= 1; ++dz)
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int cx = ci.x + dx, cy = ci.y + dy, cz = ci.z + dz;
-          const uint32_t b = bucket_of(cx, cy, cz, mask);
-          const int64_t b0 = bstart[b], b1 = b0 + bcnt[b];
-          for (int64_t q = b0; q < b1; ++q) {
-            const int32_t j = ids[q];
-            if (j <= i) continue;
-            const int4 cj = cell[j];
-            if (cj.x != cx || cj.y != cy || cj.z != cz) continue;  // other cell, same bucket
-            if (sti && is_static[j]) continue;
-            const Sphere4 sj = sph[j];
-            const double ddx = D::sub(si.x, sj.x), ddy = D::sub(si.y, sj.y), ddz = D::sub(si.z, sj.z);
-            const double dd = D::add(D::add(D::mul(ddx, ddx), D::mul(ddy, ddy)), D::mul(ddz, ddz));
-            const double rr = D::add(si.w, sj.w);
-            if (dd <= D::mul(rr, rr)) {
-              if (WRITE && o + c < cap) {
-                pairs[2 * (o + c)] = int32_t(i);
-                pairs[2 * (o + c) + 1] = j;
-              }
-              ++c;
-            }
-          }
-        }
+    const int cx = ci.x + (lane % 3) - 1, cy = ci.y + ((lane / 3) % 3) - 1, cz = ci.z + (lane / 9) - 1;
+    int64_t b0 = 0, b1 = 0;
+    if (lane < 27) {
+      const uint32_t b = bucket_of(cx, cy, cz, mask);
+      b0 = bstart[b];
+      b1 = b0 + bcnt[b];
+    }
+    // the binary64 candidate predicate (same operation order as the oracle)
+    auto is_pair = [&](int32_t j) {
+      if (j <= i) return false;
+      const int4 cj = cell[j];
+      if (cj.x != cx || cj.y != cy || cj.z != cz) return false;  // other cell, same bucket
+      if (sti && is_static[j]) return false;
+      const Sphere4 sj = sph[j];
+      const double ddx = D::sub(si.x, sj.x), ddy = D::sub(si.y, sj.y), ddz = D::sub(si.z, sj.z);
+      const double dd = D::add(D::add(D::mul(ddx, ddx), D::mul(ddy, ddy)), D::mul(ddz, ddz));
+      const double rr = D::add(si.w, sj.w);
+      return dd <= D::mul(rr, rr);
+    };
+    int c = 0;
+    for (int64_t q = b0; q < b1; ++q) c += is_pair(ids[q]) ? 1 : 0;
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, inc, 31);
     if (!WRITE) {
-      pcnt[i] = c;
-    } else {
-      // sort this particle's partners by j (short lists: insertion sort)
-      const int64_t e = o + c < cap ? o + c : cap;
-      for (int64_t a = o + 1; a < e; ++a) {
+      if (lane == 0) pcnt[i] = total;
+      continue;
+    }
+    const int64_t o = poff[i];
+    int64_t pos = o + inc - c;
+    for (int64_t q = b0; q < b1; ++q) {
+      const int32_t j = ids[q];
+      if (is_pair(j)) {
+        if (pos < cap) {
+          pairs[2 * pos] = int32_t(i);
+          pairs[2 * pos + 1] = j;
+        }
+        ++pos;
+      }
+    }
+    __syncwarp();
+    const int64_t e = o + total < cap ? o + total : cap;
+    const int m = int(e > o ? e - o : 0);
+    if (m <= 32) {
+      int32_t key = lane < m ? pairs[2 * (o + lane) + 1] : 0x7fffffff;
+      for (int k = 2; k <= 32; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          const int32_t other = __shfl_xor_sync(0xffffffffu, key, j);
+          const bool lower = (lane & j) == 0, up = (lane & k) == 0;
+          key = (lower == up) ? min(key, other) : max(key, other);
+        }
+      if (lane < m) pairs[2 * (o + lane) + 1] = key;
+    } else if (lane == 0) {
+      for (int64_t a = o + 1; a < e; ++a) {  // long lists (a large particle): insertion sort
         const int32_t v = pairs[2 * a + 1];
         int64_t b = a - 1;
         while (b >= o && pairs[2 * b + 1] > v) {
@@ -134,6 +164,7 @@ __global__ void k_pairs(int64_t n, const Sphere4 *sph, const int4 *cell, const u
         pairs[2 * (b + 1) + 1] = v;
       }
     }
+    __syncwarp();
   }
 }
 
@@ -154,11 +185,12 @@ cudaError_t launch_broad(const dem_particles &P, int32_t *pairs, int64_t cap, in
   k_count<<<grid, tb, 0, s>>>(n, S.sph, S.rho_max, mask, S.cell, S.bucket_cnt);
   S.launches += 2 + scan_exclusive_i32_to_i64(S.bucket_cnt, S.bucket_start, S.table_size, S.scan_part, s);
   k_scatter<<<grid, tb, 0, s>>>(n, S.cell, S.bucket_start, S.bucket_cur, S.bucket_ids);
-  k_pairs<false><<<grid, tb, 0, s>>>(n, S.sph, S.cell, P.is_static, S.bucket_cnt, S.bucket_start, S.bucket_ids,
-                                     mask, S.pcnt, nullptr, nullptr, 0, nullptr, S.err);
+  const unsigned wgrid = (unsigned)((n + 7) / 8);  // one warp per particle
+  k_pairs<false><<<wgrid, tb, 0, s>>>(n, S.sph, S.cell, P.is_static, S.bucket_cnt, S.bucket_start, S.bucket_ids,
+                                      mask, S.pcnt, nullptr, nullptr, 0, nullptr, S.err);
   S.launches += 2 + scan_exclusive_i64(S.pcnt, S.poff, n, n_pairs, S.scan_part, s);
-  k_pairs<true><<<grid, tb, 0, s>>>(n, S.sph, S.cell, P.is_static, S.bucket_cnt, S.bucket_start, S.bucket_ids,
-                                    mask, nullptr, S.poff, pairs, cap, n_pairs, S.err);
+  k_pairs<true><<<wgrid, tb, 0, s>>>(n, S.sph, S.cell, P.is_static, S.bucket_cnt, S.bucket_start, S.bucket_ids,
+                                     mask, nullptr, S.poff, pairs, cap, n_pairs, S.err);
   S.launches += 1;
   return cudaGetLastError();
 }
