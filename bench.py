@@ -154,15 +154,23 @@ def _profile_traffic():
     return float(m.group(1))
 
 
-def run_step(ctx, sc, ev=None):
-    """One detection step; optional events around narrow phase and collision times."""
+def run_step(ctx, sc, ev=None, fused=True):
+    """One detection step: candidates, narrow phase at the pair start and
+    collision times (fused: one dem_detect launch; else the two calls),
+    clusters.  Optional events: before the narrow phase, between the two calls
+    (not fused), after the collision times."""
     ctx.build_candidates(sc)
     if ev:
         ev[0].record()
-    ctx.narrow_phase(sc)
-    if ev:
-        ev[1].record()
-    ctx.collision_times(sc)
+    if fused:
+        ctx.detect(sc)
+        if ev:
+            ev[1].record()
+    else:
+        ctx.narrow_phase(sc)
+        if ev:
+            ev[1].record()
+        ctx.collision_times(sc)
     if ev:
         ev[2].record()
     ctx.clusters(sc)
@@ -181,12 +189,12 @@ def gpu_arm(args, rank, world, local):
     mk = lambda prec: dem.Context(K=w.K, tol=w.tol, precision=prec, max_particles=w.n, max_pairs=1 << 16,
                                   max_contacts=1 << 20, device=dev)
 
-    def measure(prec, steps, warmup, detail):
+    def measure(prec, steps, warmup, detail, fused=True):
         """Stage split from direct calls (CUDA events between the calls), then
         the timed steps as replays of the step captured in a CUDA graph."""
         ctx = mk(prec)
         for _ in range(warmup):
-            run_step(ctx, sc)
+            run_step(ctx, sc, fused=fused)
         ctx.check()
         ctx.stats(reset=True)
         # stage split: direct calls
@@ -196,23 +204,24 @@ def gpu_arm(args, rank, world, local):
             flush.fill_(float(k))
             e = E[k]
             e[0].record()
-            run_step(ctx, sc, ev=(e[1], e[2], e[3]))
+            run_step(ctx, sc, ev=(e[1], e[2], e[3]), fused=fused)
             e[4].record()
         torch.cuda.synchronize()
         ct_ms = [e[2].elapsed_time(e[3]) for e in E]
         nw_ms = [e[1].elapsed_time(e[2]) for e in E]
+        det_ms = [e[1].elapsed_time(e[3]) for e in E]
         direct_ms = [e[0].elapsed_time(e[4]) for e in E]
         # the whole step as one CUDA graph
         g = torch.cuda.CUDAGraph()
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
-            run_step(ctx, sc)
+            run_step(ctx, sc, fused=fused)
         torch.cuda.current_stream().wait_stream(side)
         torch.cuda.synchronize()
         l0 = ctx.stats()["kernel_launches"]
         with torch.cuda.graph(g):
-            run_step(ctx, sc)
+            run_step(ctx, sc, fused=fused)
         launches_step = ctx.stats()["kernel_launches"] - l0
         g.replay()
         torch.cuda.synchronize()
@@ -240,8 +249,8 @@ def gpu_arm(args, rank, world, local):
         st = ctx.stats(reset=True)
         st["kernel_launches"] = launches_step * steps
         step_ms = [e[0].elapsed_time(e[1]) for e in G]
-        return ctx, dict(step_ms=step_ms, ct_ms=ct_ms, nw_ms=nw_ms, stats=st, wall=wall, clocks=clocks,
-                         direct_ms=direct_ms, graph=g)
+        return ctx, dict(step_ms=step_ms, ct_ms=ct_ms, nw_ms=nw_ms, det_ms=det_ms, stats=st, wall=wall,
+                         clocks=clocks, direct_ms=direct_ms, graph=g)
 
     ctx32, r32 = measure(dem.DEM_PREC_FP32_FIXUP, args.steps, args.warmup, True)
     K = args.steps
@@ -249,16 +258,23 @@ def gpu_arm(args, rank, world, local):
     t_total = sum(r32["step_ms"]) / 1e3
     n_pairs = int(ctx32.n_pairs.item())
 
-    # collision-time kernel characterisation: counters of one call alone
+    # dominant kernel (the fused pair kernel of dem_detect): counters of one
+    # call alone, duration from the events around dem_detect
     ctx32.stats(reset=True)
     run_step(ctx32, sc)
     torch.cuda.synchronize()
     ctx32.stats(reset=True)
-    ctx32.collision_times(sc)
+    ctx32.detect(sc)
     st_ct = ctx32.stats(reset=True)
     ct_flops = F_SPHERE * st_ct["sphere_tests"] + F_GROUP * st_ct["group_tests"] + F_DIST32 * st_ct["dist_fp32"]
-    ct_ms = float(np.mean(r32["ct_ms"]))
+    ct_ms = float(np.mean(r32["det_ms"]))
     achieved = ct_flops / (ct_ms / 1e3) / 1e12
+    # the same step through the four separate calls (narrow phase and
+    # collision times as two launches)
+    ctx4, r4 = measure(dem.DEM_PREC_FP32_FIXUP, max(3, min(K, 10)), 2, False, fused=False)
+    four_call = {"ms_per_step": float(np.mean(r4["step_ms"])), "narrow_ms": float(np.mean(r4["nw_ms"])),
+                 "collision_times_ms": float(np.mean(r4["ct_ms"]))}
+    ctx4.close()
 
     # FP32 error against FP64 (pair minima), R = 1
     fin = torch.isfinite(ctx32.dmin[:n_pairs])
@@ -292,7 +308,7 @@ def gpu_arm(args, rank, world, local):
     e2e = e2e_arm(dem, w, ctx32, sc, max(3, min(K, 10)), r32["graph"])
 
     res = dict(value_local=checks_step * K, time_local=t_total, particles=w.n, K=K, n_pairs=n_pairs,
-               ms=float(np.mean(r32["step_ms"])), ct_ms=ct_ms, nw_ms=float(np.mean(r32["nw_ms"])),
+               ms=float(np.mean(r32["step_ms"])), ct_ms=ct_ms, four_call=four_call,
                direct_ms=float(np.mean(r32["direct_ms"])),
                achieved=achieved, ct_flops=ct_flops, st_ct=st_ct, clocks=r32["clocks"], wall=r32["wall"],
                launches=r32["stats"]["kernel_launches"], fp32_err=fp32_err, fp64=fp64, e2e=e2e,
@@ -421,7 +437,7 @@ def main():
         value = total_checks / tmax
         K = args.steps
         ms = 1e3 * tmax / K
-        roof = {"bound": "alu", "kernel": "pair_kernel<FP32, collision times>", "achieved": r["achieved"],
+        roof = {"bound": "alu", "kernel": "pair_kernel<FP32, narrow phase + collision times>", "achieved": r["achieved"],
                 "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": r["achieved"] / FP32_PEAK_TFLOPS,
                 "traffic": _profile_traffic(), "peak_source": "recipe unit counts: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                 "flops_per_launch": r["ct_flops"], "ms_per_launch": r["ct_ms"]}
@@ -433,9 +449,11 @@ def main():
                            "l2": "flushed (512 MB write) between timed steps", "parallelism": f"replicas x{world}"},
                 "particle_steps_per_s": world * r["particles"] * K / tmax,
                 "checks_per_step": r["checks_step"],
-                "stage_ms": {"narrow": r["nw_ms"], "collision_times": r["ct_ms"],
+                "stage_ms": {"detect (narrow phase + collision times)": r["ct_ms"],
                              "step_without_graph": r["direct_ms"]},
-                "cuda_graph": "timed steps are replays of the four-call step captured in one CUDA graph",
+                "four_call_step": r["four_call"],
+                "cuda_graph": "timed steps are replays of the step (candidates, detect, clusters) captured in "
+                              "one CUDA graph",
                 "roofline": roof, "cpu_baseline": cpu, "e2e": r["e2e"], "clocks": r["clocks"],
                 "gpu_launches": int(r["launches"]), "fp64_form": r["fp64"], "fp32_error": r["fp32_err"],
                 "counters_per_step": r["stats_step"]}

@@ -193,6 +193,16 @@ dem_status dem_collision_times(dem_ctx *ctx, const dem_particles *P, const int32
                                int64_t max_pairs, const int64_t *n_pairs, double *t_coll,
                                uint8_t *status, int32_t *tri_ab, void *stream);
 
+/* Narrow phase at the pair start and collision times in one launch: the
+ * outputs of dem_narrow_phase(..., t_eval = NULL, out) and of
+ * dem_collision_times(..., t_coll, status, tri_ab), identical to the two
+ * separate calls.  The evaluation at the pair start serves both (the paper's
+ * narrow collision and time-step-size phases, Section 5, evaluated at the
+ * same snapshot). */
+dem_status dem_detect(dem_ctx *ctx, const dem_particles *P, const int32_t *pairs, int64_t max_pairs,
+                      const int64_t *n_pairs, const dem_narrow_out *out, double *t_coll, uint8_t *status,
+                      int32_t *tri_ab, void *stream);
+
 /* Clusters (paper Section 3: the pruned graph's disconnected subgraphs are
  * the clusters; static objects take no part in the clustering).  Connected
  * components of the undirected graph over n particles given by edges

@@ -166,6 +166,26 @@ dem_status dem_collision_times(dem_ctx *c, const dem_particles *P, const int32_t
   return DEM_OK;
 }
 
+dem_status dem_detect(dem_ctx *c, const dem_particles *P, const int32_t *pairs, int64_t max_pairs,
+                      const int64_t *n_pairs, const dem_narrow_out *out, double *t_coll, uint8_t *status,
+                      int32_t *tri_ab, void *stream) {
+  if (!c) return DEM_ERR_ARG;
+  dem_status st = check_particles(c, P);
+  if (st != DEM_OK) return st;
+  if (max_pairs < 0 || (max_pairs > 0 && (!pairs || !t_coll || !status || !tri_ab)))
+    return fail(c, DEM_ERR_ARG, "detect: bad pairs or collision-time outputs");
+  if (max_pairs > c->S.cap_pairs) return fail(c, DEM_ERR_CAPACITY, "detect: max_pairs exceeds capacity");
+  if (!out || !out->n_contacts || out->contact_cap < 0 ||
+      (max_pairs > 0 && (!out->dmin || !out->pa || !out->pb || !out->tri_ab || !out->flag)) ||
+      (out->contact_cap > 0 && (!out->contacts || !out->contact_geom)))
+    return fail(c, DEM_ERR_ARG, "detect: bad narrow-phase outputs");
+  cudaError_t e = dem::launch_detect(c->cfg.precision, *P, pairs, max_pairs, n_pairs, *out, c->cfg.K,
+                                     c->cfg.bisect_tol, t_coll, status, tri_ab, c->S, c->num_sms,
+                                     static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "detect");
+  return DEM_OK;
+}
+
 dem_status dem_clusters(dem_ctx *c, int64_t n, const int32_t *edges, int64_t max_edges, const int64_t *n_edges,
                         const uint8_t *is_static, int32_t *cluster_id, int64_t *n_clusters, void *stream) {
   if (!c) return DEM_ERR_ARG;

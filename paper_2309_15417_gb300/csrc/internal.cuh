@@ -82,6 +82,9 @@ cudaError_t launch_broad(const dem_particles &P, int32_t *pairs, int64_t cap, in
 cudaError_t launch_narrow(int prec, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
                           const int64_t *n_pairs, const double *t_eval, const dem_narrow_out &out,
                           Scratch &S, int num_sms, cudaStream_t s);
+cudaError_t launch_detect(int prec, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
+                          const int64_t *n_pairs, const dem_narrow_out &out, int K, double tol, double *t_coll,
+                          uint8_t *status, int32_t *tri_ab, Scratch &S, int num_sms, cudaStream_t s);
 cudaError_t launch_ctime(int prec, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
                          const int64_t *n_pairs, int K, double tol, double *t_coll,
                          uint8_t *status, int32_t *tri_ab, Scratch &S, int num_sms,

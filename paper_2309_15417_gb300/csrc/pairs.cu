@@ -53,6 +53,7 @@ constexpr double ERR_REL64_LB = 9.094947017729282e-13;  // 2^-40: FP64 culling m
 
 constexpr int MODE_NARROW = 0;
 constexpr int MODE_CTIME = 1;
+constexpr int MODE_BOTH = 2;  // narrow phase at the pair start + collision times
 
 constexpr int pow2_at_least(int v) { return v <= 1 ? 1 : 2 * pow2_at_least((v + 1) / 2); }
 
@@ -568,11 +569,12 @@ struct Cta {
   }
 
   __device__ void world_of_A_frame(const V &p, double out[3]) const {
-    // FP32 points live in A's body frame: x_world = R_A p + X_A
+    // FP32 points live in A's body frame: x_world = R_A p + X_A (explicit
+    // FMA chain: the same result in every kernel that uses it)
     const double x = p.x, y = p.y, z = p.z;
-    out[0] = s.RA[0] * x + s.RA[1] * y + s.RA[2] * z + s.XA[0];
-    out[1] = s.RA[3] * x + s.RA[4] * y + s.RA[5] * z + s.XA[1];
-    out[2] = s.RA[6] * x + s.RA[7] * y + s.RA[8] * z + s.XA[2];
+    out[0] = __fma_rn(s.RA[0], x, __fma_rn(s.RA[1], y, __fma_rn(s.RA[2], z, s.XA[0])));
+    out[1] = __fma_rn(s.RA[3], x, __fma_rn(s.RA[4], y, __fma_rn(s.RA[5], z, s.XA[1])));
+    out[2] = __fma_rn(s.RA[6], x, __fma_rn(s.RA[7], y, __fma_rn(s.RA[8], z, s.XA[2])));
   }
 
   __device__ __forceinline__ unsigned long long key_of(int a, int b, int ta, int tb) const {
@@ -1420,9 +1422,9 @@ __global__ void __launch_bounds__(Cfg<PREC>::NT, Cfg<PREC>::MINB) pair_kernel(Pa
     if (k >= m || quit) break;
     const bool ok = c.setup_pair(k);
     const double chk = double(s.nA) * double(s.nB);
-    if (MODE == MODE_NARROW) {
-      const double t = A.t_eval ? A.t_eval[k] : s.ts;
-      if (ok) c.template eval<false, true, true>(t, k);
+    using D = OpsD;
+    // narrow-phase outputs of pair k from the closest pair in s.best_*
+    auto write_narrow = [&]() {
       if (c.tid == 0) {
         const bool have = ok && s.best_key != ~0ull && s.nA > 0 && s.nB > 0;
         const double d = have ? OpsD::sqrt(s.best_d2) : OpsD::inf();
@@ -1435,87 +1437,131 @@ __global__ void __launch_bounds__(Cfg<PREC>::NT, Cfg<PREC>::MINB) pair_kernel(Pa
         A.tri_ab[2 * k + 1] = have ? int32_t(s.best_key & 0xffffffffu) : -1;
         A.flag[k] = uint8_t(have && d <= s.eps);
         if (A.dmin32) A.dmin32[k] = have ? float(s.mhat) : __int_as_float(0x7f800000);
-        atomicAdd(&s.cnt[ST_EVALS], 1ull);
-        atomicAdd(&s.cnt[ST_CHECKS], (unsigned long long)chk);
-        atomicAdd(&s.cnt[ST_PAIRS], 1ull);
       }
-    } else {
-      // collision-time search (binary64, operations in the order of the
-      // definition, each rounded on its own)
-      using D = OpsD;
+    };
+    // bound on the change of any triangle-pair distance over [ts, ts+T]:
+    // each vertex moves at most (|v| + |w| R) per unit time
+    auto motion_bound = [&]() {
+      if (c.tid == 0) {
+        const double *st = A.st;
+        const int64_t n = A.n;
+        double m = 0.0;
+        for (int side = 0; side < 2; ++side) {
+          const int64_t p = side == 0 ? s.i : s.j;
+          const double v = sqrt(st[3 * n + p] * st[3 * n + p] + st[4 * n + p] * st[4 * n + p] +
+                                st[5 * n + p] * st[5 * n + p]);
+          const double om = sqrt(st[10 * n + p] * st[10 * n + p] + st[11 * n + p] * st[11 * n + p] +
+                                 st[12 * n + p] * st[12 * n + p]);
+          m += v + om * st[16 * n + p];
+        }
+        s.delta = m * s.T_ * (1.0 + 1e-9) + 1e-300;
+      }
+      __syncthreads();
+    };
+    // the K samples and the bisection after a false decision at ts
+    // (binary64, operations in the order of the definition, each rounded on
+    // its own); returns the status and sets tc / ta / tb
+    auto search = [&](int &evals, int &bis, double &tc, int32_t &ta, int32_t &tb) -> uint8_t {
       const double ts = s.ts, T = s.T_;
-      int evals = 0, bis = 0;
-      uint8_t status = 0;
-      double tc = D::add(ts, T);
-      int32_t ta = -1, tb = -1;
-      if (ok && s.nA > 0 && s.nB > 0) {
+      bool fnd = false;
+      double lo = ts, hi = ts;
+      for (int q = 1; q <= A.K; ++q) {
+        const double tq = D::add(ts, D::div(D::mul(T, double(q)), double(A.K)));
         ++evals;
-        c.pose_grid(A.K);
-        if (c.tid == 0) {
-          // bound on the change of any triangle-pair distance over [ts, ts+T]:
-          // each vertex moves at most (|v| + |w| R) per unit time
-          const double *st = A.st;
-          const int64_t n = A.n;
-          double m = 0.0;
-          for (int side = 0; side < 2; ++side) {
-            const int64_t p = side == 0 ? s.i : s.j;
-            const double v = sqrt(st[3 * n + p] * st[3 * n + p] + st[4 * n + p] * st[4 * n + p] +
-                                  st[5 * n + p] * st[5 * n + p]);
-            const double om = sqrt(st[10 * n + p] * st[10 * n + p] + st[11 * n + p] * st[11 * n + p] +
-                                   st[12 * n + p] * st[12 * n + p]);
-            m += v + om * st[16 * n + p];
-          }
-          s.delta = m * T * (1.0 + 1e-9) + 1e-300;
-        }
-        __syncthreads();
-        if (c.template eval<true, true, false>(ts, k, 0, s.delta)) {
-          status = 1;
-          ta = int32_t(s.best_key >> 32);
-          tb = int32_t(s.best_key & 0xffffffffu);
-        } else {
-          bool fnd = false;
-          double lo = ts, hi = ts;
-          for (int q = 1; q <= A.K; ++q) {
-            const double tq = D::add(ts, D::div(D::mul(T, double(q)), double(A.K)));
-            ++evals;
-            const bool useL = s.ilover == 0;
-            if (useL ? c.decide_list(tq, q) : c.template eval<true, false, false>(tq, k, q)) {
-              lo = D::add(ts, D::div(D::mul(T, double(q - 1)), double(A.K)));
-              hi = tq;
-              fnd = true;
-              break;
-            }
-          }
-          if (fnd) {
-            const double lim = D::mul(A.tol, T);
-            while (D::sub(hi, lo) > lim) {
-              const double mid = D::add(lo, D::mul(0.5, D::sub(hi, lo)));
-              ++evals;
-              ++bis;
-              const bool useL = s.ilover == 0;
-              if (useL ? c.decide_list(mid, -1) : c.template eval<true, false, false>(mid, k))
-                hi = mid;
-              else
-                lo = mid;
-            }
-            status = 2;
-            tc = hi;
-            c.template eval<false, true, false>(hi, k);
-            ta = int32_t(s.best_key >> 32);
-            tb = int32_t(s.best_key & 0xffffffffu);
-          }
+        const bool useL = s.ilover == 0;
+        if (useL ? c.decide_list(tq, q) : c.template eval<true, false, false>(tq, k, q)) {
+          lo = D::add(ts, D::div(D::mul(T, double(q - 1)), double(A.K)));
+          hi = tq;
+          fnd = true;
+          break;
         }
       }
+      if (!fnd) return 0;
+      const double lim = D::mul(A.tol, T);
+      while (D::sub(hi, lo) > lim) {
+        const double mid = D::add(lo, D::mul(0.5, D::sub(hi, lo)));
+        ++evals;
+        ++bis;
+        const bool useL = s.ilover == 0;
+        if (useL ? c.decide_list(mid, -1) : c.template eval<true, false, false>(mid, k))
+          hi = mid;
+        else
+          lo = mid;
+      }
+      tc = hi;
+      c.template eval<false, true, false>(hi, k);
+      ta = int32_t(s.best_key >> 32);
+      tb = int32_t(s.best_key & 0xffffffffu);
+      return 2;
+    };
+    // performed: pair evaluations done; method: evaluations the method defines
+    auto write_times = [&](uint8_t status, double tc, int32_t ta, int32_t tb, int performed, int method, int bis) {
       if (c.tid == 0) {
         A.t_coll[k] = tc;
         A.status[k] = status;
         A.ct_ab[2 * k] = ta;
         A.ct_ab[2 * k + 1] = tb;
-        atomicAdd(&s.cnt[ST_EVALS], (unsigned long long)evals);
-        atomicAdd(&s.cnt[ST_CHECKS], (unsigned long long)(chk * evals));
+        atomicAdd(&s.cnt[ST_EVALS], (unsigned long long)performed);
+        atomicAdd(&s.cnt[ST_CHECKS], (unsigned long long)(chk * method));
         atomicAdd(&s.cnt[ST_BISECT], (unsigned long long)bis);
         atomicAdd(&s.cnt[ST_PAIRS], 1ull);
       }
+    };
+    if (MODE == MODE_NARROW) {
+      const double t = A.t_eval ? A.t_eval[k] : s.ts;
+      if (ok) c.template eval<false, true, true>(t, k);
+      write_narrow();
+      if (c.tid == 0) {
+        atomicAdd(&s.cnt[ST_EVALS], 1ull);
+        atomicAdd(&s.cnt[ST_CHECKS], (unsigned long long)chk);
+        atomicAdd(&s.cnt[ST_PAIRS], 1ull);
+      }
+    } else if (MODE == MODE_CTIME) {
+      int evals = 0, bis = 0;
+      uint8_t status = 0;
+      double tc = D::add(s.ts, s.T_);
+      int32_t ta = -1, tb = -1;
+      if (ok && s.nA > 0 && s.nB > 0) {
+        ++evals;
+        c.pose_grid(A.K);
+        motion_bound();
+        if (c.template eval<true, true, false>(s.ts, k, 0, s.delta)) {
+          status = 1;
+          ta = int32_t(s.best_key >> 32);
+          tb = int32_t(s.best_key & 0xffffffffu);
+        } else {
+          status = search(evals, bis, tc, ta, tb);
+        }
+      }
+      write_times(status, tc, ta, tb, evals, evals, bis);
+    } else {
+      // one evaluation at ts gives the narrow phase, the decision at ts
+      // (closest distance <= eps), the closest pair for status 1 and the
+      // interval list for the search
+      int evals = 0, bis = 0;
+      uint8_t status = 0;
+      double tc = D::add(s.ts, s.T_);
+      int32_t ta = -1, tb = -1;
+      if (ok && s.nA > 0 && s.nB > 0) {
+        ++evals;
+        c.pose_grid(A.K);
+        motion_bound();
+        c.template eval<false, true, true>(s.ts, k, 0, s.delta);
+        write_narrow();
+        if (s.best_key != ~0ull && OpsD::sqrt(s.best_d2) <= s.eps) {
+          status = 1;
+          ta = int32_t(s.best_key >> 32);
+          tb = int32_t(s.best_key & 0xffffffffu);
+        } else {
+          status = search(evals, bis, tc, ta, tb);
+        }
+      } else {
+        if (ok) c.template eval<false, true, true>(s.ts, k);
+        write_narrow();
+      }
+      // the method's count: one narrow-phase evaluation plus the search's
+      // (the evaluation at ts serves both)
+      write_times(status, tc, ta, tb, evals > 0 ? evals : 1, evals + 1, bis);
     }
     __syncthreads();
   }
@@ -1661,6 +1707,44 @@ PairArgs make_args(const dem_particles &P, const int32_t *pairs, int64_t max_pai
 
 }  // namespace
 
+// memsets, the pair kernel (narrow or fused mode), contact offsets, scatter
+// and per-pair sort
+cudaError_t finish_narrow(int prec, PairArgs &a, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
+                          const int64_t *n_pairs, const dem_narrow_out &out, Scratch &S, int num_sms,
+                          cudaStream_t s, bool fused) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(S.work, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(S.st_count, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+  if (max_pairs > 0) {
+    if ((e = cudaMemsetAsync(S.pc, 0, sizeof(int64_t) * max_pairs, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(S.pcur, 0, sizeof(int32_t) * max_pairs, s)) != cudaSuccess) return e;
+    if (fused)
+      e = prec == 0 ? launch_pairs<0, MODE_BOTH>(a, num_sms, s) : launch_pairs<1, MODE_BOTH>(a, num_sms, s);
+    else
+      e = prec == 0 ? launch_pairs<0, MODE_NARROW>(a, num_sms, s) : launch_pairs<1, MODE_NARROW>(a, num_sms, s);
+    if (e != cudaSuccess) return e;
+    S.launches += 1;
+  }
+  // per-pair offsets, scatter, sort
+  int64_t *total = S.tmp;
+  if (max_pairs > 0) {
+    S.launches += scan_exclusive_i64(S.pc, S.po, max_pairs, total, S.scan_part, s);
+  } else {
+    if ((e = cudaMemsetAsync(total, 0, sizeof(int64_t), s)) != cudaSuccess) return e;
+  }
+  if (max_pairs > 0) {
+    const int64_t ocap = out.contact_cap < S.cap_contacts ? out.contact_cap : S.cap_contacts;
+    contact_scatter<<<num_sms * 4, 256, 0, s>>>(S.st_keys, S.st_count, S.cap_contacts, S.po, S.pcur, S.sidx, ocap,
+                                                S.err);
+    contact_sort<<<num_sms * 4, 256, 0, s>>>(S.st_keys, S.st_geom, S.cap_contacts, S.pc, S.po, n_pairs,
+                                             max_pairs, S.sidx, out.contacts, out.contact_geom, ocap, S.err);
+    S.launches += 2;
+  }
+  contact_total<<<1, 1, 0, s>>>(total, S.st_count, S.cap_contacts, out.n_contacts, S.err);
+  S.launches += 1;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_narrow(int prec, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
                           const int64_t *n_pairs, const double *t_eval, const dem_narrow_out &out,
                           Scratch &S, int num_sms, cudaStream_t s) {
@@ -1677,37 +1761,30 @@ cudaError_t launch_narrow(int prec, const dem_particles &P, const int32_t *pairs
   a.st_count = S.st_count;
   a.st_cap = S.cap_contacts;
   a.pc = S.pc;
-  cudaError_t e;
-  if ((e = cudaMemsetAsync(S.work, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(S.st_count, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
-  if (max_pairs > 0) {
-    if ((e = cudaMemsetAsync(S.pc, 0, sizeof(int64_t) * max_pairs, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(S.pcur, 0, sizeof(int32_t) * max_pairs, s)) != cudaSuccess) return e;
-    e = prec == 0 ? launch_pairs<0, MODE_NARROW>(a, num_sms, s) : launch_pairs<1, MODE_NARROW>(a, num_sms, s);
-    if (e != cudaSuccess) return e;
-    S.launches += 1;
-  }
-  // per-pair offsets, scatter, sort
-  int64_t *total = S.tmp;
-  if (max_pairs > 0) {
-    S.launches += scan_exclusive_i64(S.pc, S.po, max_pairs, total, S.scan_part, s);
-  } else {
-    if ((e = cudaMemsetAsync(total, 0, sizeof(int64_t), s)) != cudaSuccess) return e;
-  }
-  if (max_pairs > 0) {
-    contact_scatter<<<num_sms * 4, 256, 0, s>>>(S.st_keys, S.st_count, S.cap_contacts, S.po, S.pcur, S.sidx,
-                                                out.contact_cap < S.cap_contacts ? out.contact_cap : S.cap_contacts,
-                                                S.err);
-    contact_sort<<<num_sms * 4, 256, 0, s>>>(S.st_keys, S.st_geom, S.cap_contacts, S.pc, S.po, n_pairs,
-                                             max_pairs, S.sidx,
-                                             out.contacts, out.contact_geom,
-                                             out.contact_cap < S.cap_contacts ? out.contact_cap : S.cap_contacts,
-                                             S.err);
-    S.launches += 2;
-  }
-  contact_total<<<1, 1, 0, s>>>(total, S.st_count, S.cap_contacts, out.n_contacts, S.err);
-  S.launches += 1;
-  return cudaGetLastError();
+  return finish_narrow(prec, a, P, pairs, max_pairs, n_pairs, out, S, num_sms, s, false);
+}
+
+cudaError_t launch_detect(int prec, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
+                          const int64_t *n_pairs, const dem_narrow_out &out, int K, double tol, double *t_coll,
+                          uint8_t *status, int32_t *tri_ab, Scratch &S, int num_sms, cudaStream_t s) {
+  PairArgs a = make_args(P, pairs, max_pairs, n_pairs, S);
+  a.dmin = out.dmin;
+  a.pa = out.pa;
+  a.pb = out.pb;
+  a.tri_ab = out.tri_ab;
+  a.flag = out.flag;
+  a.dmin32 = out.dmin32;
+  a.st_keys = S.st_keys;
+  a.st_geom = S.st_geom;
+  a.st_count = S.st_count;
+  a.st_cap = S.cap_contacts;
+  a.pc = S.pc;
+  a.t_coll = t_coll;
+  a.status = status;
+  a.ct_ab = tri_ab;
+  a.K = K;
+  a.tol = tol;
+  return finish_narrow(prec, a, P, pairs, max_pairs, n_pairs, out, S, num_sms, s, true);
 }
 
 cudaError_t launch_ctime(int prec, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,

@@ -30,7 +30,8 @@ STATUS = {0: "DEM_OK", -1: "DEM_ERR_ARG", -2: "DEM_ERR_CAPACITY", -3: "DEM_ERR_C
 
 # every symbol include/dem.h declares
 EXPORTS = ["dem_create", "dem_destroy", "dem_last_error", "dem_build_candidates", "dem_narrow_phase",
-           "dem_collision_times", "dem_clusters", "dem_check", "dem_get_stats", "dem_build_candidates_noalloc"]
+           "dem_collision_times", "dem_detect", "dem_clusters", "dem_check", "dem_get_stats",
+           "dem_build_candidates_noalloc"]
 DEM_NOALLOC_MAX_PARTICLES = 16384
 
 
@@ -98,6 +99,9 @@ def load(build_if_needed: bool = True):
         L.dem_narrow_phase.restype = C.c_int
         L.dem_collision_times.argtypes = [vp, C.POINTER(dem_particles), vp, i64, vp, vp, vp, vp, vp]
         L.dem_collision_times.restype = C.c_int
+        L.dem_detect.argtypes = [vp, C.POINTER(dem_particles), vp, i64, vp, C.POINTER(dem_narrow_out), vp, vp,
+                                 vp, vp]
+        L.dem_detect.restype = C.c_int
         L.dem_clusters.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp, vp]
         L.dem_clusters.restype = C.c_int
         L.dem_check.argtypes = [vp, vp]
@@ -168,6 +172,12 @@ def dem_collision_times(ctx, P: dem_particles, pairs, max_pairs: int, n_pairs, t
                         stream=None):
     _check(ctx, load().dem_collision_times(ctx, C.byref(P), _ptr(pairs), int(max_pairs), _ptr(n_pairs),
                                            _ptr(t_coll), _ptr(status), _ptr(tri_ab), _stream(stream)))
+
+
+def dem_detect(ctx, P: dem_particles, pairs, max_pairs: int, n_pairs, out: dem_narrow_out, t_coll, status, tri_ab,
+               stream=None):
+    _check(ctx, load().dem_detect(ctx, C.byref(P), _ptr(pairs), int(max_pairs), _ptr(n_pairs), C.byref(out),
+                                  _ptr(t_coll), _ptr(status), _ptr(tri_ab), _stream(stream)))
 
 
 def dem_clusters(ctx, n: int, edges, max_edges: int, n_edges, is_static, cluster_id, n_clusters, stream=None):
@@ -278,6 +288,14 @@ class Context:
             m, cnt = int(pairs.shape[0]), n_pairs
         dem_collision_times(self.h, scene.P, pairs, m, cnt, self.t_coll, self.status, self.ct_ab, stream)
 
+    def detect(self, scene: Scene, pairs=None, n_pairs=None, stream=None):
+        """Narrow phase at the pair start and collision times in one launch."""
+        if pairs is None:
+            pairs, m, cnt = self.pairs, self.max_pairs, self.n_pairs
+        else:
+            m, cnt = int(pairs.shape[0]), n_pairs
+        dem_detect(self.h, scene.P, pairs, m, cnt, self.out, self.t_coll, self.status, self.ct_ab, stream)
+
     def clusters(self, scene: Scene, edges=None, n_edges=None, stream=None):
         import torch
         if self.cluster_id is None or self.cluster_id.numel() < scene.n:
@@ -294,6 +312,13 @@ class Context:
         self.build_candidates(scene, stream)
         self.narrow_phase(scene, stream=stream)
         self.collision_times(scene, stream=stream)
+        self.clusters(scene, stream=stream)
+
+    def step_fused(self, scene: Scene, stream=None):
+        """The same step with the narrow phase and the collision times fused
+        (dem_detect): candidates, detect, clusters."""
+        self.build_candidates(scene, stream)
+        self.detect(scene, stream=stream)
         self.clusters(scene, stream=stream)
 
     def check(self, stream=None):

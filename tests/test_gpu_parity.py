@@ -456,3 +456,47 @@ def test_step_in_cuda_graph_matches_direct_calls(dem, prec):
     assert nc == int(c2.n_contacts.item())
     assert torch.equal(c1.contacts[:nc], c2.contacts[:nc])
     assert torch.equal(c1.cluster_id[:w.n], c2.cluster_id[:w.n])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("kind", ["small", "dense", "uneven"])
+def test_detect_equals_separate_calls_and_oracle(dem, prec, kind):
+    """dem_detect (narrow phase at the pair start + collision times in one
+    launch) gives the outputs of the two separate calls."""
+    import torch
+    if kind == "small":
+        w = W.small_icospheres(1)
+    elif kind == "dense":
+        w = W.dense_packing(6, nside=5)
+    else:
+        w = W.uneven_meshes(2, n=200, box=25.0)
+    sc = dem.Scene.from_workload(w)
+    c1, c2 = _ctx(dem, w, prec), _ctx(dem, w, prec)
+    c1.build_candidates(sc)
+    c1.narrow_phase(sc)
+    c1.collision_times(sc)
+    c1.check()
+    c2.build_candidates(sc)
+    c2.detect(sc)
+    c2.check()
+    m = int(c1.n_pairs.item())
+    assert m > 0
+    for name in ("dmin", "pa", "pb", "tri_ab", "flag", "t_coll", "status", "ct_ab"):
+        assert torch.equal(getattr(c1, name)[:m], getattr(c2, name)[:m]), name
+    nc = int(c1.n_contacts.item())
+    assert nc == int(c2.n_contacts.item())
+    assert torch.equal(c1.contacts[:nc], c2.contacts[:nc])
+    if prec == 1:
+        assert torch.equal(c1.contact_geom[:nc], c2.contact_geom[:nc])
+    else:
+        # FP32 contact geometry is defined to within the FP32 tolerance
+        R = float(np.max(w.state[W.F_RADIUS]))
+        assert float((c1.contact_geom[:nc] - c2.contact_geom[:nc]).abs().max()) <= 1e-5 * R
+    if kind == "small":
+        pairs = c2.pairs[:m].cpu().numpy()
+        oc = oracle.collision_times(w, pairs)
+        on = oracle.narrow_phase(w, pairs)
+        assert np.array_equal(c2.status[:m].cpu().numpy(), oc["status"])
+        assert np.array_equal(c2.t_coll[:m].cpu().numpy(), oc["t_coll"])
+        assert np.array_equal(c2.ct_ab[:m].cpu().numpy(), oc["tri_ab"])
+        assert np.array_equal(c2.dmin[:m].cpu().numpy(), on["dmin"])
