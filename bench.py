@@ -58,7 +58,7 @@ F_GROUP = 13
 F_DIST32 = 1311
 # FP32 peak: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz maximum SM clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "ctime_kernel_dense1000.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "detect_kernel_dense1000.md")
 
 
 def parse():
