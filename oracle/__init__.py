@@ -58,6 +58,8 @@ def lib():
             L.demo_seg_seg.restype = C.c_double
             L.demo_broad_phase.argtypes = [dp, u8p, C.c_int64, i32p, C.c_int64]
             L.demo_broad_phase.restype = C.c_int64
+            L.demo_broad_partners.argtypes = [dp, u8p, C.c_int64, C.c_int64, i32p, C.c_int64]
+            L.demo_broad_partners.restype = C.c_int64
             L.demo_narrow_phase.argtypes = [dp, C.c_int64, i64p, fp, C.c_int64, i32p, C.c_int64,
                                             dp, dp, dp, dp, i32p, u8p, i32p, dp, C.c_int64, C.c_int]
             L.demo_narrow_phase.restype = C.c_int64
@@ -123,6 +125,21 @@ def broad_phase(w):
     while True:
         pairs = np.zeros((cap, 2), np.int32)
         cnt = lib().demo_broad_phase(_p(state, C.c_double), _p(st, C.c_uint8), n, _p(pairs, C.c_int32), cap)
+        if cnt <= cap:
+            return pairs[:cnt].copy()
+        cap = int(cnt)
+
+
+def broad_partners(w, p):
+    """Candidate pairs involving particle p, (min, max), by brute force over j."""
+    state = _c(w.state, np.float64)
+    st = _c(w.is_static, np.uint8)
+    n = state.shape[1]
+    cap = 256
+    while True:
+        pairs = np.zeros((cap, 2), np.int32)
+        cnt = lib().demo_broad_partners(_p(state, C.c_double), _p(st, C.c_uint8), n, int(p),
+                                        _p(pairs, C.c_int32), cap)
         if cnt <= cap:
             return pairs[:cnt].copy()
         cap = int(cnt)

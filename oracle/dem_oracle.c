@@ -299,6 +299,38 @@ int64_t demo_broad_phase(const double *state, const uint8_t *is_static, int64_t 
   return cnt;
 }
 
+/* Candidate partners of one particle: every j != p (both static excluded)
+ * with the broad-phase predicate above, pairs written as (min, max) in
+ * increasing order of the partner.  Returns the number of partners. */
+int64_t demo_broad_partners(const double *state, const uint8_t *is_static, int64_t n, int64_t p,
+                            int32_t *pairs, int64_t cap) {
+  int64_t cnt = 0;
+  vec3 mp;
+  double rp;
+  swept_sphere(state, n, p, &mp, &rp);
+  for (int64_t j = 0; j < n; ++j) {
+    if (j == p) continue;
+    if (is_static && is_static[p] && is_static[j]) continue;
+    int64_t a = p < j ? p : j, b = p < j ? j : p;
+    vec3 ma, mb;
+    double ra, rb;
+    swept_sphere(state, n, a, &ma, &ra);
+    swept_sphere(state, n, b, &mb, &rb);
+    vec3 d = sub(ma, mb);
+    double rr = ra + rb;
+    if (dot(d, d) <= rr * rr) {
+      if (cnt < cap) {
+        pairs[2 * cnt] = (int32_t)a;
+        pairs[2 * cnt + 1] = (int32_t)b;
+      }
+      ++cnt;
+    }
+  }
+  (void)mp;
+  (void)rp;
+  return cnt;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Pair evaluation at one time: world vertices of both particles, then every
  * triangle pair in (a, b) lexicographic order. */

@@ -42,6 +42,11 @@ double demo_seg_seg(const double p1[3], const double q1[3], const double p2[3],
 int64_t demo_broad_phase(const double *state, const uint8_t *is_static, int64_t n,
                          int32_t *pairs, int64_t cap);
 
+/* Candidate partners of particle p alone (same predicate, brute force over
+ * j); pairs (min, max) in increasing partner order; returns the count. */
+int64_t demo_broad_partners(const double *state, const uint8_t *is_static, int64_t n, int64_t p,
+                            int32_t *pairs, int64_t cap);
+
 /* Narrow phase over m pairs at times t_eval[k] (NULL: the pair's start time).
  * Per pair: dmin, pa[3], pb[3], tri_ab[2] (indices local to each particle),
  * flag (dmin <= eps_pair).  Contacts (all triangle pairs with d <= eps_pair)

@@ -345,24 +345,85 @@ def uneven_meshes(seed: int = 0, n: int = 10000, box: float = 200.0, n_clusters:
     centres = rng.uniform(0, box, size=(n_clusters, 3))
     order = rng.permutation(n)
     pos = np.zeros((n, 3))
-    placed_c, placed_r = [], []
     n_cl = int(frac_clustered * n)
+    # overlap test against the placed spheres through a grid hash (cell =
+    # largest diameter, so every sphere that can overlap is in the 27 cells)
+    h = 2.0 * float(radius.max())
+    grid: dict = {}
     for rank, p in enumerate(order):
         for _ in range(1000):
             if rank < n_cl:
                 c = centres[rank % n_clusters] + rng.normal(0, sigma, size=3)
             else:
                 c = rng.uniform(0, box, size=3)
-            if placed_c:
-                d = np.linalg.norm(np.asarray(placed_c) - c, axis=1) - np.asarray(placed_r)
-                if np.min(d) < radius[p]:
-                    continue
+            k = np.floor(c / h).astype(int)
+            clash = False
+            for dx in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dz in (-1, 0, 1):
+                        for q in grid.get((k[0] + dx, k[1] + dy, k[2] + dz), ()):
+                            if np.linalg.norm(pos[q] - c) - radius[q] < radius[p]:
+                                clash = True
+                                break
+                        if clash:
+                            break
+                    if clash:
+                        break
+                if clash:
+                    break
+            if clash:
+                continue
             break
         pos[p] = c
-        placed_c.append(c)
-        placed_r.append(radius[p])
+        k = np.floor(c / h).astype(int)
+        grid.setdefault((k[0], k[1], k[2]), []).append(p)
     vel = rng.normal(0, 1.0, size=(n, 3))
     omega = rng.normal(0, 0.5, size=(n, 3))
     quat = random_quaternions(rng, n)
     return _assemble(f"uneven-{n}", meshes, mesh_of, pos, vel, quat, omega, 0.0, dt,
                      0.02 * radius, meta=dict(seed=seed))
+
+
+def lts_mixed_steps(seed: int = 0, n: int = 100_000, blob_frac: float = 0.2, n_blobs: int = 10,
+                    phi_blob: float = 0.55, phi_free: float = 0.02, jitter: float = 0.1,
+                    dt_range=(1e-5, 1e-2), eps: float = 0.02) -> Workload:
+    """Local time stepping with mixed step sizes: icospheres (320 triangles,
+    radius 1); ``blob_frac`` of them in dense blobs on an FCC lattice at volume
+    fraction ``phi_blob`` (nearest-neighbour spacing 2 r (0.7405/phi)^(1/3),
+    jitter +-``jitter``), the rest free on a jittered simple-cubic lattice at
+    volume fraction ``phi_free`` (non-overlapping by construction); each
+    particle's step log-uniform in ``dt_range``; v ~ N(0,1), w ~ N(0,0.5)."""
+    rng = np.random.default_rng(seed)
+    r = 1.0
+    mesh = icosphere(2, r)
+    n_blob = int(round(blob_frac * n))
+    n_free = n - n_blob
+    # free particles: simple-cubic lattice with large jitter
+    s_free = (4.0 * math.pi * r ** 3 / 3.0 / phi_free) ** (1.0 / 3.0)
+    side = int(math.ceil(n_free ** (1.0 / 3.0)))
+    g = np.arange(side) * s_free
+    F = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3)[:n_free]
+    amp = max(0.0, 0.5 * (s_free - 2 * r) - 0.05)
+    F = F + rng.uniform(-amp, amp, size=F.shape)
+    # blobs: FCC, placed along a line outside the free lattice
+    d_nn = 2 * r * (0.7405 / phi_blob) ** (1.0 / 3.0)
+    a = d_nn * math.sqrt(2.0)
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]]) * a
+    per = int(math.ceil(n_blob / n_blobs))
+    cells = int(math.ceil((per / 4.0) ** (1.0 / 3.0)))
+    c = np.arange(cells) * a
+    C3 = np.stack(np.meshgrid(c, c, c, indexing="ij"), axis=-1).reshape(-1, 3)
+    one = (C3[:, None, :] + basis[None, :, :]).reshape(-1, 3)[:per]
+    blobs = []
+    for b in range(n_blobs):
+        off = np.array([-(cells * a + 20.0) * (b + 1), 0.0, 0.0])
+        blobs.append(one + off)
+    B = np.concatenate(blobs)[:n_blob]
+    B = B + rng.uniform(-jitter, jitter, size=B.shape)
+    pos = np.concatenate([B, F])
+    vel = rng.normal(0.0, 1.0, size=(n, 3))
+    omega = rng.normal(0.0, 0.5, size=(n, 3))
+    quat = random_quaternions(rng, n)
+    dt = np.exp(rng.uniform(np.log(dt_range[0]), np.log(dt_range[1]), size=n))
+    return _assemble(f"lts-{n}", [mesh], [0] * n, pos, vel, quat, omega, 0.0, dt, eps,
+                     meta=dict(seed=seed, n_blob=n_blob, spacing_free=s_free, d_nn=d_nn))

@@ -1,0 +1,92 @@
+"""Full-size parity cases: the 10,000-particle uneven-mesh batch (icospheres of
+80/320/1280 triangles and convex hulls, radii 0.5-4, clustered) and the
+100,000-particle local-time-stepping layout (dense FCC blobs and free
+particles, per-particle steps log-uniform in [1e-5, 1e-2]).
+
+The GPU runs the whole step on all pairs; the oracle checks the candidate
+set (in full, or the partners of sampled particles where O(N^2) is too slow)
+and a seeded sample of pairs one by one.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_15417_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(dem, w, prec=0, max_pairs=1 << 20):
+    c = dem.Context(K=w.K, tol=w.tol, precision=prec, max_particles=w.n, max_pairs=max_pairs,
+                    max_contacts=1 << 22)
+    sc = dem.Scene.from_workload(w)
+    c.step_fused(sc)
+    c.check()
+    m = int(c.n_pairs.item())
+    nc = int(c.n_contacts.item())
+    out = dict(pairs=c.pairs[:m].cpu().numpy(), dmin=c.dmin[:m].cpu().numpy(), pa=c.pa[:m].cpu().numpy(),
+               pb=c.pb[:m].cpu().numpy(), tri_ab=c.tri_ab[:m].cpu().numpy(), flag=c.flag[:m].cpu().numpy(),
+               t_coll=c.t_coll[:m].cpu().numpy(), status=c.status[:m].cpu().numpy(),
+               ct_ab=c.ct_ab[:m].cpu().numpy(), contacts=c.contacts[:nc].cpu().numpy(),
+               ids=c.cluster_id[:w.n].cpu().numpy(), n_clusters=int(c.n_clusters.item()))
+    c.close()
+    return out
+
+
+def _check_sampled_pairs(w, g, idx):
+    sel = g["pairs"][idx]
+    on = oracle.narrow_phase(w, sel)
+    oc = oracle.collision_times(w, sel)
+    for key in ("flag", "tri_ab", "dmin", "pa", "pb"):
+        assert np.array_equal(g[key][idx], on[key]), key
+    assert np.array_equal(g["status"][idx], oc["status"])
+    assert np.array_equal(g["t_coll"][idx], oc["t_coll"])
+    assert np.array_equal(g["ct_ab"][idx], oc["tri_ab"])
+    # contact keys of the sampled pairs
+    gk = g["contacts"]
+    rows = np.isin(gk[:, 0], idx)
+    remap = {int(k): q for q, k in enumerate(idx)}
+    sub = gk[rows].copy()
+    sub[:, 0] = [remap[int(k)] for k in sub[:, 0]]
+    assert np.array_equal(sub, on["contacts"])
+    return oc
+
+
+def test_uneven_10k_full_size(dem):
+    w = W.uneven_meshes(0)
+    g = _run(dem, w)
+    o = oracle.broad_phase(w)
+    assert len(o) > 100
+    assert np.array_equal(g["pairs"], o)
+    ids, nc = oracle.clusters(w.n, o, w.is_static)
+    assert np.array_equal(g["ids"], ids) and g["n_clusters"] == nc
+    # sample: the costliest pairs (largest T_i * T_j) plus random ones
+    cnt = w.tri_counts()
+    cost = cnt[o[:, 0]] * cnt[o[:, 1]]
+    rng = np.random.default_rng(0)
+    idx = np.unique(np.concatenate([np.argsort(-cost)[:4], rng.choice(len(o), 16, replace=False)]))
+    _check_sampled_pairs(w, g, idx)
+
+
+def test_lts_100k_full_size(dem):
+    w = W.lts_mixed_steps(0)
+    g = _run(dem, w)
+    pairs = g["pairs"]
+    assert len(pairs) > 1000
+    assert np.all(pairs[:, 0] < pairs[:, 1])
+    assert np.all(np.diff(pairs[:, 0].astype(np.int64) * w.n + pairs[:, 1]) > 0)
+    # candidate partners of sampled particles (blob and free)
+    rng = np.random.default_rng(1)
+    blob = int(w.meta["n_blob"])
+    parts = np.concatenate([rng.choice(blob, 150, replace=False), blob + rng.choice(w.n - blob, 150, replace=False)])
+    for p in parts:
+        op = oracle.broad_partners(w, int(p))
+        gp = pairs[(pairs[:, 0] == p) | (pairs[:, 1] == p)]
+        assert np.array_equal(op, gp), p
+    # clusters of the candidate graph
+    ids, nc = oracle.clusters(w.n, pairs, w.is_static)
+    assert np.array_equal(g["ids"], ids) and g["n_clusters"] == nc
+    # sampled pairs, including every pair whose search bisected (status 2)
+    idx = np.unique(np.concatenate([np.where(g["status"] == 2)[0][:8], rng.choice(len(pairs), 16, replace=False)]))
+    oc = _check_sampled_pairs(w, g, idx)
+    assert set(np.unique(oc["status"])) >= {0, 1}

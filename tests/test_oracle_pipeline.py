@@ -240,3 +240,12 @@ def test_clusters_closed_form_graphs():
     # no edges: every particle its own cluster
     ids, nc = oracle.clusters(5, np.zeros((0, 2), np.int32))
     assert list(ids) == [0, 1, 2, 3, 4] and nc == 5
+
+
+def test_broad_partners_agree_with_full_brute_force():
+    w = W.dense_packing(0, nside=4)
+    w.is_static[3] = w.is_static[7] = 1
+    full = {tuple(p) for p in oracle.broad_phase(w)}
+    for p in range(w.n):
+        part = {tuple(x) for x in oracle.broad_partners(w, p)}
+        assert part == {q for q in full if p in q}
