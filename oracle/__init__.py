@@ -56,9 +56,10 @@ def lib():
             L.demo_closest_pt_tri.restype = C.c_double
             L.demo_seg_seg.argtypes = [dp, dp, dp, dp, dp, dp]
             L.demo_seg_seg.restype = C.c_double
-            L.demo_broad_phase.argtypes = [dp, u8p, C.c_int64, i32p, C.c_int64]
+            L.demo_broad_phase.argtypes = [dp, u8p, C.c_int64, i64p, fp, C.c_int64, i32p, C.c_int64]
             L.demo_broad_phase.restype = C.c_int64
-            L.demo_broad_partners.argtypes = [dp, u8p, C.c_int64, C.c_int64, i32p, C.c_int64]
+            L.demo_broad_partners.argtypes = [dp, u8p, C.c_int64, i64p, fp, C.c_int64, C.c_int64, i32p,
+                                              C.c_int64]
             L.demo_broad_partners.restype = C.c_int64
             L.demo_narrow_phase.argtypes = [dp, C.c_int64, i64p, fp, C.c_int64, i32p, C.c_int64,
                                             dp, dp, dp, dp, i32p, u8p, i32p, dp, C.c_int64, C.c_int]
@@ -117,29 +118,34 @@ def seg_seg(p1, q1, p2, q2):
     return d2, c1, c2
 
 
+def _geometry(w):
+    return (_c(w.state, np.float64), _c(w.is_static, np.uint8), _c(w.tri_off, np.int64),
+            _c(w.tris, np.float32))
+
+
 def broad_phase(w):
-    state = _c(w.state, np.float64)
-    st = _c(w.is_static, np.uint8)
+    """All candidate pairs (first, second), sorted; a static member is second."""
+    state, st, off, tris = _geometry(w)
     n = state.shape[1]
     cap = 1024
     while True:
         pairs = np.zeros((cap, 2), np.int32)
-        cnt = lib().demo_broad_phase(_p(state, C.c_double), _p(st, C.c_uint8), n, _p(pairs, C.c_int32), cap)
+        cnt = lib().demo_broad_phase(_p(state, C.c_double), _p(st, C.c_uint8), n, _p(off, C.c_int64),
+                                     _p(tris, C.c_float), tris.shape[1], _p(pairs, C.c_int32), cap)
         if cnt <= cap:
             return pairs[:cnt].copy()
         cap = int(cnt)
 
 
 def broad_partners(w, p):
-    """Candidate pairs involving particle p, (min, max), by brute force over j."""
-    state = _c(w.state, np.float64)
-    st = _c(w.is_static, np.uint8)
+    """The candidate pairs that contain particle p, by brute force over the others."""
+    state, st, off, tris = _geometry(w)
     n = state.shape[1]
     cap = 256
     while True:
         pairs = np.zeros((cap, 2), np.int32)
-        cnt = lib().demo_broad_partners(_p(state, C.c_double), _p(st, C.c_uint8), n, int(p),
-                                        _p(pairs, C.c_int32), cap)
+        cnt = lib().demo_broad_partners(_p(state, C.c_double), _p(st, C.c_uint8), n, _p(off, C.c_int64),
+                                        _p(tris, C.c_float), tris.shape[1], int(p), _p(pairs, C.c_int32), cap)
         if cnt <= cap:
             return pairs[:cnt].copy()
         cap = int(cnt)

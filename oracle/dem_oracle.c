@@ -260,78 +260,6 @@ double demo_seg_seg(const double p1[3], const double q1[3], const double p2[3], 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Broad phase (paper Section 3: free-flight extrapolation of each particle
- * over its own step, bounding spheres that cover the particle and its halo,
- * symmetric pairwise overlap test).  Swept sphere of p over [t_cur, t_cur+dt]:
- * centre m = x + v (dt/2), radius rho = (radius + eps) + |v| (dt/2).
- * Candidate iff |m_i - m_j|^2 <= (rho_i + rho_j)^2.  Pairs of two static
- * particles are never candidates.  Brute force over all i < j. */
-static void swept_sphere(const double *s, int64_t n, int64_t p, vec3 *m, double *rho) {
-  double hdt = s[FDT * n + p] * 0.5;
-  vec3 v = mk(s[FVX * n + p], s[FVY * n + p], s[FVZ * n + p]);
-  *m = mk(s[FX * n + p] + v.x * hdt, s[FY * n + p] + v.y * hdt, s[FZ * n + p] + v.z * hdt);
-  *rho = (s[FRADIUS * n + p] + s[FEPS * n + p]) + sqrt(dot(v, v)) * hdt;
-}
-
-int64_t demo_broad_phase(const double *state, const uint8_t *is_static, int64_t n, int32_t *pairs,
-                         int64_t cap) {
-  int64_t cnt = 0;
-  for (int64_t i = 0; i < n; ++i) {
-    vec3 mi;
-    double ri;
-    swept_sphere(state, n, i, &mi, &ri);
-    for (int64_t j = i + 1; j < n; ++j) {
-      if (is_static && is_static[i] && is_static[j]) continue;
-      vec3 mj;
-      double rj;
-      swept_sphere(state, n, j, &mj, &rj);
-      vec3 d = sub(mi, mj);
-      double rr = ri + rj;
-      if (dot(d, d) <= rr * rr) {
-        if (cnt < cap) {
-          pairs[2 * cnt] = (int32_t)i;
-          pairs[2 * cnt + 1] = (int32_t)j;
-        }
-        ++cnt;
-      }
-    }
-  }
-  return cnt;
-}
-
-/* Candidate partners of one particle: every j != p (both static excluded)
- * with the broad-phase predicate above, pairs written as (min, max) in
- * increasing order of the partner.  Returns the number of partners. */
-int64_t demo_broad_partners(const double *state, const uint8_t *is_static, int64_t n, int64_t p,
-                            int32_t *pairs, int64_t cap) {
-  int64_t cnt = 0;
-  vec3 mp;
-  double rp;
-  swept_sphere(state, n, p, &mp, &rp);
-  for (int64_t j = 0; j < n; ++j) {
-    if (j == p) continue;
-    if (is_static && is_static[p] && is_static[j]) continue;
-    int64_t a = p < j ? p : j, b = p < j ? j : p;
-    vec3 ma, mb;
-    double ra, rb;
-    swept_sphere(state, n, a, &ma, &ra);
-    swept_sphere(state, n, b, &mb, &rb);
-    vec3 d = sub(ma, mb);
-    double rr = ra + rb;
-    if (dot(d, d) <= rr * rr) {
-      if (cnt < cap) {
-        pairs[2 * cnt] = (int32_t)a;
-        pairs[2 * cnt + 1] = (int32_t)b;
-      }
-      ++cnt;
-    }
-  }
-  (void)mp;
-  (void)rp;
-  return cnt;
-}
-
-/* ------------------------------------------------------------------------ */
 /* Pair evaluation at one time: world vertices of both particles, then every
  * triangle pair in (a, b) lexicographic order. */
 
@@ -357,6 +285,154 @@ static vec3 *world_verts(const double *state, int64_t n, const int64_t *tri_off,
       w[3 * k + s] = to_world(R, X, mk((double)v[0], (double)v[1], (double)v[2]));
     }
   return w;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Broad phase (paper Section 3: free-flight extrapolation of each particle
+ * over its own step, bounding volumes that cover the particle and its halo,
+ * a symmetric pairwise overlap test; static geometry treated apart).
+ *
+ * Swept sphere of a moving particle p over [t_cur, t_cur+dt]: centre
+ * m = x + v (dt/2), radius rho = (radius + eps) + |v| (dt/2).  Two moving
+ * particles i < j are a candidate iff |m_i - m_j|^2 <= (rho_i + rho_j)^2.
+ *
+ * A static particle s (paper Section 3, "Static geometric objects"; the
+ * axis-aligned boxes of Check 1) is represented by the box of its world
+ * vertices at t_cur, widened by eps_s on every side: a floor made of a few
+ * huge triangles would otherwise have a bounding sphere that reaches far
+ * above it.  A moving p and a static s are a candidate iff p's swept sphere
+ * meets that box, and the pair is written (p, s): the static particle is
+ * always second.  Two static particles never pair.  Output order: by first
+ * member, then by second.  Brute force over all pairs. */
+static void swept_sphere(const double *s, int64_t n, int64_t p, vec3 *m, double *rho) {
+  double hdt = s[FDT * n + p] * 0.5;
+  vec3 v = mk(s[FVX * n + p], s[FVY * n + p], s[FVZ * n + p]);
+  *m = mk(s[FX * n + p] + v.x * hdt, s[FY * n + p] + v.y * hdt, s[FZ * n + p] + v.z * hdt);
+  *rho = (s[FRADIUS * n + p] + s[FEPS * n + p]) + sqrt(dot(v, v)) * hdt;
+}
+
+static int spheres_meet(vec3 ma, double ra, vec3 mb, double rb) {
+  vec3 d = sub(ma, mb);
+  double rr = ra + rb;
+  return dot(d, d) <= rr * rr;
+}
+
+/* box [lo, hi] of static particle s: componentwise extremes of its world
+ * vertices at t_cur, then lo - eps_s and hi + eps_s (empty mesh: +inf/-inf,
+ * which meets no sphere) */
+static void static_box(const double *state, int64_t n, const int64_t *tri_off, const float *tris,
+                       int64_t n_tris, int64_t s, vec3 *lo, vec3 *hi) {
+  vec3 *w = world_verts(state, n, tri_off, tris, n_tris, s, state[FTCUR * n + s]);
+  int64_t nv = 3 * (tri_off[s + 1] - tri_off[s]);
+  vec3 l = mk(INFINITY, INFINITY, INFINITY), h = mk(-INFINITY, -INFINITY, -INFINITY);
+  for (int64_t k = 0; k < nv; ++k) {
+    l = mk(fmin(l.x, w[k].x), fmin(l.y, w[k].y), fmin(l.z, w[k].z));
+    h = mk(fmax(h.x, w[k].x), fmax(h.y, w[k].y), fmax(h.z, w[k].z));
+  }
+  free(w);
+  double e = state[FEPS * n + s];
+  *lo = mk(l.x - e, l.y - e, l.z - e);
+  *hi = mk(h.x + e, h.y + e, h.z + e);
+}
+
+/* distance of coordinate m outside [lo, hi] (0 inside) */
+static double gap(double m, double lo, double hi) { return m < lo ? lo - m : (m > hi ? m - hi : 0.0); }
+
+static int sphere_meets_box(vec3 m, double rho, vec3 lo, vec3 hi) {
+  vec3 g = mk(gap(m.x, lo.x, hi.x), gap(m.y, lo.y, hi.y), gap(m.z, lo.z, hi.z));
+  return dot(g, g) <= rho * rho;
+}
+
+static int is_st(const uint8_t *is_static, int64_t p) { return is_static && is_static[p]; }
+
+static void emit(int32_t *pairs, int64_t cap, int64_t *cnt, int64_t a, int64_t b) {
+  if (*cnt < cap) {
+    pairs[2 * *cnt] = (int32_t)a;
+    pairs[2 * *cnt + 1] = (int32_t)b;
+  }
+  ++*cnt;
+}
+
+int64_t demo_broad_phase(const double *state, const uint8_t *is_static, int64_t n, const int64_t *tri_off,
+                         const float *tris, int64_t n_tris, int32_t *pairs, int64_t cap) {
+  vec3 *m = (vec3 *)malloc(sizeof(vec3) * (size_t)(n > 0 ? n : 1));
+  vec3 *lo = (vec3 *)malloc(sizeof(vec3) * (size_t)(n > 0 ? n : 1));
+  vec3 *hi = (vec3 *)malloc(sizeof(vec3) * (size_t)(n > 0 ? n : 1));
+  double *rho = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  for (int64_t p = 0; p < n; ++p) {
+    swept_sphere(state, n, p, &m[p], &rho[p]);
+    if (is_st(is_static, p)) static_box(state, n, tri_off, tris, n_tris, p, &lo[p], &hi[p]);
+  }
+  int64_t cnt = 0;
+  for (int64_t a = 0; a < n; ++a) {
+    if (is_st(is_static, a)) continue; /* a static particle is never first */
+    for (int64_t b = 0; b < n; ++b) {
+      if (b == a) continue;
+      if (is_st(is_static, b)) {
+        if (sphere_meets_box(m[a], rho[a], lo[b], hi[b])) emit(pairs, cap, &cnt, a, b);
+      } else if (b > a && spheres_meet(m[a], rho[a], m[b], rho[b])) {
+        emit(pairs, cap, &cnt, a, b);
+      }
+    }
+  }
+  free(m);
+  free(lo);
+  free(hi);
+  free(rho);
+  return cnt;
+}
+
+static int cmp_pair(const void *x, const void *y) {
+  const int32_t *a = (const int32_t *)x, *b = (const int32_t *)y;
+  if (a[0] != b[0]) return a[0] < b[0] ? -1 : 1;
+  return a[1] < b[1] ? -1 : (a[1] > b[1] ? 1 : 0);
+}
+
+/* Candidate pairs that contain particle p (same predicates and pair order as
+ * demo_broad_phase), brute force over the other particles, then sorted by
+ * (first, second).  Returns the number of pairs; writes at most cap. */
+int64_t demo_broad_partners(const double *state, const uint8_t *is_static, int64_t n, const int64_t *tri_off,
+                            const float *tris, int64_t n_tris, int64_t p, int32_t *pairs, int64_t cap) {
+  int64_t cnt = 0, room = 64;
+  int32_t *all = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)room);
+  vec3 mp, lp, hp;
+  double rp;
+  swept_sphere(state, n, p, &mp, &rp);
+  if (is_st(is_static, p)) static_box(state, n, tri_off, tris, n_tris, p, &lp, &hp);
+  for (int64_t q = 0; q < n; ++q) {
+    if (q == p || (is_st(is_static, p) && is_st(is_static, q))) continue;
+    vec3 mq, lq, hq;
+    double rq;
+    swept_sphere(state, n, q, &mq, &rq);
+    int64_t a, b;
+    int hit;
+    if (is_st(is_static, p)) {
+      hit = sphere_meets_box(mq, rq, lp, hp);
+      a = q;
+      b = p;
+    } else if (is_st(is_static, q)) {
+      static_box(state, n, tri_off, tris, n_tris, q, &lq, &hq);
+      hit = sphere_meets_box(mp, rp, lq, hq);
+      a = p;
+      b = q;
+    } else {
+      hit = p < q ? spheres_meet(mp, rp, mq, rq) : spheres_meet(mq, rq, mp, rp);
+      a = p < q ? p : q;
+      b = p < q ? q : p;
+    }
+    if (!hit) continue;
+    if (cnt == room) {
+      room *= 2;
+      all = (int32_t *)realloc(all, sizeof(int32_t) * 2 * (size_t)room);
+    }
+    all[2 * cnt] = (int32_t)a;
+    all[2 * cnt + 1] = (int32_t)b;
+    ++cnt;
+  }
+  qsort(all, (size_t)cnt, 2 * sizeof(int32_t), cmp_pair);
+  memcpy(pairs, all, sizeof(int32_t) * 2 * (size_t)(cnt < cap ? cnt : cap));
+  free(all);
+  return cnt;
 }
 
 static void push_contact(pair_eval *e, int32_t a, int32_t b, double d, vec3 pa, vec3 pb) {

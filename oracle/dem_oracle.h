@@ -37,14 +37,20 @@ double demo_closest_pt_tri(const double p[3], const double T[9], double q[3]);
 double demo_seg_seg(const double p1[3], const double q1[3], const double p2[3],
                     const double q2[3], double c1[3], double c2[3]);
 
-/* Broad phase: all pairs i<j whose swept halo spheres overlap.  Writes up to
- * cap pairs (i,j interleaved) in (i,j) order; returns the number of pairs. */
+/* Broad phase: every candidate pair.  Two moving particles i < j pair when
+ * their swept halo spheres overlap; a moving particle p and a static
+ * particle s pair, written (p, s), when p's swept sphere meets the box of
+ * s's world vertices at t_cur widened by eps_s; two static particles never
+ * pair.  Pairs sorted by (first, second); writes up to cap pairs (first,
+ * second interleaved); returns the number of pairs. */
 int64_t demo_broad_phase(const double *state, const uint8_t *is_static, int64_t n,
+                         const int64_t *tri_off, const float *tris, int64_t n_tris,
                          int32_t *pairs, int64_t cap);
 
-/* Candidate partners of particle p alone (same predicate, brute force over
- * j); pairs (min, max) in increasing partner order; returns the count. */
-int64_t demo_broad_partners(const double *state, const uint8_t *is_static, int64_t n, int64_t p,
+/* The candidate pairs that contain particle p alone (same predicates and
+ * order, brute force over the other particles); returns the count. */
+int64_t demo_broad_partners(const double *state, const uint8_t *is_static, int64_t n,
+                            const int64_t *tri_off, const float *tris, int64_t n_tris, int64_t p,
                             int32_t *pairs, int64_t cap);
 
 /* Narrow phase over m pairs at times t_eval[k] (NULL: the pair's start time).

@@ -149,19 +149,35 @@ def convex_hull_mesh(rng: np.random.Generator, n_points: int, radius: float = 1.
     return V[F[key]]
 
 
+def _morton2(ix: np.ndarray, iy: np.ndarray) -> np.ndarray:
+    """Interleave the bits of two non-negative integers below 2^16 (Z-order)."""
+    def spread(v):
+        v = v.astype(np.uint64) & np.uint64(0xFFFF)
+        v = (v | (v << np.uint64(8))) & np.uint64(0x00FF00FF)
+        v = (v | (v << np.uint64(4))) & np.uint64(0x0F0F0F0F)
+        v = (v | (v << np.uint64(2))) & np.uint64(0x33333333)
+        v = (v | (v << np.uint64(1))) & np.uint64(0x55555555)
+        return v
+    return spread(ix) | (spread(iy) << np.uint64(1))
+
+
 def floor_grid(nq: int, size: float, z: float = 0.0) -> np.ndarray:
     """Static floor: an ``nq`` x ``nq`` grid of quads (2 triangles each),
-    centred at the origin of its body frame, spanning ``size``."""
+    centred at the origin of its body frame, spanning ``size``.  Quads are in
+    Z-order (Morton order) of their grid cell and the two triangles of a quad
+    are adjacent, so every run of consecutive triangles covers a compact patch
+    of the floor."""
     xs = np.linspace(-size / 2, size / 2, nq + 1)
     X, Y = np.meshgrid(xs, xs, indexing="ij")
     P = np.stack([X, Y, np.full_like(X, z)], axis=-1).astype(np.float32)
-    a = P[:-1, :-1].reshape(-1, 3)
-    b = P[1:, :-1].reshape(-1, 3)
-    c = P[1:, 1:].reshape(-1, 3)
-    d = P[:-1, 1:].reshape(-1, 3)
+    ix, iy = np.meshgrid(np.arange(nq), np.arange(nq), indexing="ij")
+    ix, iy = ix.ravel(), iy.ravel()
+    order = np.argsort(_morton2(ix, iy), kind="stable")
+    ix, iy = ix[order], iy[order]
+    a, b, c, d = P[ix, iy], P[ix + 1, iy], P[ix + 1, iy + 1], P[ix, iy + 1]
     t1 = np.stack([a, b, c], axis=1)
     t2 = np.stack([a, c, d], axis=1)
-    return np.concatenate([t1, t2], axis=0)
+    return np.stack([t1, t2], axis=1).reshape(-1, 3, 3)
 
 
 def mesh_radius(soup: np.ndarray) -> float:
@@ -186,15 +202,25 @@ def random_quaternions(rng: np.random.Generator, n: int) -> np.ndarray:
 def _assemble(name, meshes, mesh_of, pos, vel, quat, omega, t_cur, dt, eps, is_static=None,
               K=8, tol=1e-3, meta=None) -> Workload:
     n = len(mesh_of)
-    radii = [mesh_radius(m) for m in meshes]
-    counts = np.array([len(meshes[k]) for k in mesh_of], np.int64)
+    mesh_of = np.asarray(mesh_of, np.int64).reshape(n)
+    mesh_len = np.array([len(m) for m in meshes], np.int64)
+    radii = np.array([mesh_radius(m) for m in meshes], np.float64)
+    counts = mesh_len[mesh_of]
     off = np.zeros(n + 1, np.int64)
     off[1:] = np.cumsum(counts)
     tris = np.zeros((3, int(off[-1]), 4), np.float32)
-    for p, k in enumerate(mesh_of):
-        m = meshes[k]
+    M = np.concatenate([np.asarray(m, np.float32).reshape(-1, 3, 3) for m in meshes]) if meshes else \
+        np.zeros((0, 3, 3), np.float32)
+    mo = np.zeros(len(meshes) + 1, np.int64)
+    mo[1:] = np.cumsum(mesh_len)
+    chunk = 1 << 16  # particles per block of the copy (bounds temporaries)
+    for p0 in range(0, n, chunk):
+        p1 = min(n, p0 + chunk)
+        c = counts[p0:p1]
+        local = np.arange(int(off[p1] - off[p0]), dtype=np.int64) - np.repeat(off[p0:p1] - off[p0], c)
+        g = np.repeat(mo[mesh_of[p0:p1]], c) + local
         for s in range(3):
-            tris[s, off[p]:off[p + 1], :3] = m[:, s, :]
+            tris[s, off[p0]:off[p1], :3] = M[g, s, :]
     st = np.zeros((DEM_NFIELDS, n), np.float64)
     st[F_X:F_Z + 1] = np.asarray(pos, np.float64).T
     st[F_VX:F_VZ + 1] = np.asarray(vel, np.float64).T
@@ -203,7 +229,7 @@ def _assemble(name, meshes, mesh_of, pos, vel, quat, omega, t_cur, dt, eps, is_s
     st[F_TCUR] = t_cur
     st[F_DT] = dt
     st[F_EPS] = eps
-    st[F_RADIUS] = [radii[k] for k in mesh_of]
+    st[F_RADIUS] = radii[mesh_of] if n else 0.0
     if is_static is None:
         is_static = np.zeros(n, np.uint8)
     return Workload(name, st, np.asarray(is_static, np.uint8), off, tris, K, tol, meta or {})
@@ -427,3 +453,104 @@ def lts_mixed_steps(seed: int = 0, n: int = 100_000, blob_frac: float = 0.2, n_b
     dt = np.exp(rng.uniform(np.log(dt_range[0]), np.log(dt_range[1]), size=n))
     return _assemble(f"lts-{n}", [mesh], [0] * n, pos, vel, quat, omega, 0.0, dt, eps,
                      meta=dict(seed=seed, n_blob=n_blob, spacing_free=s_free, d_nn=d_nn))
+
+
+def floor_scene(seed: int = 0, n_side: int = 6, nq: int = 40, size: float = 24.0, eps: float = 0.02,
+                dt: float = 1e-3) -> Workload:
+    """Static geometry: particle 0 is a static floor (``nq`` x ``nq`` quads,
+    Morton order, z = 0, more than one 320-triangle tile), the particle in the
+    middle of the index range is a static icosphere post standing on it, and
+    the others are moving icospheres (80 or 320 triangles, radius 1) over an
+    ``n_side`` x ``n_side`` grid of the floor, one of four kinds at random:
+    resting within the halo sum of the floor, falling onto it during the step,
+    sliding just above it, or clear of it (well above the floor's box but inside
+    its bounding sphere).  Random rotations, w ~ N(0, 0.5)."""
+    rng = np.random.default_rng(seed)
+    floor = floor_grid(nq, size)
+    small, big = icosphere(1), icosphere(2)
+    R = max(mesh_radius(small), mesh_radius(big))
+    spacing = size / (n_side + 1)
+    g = (np.arange(n_side) - (n_side - 1) / 2) * spacing
+    XY = np.stack(np.meshgrid(g, g, indexing="ij"), axis=-1).reshape(-1, 2)
+    m = len(XY)
+    kind = rng.integers(0, 4, size=m)
+    z = np.empty(m)
+    vel = rng.normal(0.0, 0.2, size=(m, 3))
+    eps_pair = 2 * eps
+    for q in range(m):
+        if kind[q] == 0:    # resting: lowest point within the halo sum
+            z[q] = R + rng.uniform(0.1, 0.9) * eps_pair
+        elif kind[q] == 1:  # falling: reaches the floor part way through the step
+            gap = rng.uniform(0.05, 0.3)
+            z[q] = R + eps_pair + gap
+            vel[q, 2] = -gap / (dt * rng.uniform(0.2, 0.9))
+        elif kind[q] == 2:  # sliding just above the halo sum
+            z[q] = R + eps_pair + rng.uniform(0.002, 0.02)
+            vel[q, :2] = rng.normal(0.0, 20.0, size=2)
+            vel[q, 2] = 0.0
+        else:               # clear: far above the box, inside the bounding sphere
+            z[q] = R + rng.uniform(3.0, 8.0)
+    pos = np.concatenate([XY, z[:, None]], axis=1)
+    post_at = (m + 2) // 2
+    # particle list: floor, first half of the spheres, post, second half
+    n = m + 2
+    mesh_of = np.empty(n, np.int64)
+    mesh_of[0] = 0
+    kinds_mesh = rng.integers(1, 3, size=m)
+    others = [p for p in range(n) if p not in (0, post_at)]
+    mesh_of[others] = kinds_mesh
+    mesh_of[post_at] = 2
+    P = np.zeros((n, 3))
+    V = np.zeros((n, 3))
+    W = np.zeros((n, 3))
+    Q = np.zeros((n, 4))
+    Q[:, 0] = 1.0
+    P[others] = pos
+    V[others] = vel
+    W[others] = rng.normal(0.0, 0.5, size=(m, 3))
+    Q[others] = random_quaternions(rng, m)
+    # the post sits on the floor between two grid points, touching its neighbours' halos
+    P[post_at] = (0.5 * spacing, 0.5 * spacing, R)
+    st = np.zeros(n, np.uint8)
+    st[0] = st[post_at] = 1
+    return _assemble(f"floor-scene-{n}", [floor, small, big], mesh_of, P, V, Q, W, 0.0, dt, eps,
+                     is_static=st, meta=dict(seed=seed, kind=kind.tolist(), post=post_at))
+
+
+def settling_column(seed: int = 0, nside: int = 100, spacing: float = 2.2, jitter: float = 0.1,
+                    nq: int = 316, eps: float = 0.01, dt: float = 1e-3, vsig: float = 0.1,
+                    wsig: float = 0.1, lift: float = 0.005) -> Workload:
+    """Throughput scale: a settling column of nside^3 icospheres of radius 1,
+    half with 80 and half with 320 triangles (types shuffled), on a simple-cubic
+    lattice of spacing ``spacing``, jitter uniform in +-``jitter`` per axis
+    (horizontal only in the bottom layer, whose lowest points stay ``lift``
+    above the floor), over a static floor of ``nq`` x ``nq`` quads (Morton
+    order) spanning the column's footprint.  The floor is the last particle.
+    v ~ N(0, vsig), w ~ N(0, wsig), dt = 1e-3, eps = 0.01.  ``meta['gravity']``
+    is the acceleration a stepping loop applies between steps (free flight
+    within a step is at constant velocity)."""
+    rng = np.random.default_rng(seed)
+    small, big = icosphere(1), icosphere(2)
+    R = max(mesh_radius(small), mesh_radius(big))
+    n = nside ** 3
+    g = np.arange(nside) * spacing
+    IX, IY, IZ = np.meshgrid(g, g, g, indexing="ij")
+    P = np.stack([IX, IY, IZ], axis=-1).reshape(-1, 3)
+    J = rng.uniform(-jitter, jitter, size=P.shape)
+    bottom = P[:, 2] == 0.0
+    J[bottom, 2] = 0.0
+    P = P + J
+    P[:, 2] += R + lift
+    foot = (nside - 1) * spacing
+    size = foot + 2 * (R + 2 * jitter + 1.0)
+    floor = floor_grid(nq, size)
+    types = rng.permutation(np.arange(n) % 2) + 1
+    mesh_of = np.concatenate([types, [0]])
+    pos = np.concatenate([P, [[foot / 2, foot / 2, 0.0]]])
+    vel = np.concatenate([rng.normal(0.0, vsig, size=(n, 3)), np.zeros((1, 3))])
+    omega = np.concatenate([rng.normal(0.0, wsig, size=(n, 3)), np.zeros((1, 3))])
+    quat = np.concatenate([random_quaternions(rng, n), [[1.0, 0.0, 0.0, 0.0]]])
+    st = np.zeros(n + 1, np.uint8)
+    st[n] = 1
+    return _assemble(f"settling-column-{n}", [floor, small, big], mesh_of, pos, vel, quat, omega, 0.0, dt,
+                     eps, is_static=st, meta=dict(seed=seed, gravity=(0.0, 0.0, -9.81), floor=n))

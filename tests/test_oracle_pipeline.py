@@ -72,6 +72,76 @@ def test_broad_phase_skips_static_static():
     assert (0, 1) not in {tuple(p) for p in pairs}
 
 
+def _static_pair(static_tris, quat, shift, at, rho=1.5, eps=0.25):
+    """A static mesh (particle 0) and a resting icosphere (particle 1) whose
+    swept sphere has radius ``rho`` (radius field overridden)."""
+    w = W._assemble("static-box", [np.asarray(static_tris, np.float32), W.icosphere(1)], [0, 1],
+                    [shift, at], np.zeros((2, 3)), [quat, (1, 0, 0, 0)], np.zeros((2, 3)), 0.0, 1e-3,
+                    eps, is_static=[1, 0])
+    w.state[W.F_RADIUS, 1] = rho - eps
+    return w
+
+
+def test_broad_phase_static_box_closed_form():
+    """A static object pairs with a moving particle exactly when the swept
+    sphere reaches the box of its world vertices widened by eps_s (Section 3,
+    static geometry and axis-aligned boxes).  Dyadic values make touching
+    exact: the triangle (0,0,0), (4,0,0), (0,4,0) turned by 180 degrees about
+    z and moved by (1,2,3) has the world box [-3,1] x [-2,2] x [3,3]; widened
+    by 0.25 and met by a sphere of radius 1.5 on a face, beyond an edge and
+    off a corner (gaps 1, 1, 0.5).  The static particle is written second."""
+    tri = [[[0, 0, 0], [4, 0, 0], [0, 4, 0]]]
+    turn, shift = (0.0, 0.0, 0.0, 1.0), (1.0, 2.0, 3.0)
+    tiny = 2.0 ** -30
+    cases = [((1.0 + 0.25 + 1.5, 0.0, 3.0), 1), ((1.0 + 0.25 + 1.5 + tiny, 0.0, 3.0), 0),
+             ((-3.0 - 0.25 - 1.5, 0.0, 3.0), 1), ((-3.0 - 0.25 - 1.5 - tiny, 0.0, 3.0), 0),
+             ((0.0, 0.0, 3.0 + 0.25 + 1.5), 1), ((0.0, 0.0, 3.0 - 0.25 - 1.5 - tiny), 0),
+             ((1.25 + 1.0, 2.25 + 1.0, 3.25 + 0.5), 1), ((1.25 + 1.0 + tiny, 2.25 + 1.0, 3.25 + 0.5), 0)]
+    for at, expect in cases:
+        pairs = oracle.broad_phase(_static_pair(tri, turn, shift, at))
+        assert pairs.tolist() == ([[1, 0]] if expect else []), at
+
+
+def test_broad_phase_static_box_not_sphere():
+    """Particles well above a floor, inside the floor's bounding sphere but
+    outside its widened box, are not candidates; those that reach the box are,
+    and every pair with a static member has it second."""
+    w = W.floor_scene(0)
+    pairs = oracle.broad_phase(w)
+    st = w.is_static.astype(bool)
+    assert not st[pairs[:, 0]].any()
+    floor_partners = set(pairs[pairs[:, 1] == 0, 0].tolist())
+    kinds = np.array(w.meta["kind"])
+    movers = [p for p in range(w.n) if not st[p]]
+    clear = [p for p, k in zip(movers, kinds) if k == 3]
+    resting = [p for p, k in zip(movers, kinds) if k == 0]
+    R0 = w.state[W.F_RADIUS, 0]
+    assert clear and resting
+    for p in clear:
+        assert p not in floor_partners
+        assert np.linalg.norm(w.state[0:3, p] - w.state[0:3, 0]) < R0  # the sphere test would pair it
+    assert set(resting) <= floor_partners
+    # output sorted by (first, second)
+    key = pairs[:, 0].astype(np.int64) * w.n + pairs[:, 1]
+    assert np.all(np.diff(key) > 0)
+
+
+def test_broad_phase_static_is_conservative():
+    """Every (moving, static) pair whose meshes come within the halo sum at
+    some time of the step is a candidate."""
+    for seed in range(3):
+        w = W.floor_scene(seed)
+        cand = {tuple(p) for p in oracle.broad_phase(w)}
+        statics = np.where(w.is_static)[0]
+        allp = np.array([(p, s) for p in range(w.n) if not w.is_static[p] for s in statics], np.int32)
+        hit = set()
+        for t in np.linspace(0.0, 1e-3, 6):
+            r = oracle.narrow_phase(w, allp, t_eval=np.full(len(allp), t), n_threads=8)
+            hit |= {tuple(p) for p, f in zip(allp, r["flag"]) if f}
+        assert len(hit) > 5
+        assert hit <= cand
+
+
 # ----------------------------------------------------------------------------- narrow phase
 
 def test_narrow_contacts_are_exactly_the_close_triangle_pairs():
@@ -243,9 +313,11 @@ def test_clusters_closed_form_graphs():
 
 
 def test_broad_partners_agree_with_full_brute_force():
-    w = W.dense_packing(0, nside=4)
-    w.is_static[3] = w.is_static[7] = 1
-    full = {tuple(p) for p in oracle.broad_phase(w)}
-    for p in range(w.n):
-        part = {tuple(x) for x in oracle.broad_partners(w, p)}
-        assert part == {q for q in full if p in q}
+    for w in (W.dense_packing(0, nside=4), W.floor_scene(1)):
+        if not w.is_static.any():
+            w.is_static[3] = w.is_static[7] = 1
+        full = oracle.broad_phase(w)
+        for p in range(w.n):
+            part = oracle.broad_partners(w, p)
+            mine = full[(full[:, 0] == p) | (full[:, 1] == p)]
+            assert np.array_equal(part, mine), p
