@@ -98,6 +98,8 @@ typedef struct {
   int64_t max_particles; /* capacity: particles per call (0 -> 65536) */
   int64_t max_pairs;     /* capacity: pairs / edges per call (0 -> 1<<20) */
   int64_t max_contacts;  /* capacity: contact staging per narrow-phase call (0 -> 1<<20) */
+  int64_t max_triangles; /* capacity: n_tris per call (0 -> 1280 * max_particles); sizes the
+                            bounding spheres of the 320-triangle tiles of large meshes */
 } dem_config;
 
 /* Outputs of dem_narrow_phase.  Per pair k (M = pair count):
@@ -154,15 +156,21 @@ const char *dem_last_error(const dem_ctx *ctx);
 
 /* Broad phase (paper Section 3, "Broad phase collision detection to identify
  * clusters", and the pair interval of Eq. "max time span between two
- * particles"): the candidate pairs c(i, j) = true.  Each particle is extruded
- * over its own step in free flight: swept sphere centre m = x + v dt/2,
- * radius rho = (radius + eps) + |v| dt/2; (i, j) is a candidate iff
- * |m_i - m_j|^2 <= (rho_i + rho_j)^2 (binary64).  Pairs of two static
- * particles are never candidates.  Uses a uniform hashed cell grid of cell
- * size >= 2 max rho; the result equals the brute-force set.
- * Output: pairs [cap][2] in (i, j) order, *n_pairs (device) = number of
- * candidates; if it exceeds cap only cap are written and dem_check() returns
- * DEM_ERR_CAPACITY. */
+ * particles"): the candidate pairs c(i, j) = true.  Each moving particle is
+ * extruded over its own step in free flight: swept sphere centre
+ * m = x + v dt/2, radius rho = (radius + eps) + |v| dt/2; two moving
+ * particles i < j are a candidate iff |m_i - m_j|^2 <= (rho_i + rho_j)^2
+ * (binary64).  A static particle s (Section 3, "Static geometric objects")
+ * is represented by the axis-aligned box of its world vertices at its t_cur,
+ * widened by eps_s; a moving p and s are a candidate iff p's swept sphere
+ * meets that box (binary64), written (p, s): the static member is always
+ * second.  Two static particles never pair.  Moving particles are binned in a
+ * uniform hashed cell grid of cell size >= 2 max rho (over moving particles)
+ * and every moving particle tests every static box; the result equals the
+ * brute-force set.
+ * Output: pairs [cap][2] sorted by (first, second), *n_pairs (device) =
+ * number of candidates; if it exceeds cap only cap are written and
+ * dem_check() returns DEM_ERR_CAPACITY. */
 dem_status dem_build_candidates(dem_ctx *ctx, const dem_particles *P, int32_t *pairs, int64_t cap,
                                 int64_t *n_pairs, void *stream);
 
@@ -221,7 +229,7 @@ dem_status dem_clusters(dem_ctx *ctx, int64_t n, const int32_t *edges, int64_t m
  * allocation could block or fail.  Same predicate, output and order as
  * dem_build_candidates.  Scratch lives in a fixed device array inside the
  * library, sized for at most DEM_NOALLOC_MAX_PARTICLES particles (about
- * 1.7 MB, held on every GPU that loads the library until the process exits);
+ * 3.9 MB, held on every GPU that loads the library until the process exits);
  * larger inputs return DEM_ERR_CAPACITY without launching anything.  No
  * cudaMalloc / cudaFree is called.  The first call on each device looks up
  * the array's device address (cudaGetSymbolAddress, with that device

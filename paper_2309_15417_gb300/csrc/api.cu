@@ -54,6 +54,7 @@ dem_status check_particles(dem_ctx *c, const dem_particles *P) {
   if (P->n > c->S.cap_particles) return fail(c, DEM_ERR_CAPACITY, "particles: n exceeds max_particles");
   if (P->n > 0 && (!P->state || !P->tri_off)) return fail(c, DEM_ERR_ARG, "particles: null state or tri_off");
   if (P->n_tris < 0) return fail(c, DEM_ERR_ARG, "particles: n_tris < 0");
+  if (P->n_tris > c->S.cap_triangles) return fail(c, DEM_ERR_CAPACITY, "particles: n_tris exceeds max_triangles");
   if (P->n_tris > 0 && !P->tris) return fail(c, DEM_ERR_ARG, "particles: null tris");
   if (reinterpret_cast<uintptr_t>(P->tris) % 16 != 0)
     return fail(c, DEM_ERR_ARG, "particles: tris must be 16-byte aligned (float4)");
@@ -76,8 +77,10 @@ dem_status dem_create(const dem_config *cfg, dem_ctx **out) {
   if (k.max_particles == 0) k.max_particles = 65536;
   if (k.max_pairs == 0) k.max_pairs = 1 << 20;
   if (k.max_contacts == 0) k.max_contacts = 1 << 20;
+  if (k.max_triangles == 0) k.max_triangles = 1280 * k.max_particles;
   if (k.K < 1 || !(k.bisect_tol > 0.0) || (k.precision != DEM_PREC_FP32_FIXUP && k.precision != DEM_PREC_FP64) ||
-      k.max_particles < 0 || k.max_pairs < 0 || k.max_contacts < 0 ||
+      k.max_particles < 0 || k.max_pairs < 0 || k.max_contacts < 0 || k.max_triangles < 0 ||
+      k.max_triangles > ((int64_t)1 << 40) ||
       k.max_particles > (int64_t)(dem::SCAN_BLOCK * dem::SCAN_PART_CAP / 2) ||
       k.max_pairs > (int64_t)(dem::SCAN_BLOCK * dem::SCAN_PART_CAP) || k.max_contacts > ((int64_t)1 << 31) - 1) {
     delete c;
@@ -95,15 +98,18 @@ dem_status dem_create(const dem_config *cfg, dem_ctx **out) {
   S.table_size = pow2_at_least(2 * (k.max_particles > 512 ? k.max_particles : 512));
   S.cap_pairs = k.max_pairs;
   S.cap_contacts = k.max_contacts;
+  S.cap_triangles = k.max_triangles;
+  S.cap_tiles = k.max_triangles / dem::TILE_TRIS + k.max_particles + 1;
   const int64_t np = k.max_particles, nq = k.max_pairs, nc = k.max_contacts;
   bool ok = alloc(c, &S.err, 1) && alloc(c, &S.stats, dem::ST_N) && alloc(c, &S.work, 4) &&
             alloc(c, &S.scan_part, dem::SCAN_PART_CAP) && alloc(c, &S.tmp, 8) && alloc(c, &S.sph, np) &&
             alloc(c, &S.cell, np) && alloc(c, &S.bucket_cnt, S.table_size) &&
             alloc(c, &S.bucket_start, S.table_size) && alloc(c, &S.bucket_cur, S.table_size) &&
             alloc(c, &S.bucket_ids, np) && alloc(c, &S.pcnt, np) && alloc(c, &S.poff, np) &&
-            alloc(c, &S.rho_max, 1) && alloc(c, &S.st_keys, 3 * nc) && alloc(c, &S.st_geom, 7 * nc) &&
+            alloc(c, &S.rho_max, 1) && alloc(c, &S.static_ids, np) && alloc(c, &S.n_static, 1) &&
+            alloc(c, &S.spose, 12 * np) && alloc(c, &S.sbox, 6 * np) && alloc(c, &S.st_keys, 3 * nc) && alloc(c, &S.st_geom, 7 * nc) &&
             alloc(c, &S.st_count, 1) && alloc(c, &S.pc, nq) && alloc(c, &S.po, nq) && alloc(c, &S.pcur, nq) &&
-            alloc(c, &S.sidx, nc);
+            alloc(c, &S.sidx, nc) && alloc(c, &S.tile_sph, S.cap_tiles);
   if (!ok) {
     dem_destroy(c);
     return DEM_ERR_CUDA;

@@ -1,19 +1,23 @@
 // broad.cu -- candidate pairs (paper Section 3: free-flight extrapolation of
-// each particle over its own step, bounding spheres that cover the particle and
-// its halo, a symmetric pairwise overlap test).
+// each particle over its own step, bounding volumes that cover the particle
+// and its halo, a symmetric pairwise overlap test; static geometry apart).
 //
-// Swept sphere of p over [t_cur, t_cur + dt]: centre m = x + v (dt/2), radius
-// rho = (radius + eps) + |v| (dt/2).  (i, j), i < j, is a candidate iff
-// |m_i - m_j|^2 <= (rho_i + rho_j)^2, evaluated in binary64 with each
-// operation rounded on its own; two static particles never pair.
+// Swept sphere of a moving p over [t_cur, t_cur + dt]: centre m = x + v (dt/2),
+// radius rho = (radius + eps) + |v| (dt/2).  Two moving particles (i, j),
+// i < j, are a candidate iff |m_i - m_j|^2 <= (rho_i + rho_j)^2.  A static
+// particle s is the axis-aligned box of its world vertices at t_cur widened
+// by eps_s; (p, s) is a candidate iff p's swept sphere meets the box, and the
+// static member is written second.  Every predicate is evaluated in binary64
+// with each operation rounded on its own; two static particles never pair.
 //
-// A uniform grid with cell size h >= 2 max rho is hashed into a power-of-two
-// table (counting sort of particles into buckets).  Overlapping spheres lie in
-// the same or adjacent cells, so scanning the 27 neighbour cells finds every
-// candidate; the binary64 predicate then decides, so the set equals the
-// brute-force set.  Per particle (one warp, lanes over the 27 cells) the
-// candidates are counted, offsets are scanned, and each particle writes its
-// partners sorted by j: the output is in (i, j) order without a global sort.
+// Moving particles go into a uniform grid with cell size h >= 2 max rho,
+// hashed into a power-of-two table (counting sort of particles into buckets).
+// Overlapping spheres lie in the same or adjacent cells, so scanning the 27
+// neighbour cells finds every moving partner; every static box is tested
+// directly (static objects are few: floors, walls).  Per particle (one warp,
+// lanes over the 27 cells and then over the static boxes) the candidates are
+// counted, offsets are scanned, and each particle writes its partners sorted:
+// the output is in (first, second) order without a global sort.
 #include "internal.cuh"
 
 namespace dem {
@@ -22,8 +26,24 @@ namespace {
 
 using D = OpsD;
 
-__global__ void k_prep(int64_t n, const double *st, Sphere4 *sph, unsigned long long *rho_max) {
+// order-preserving unsigned key of a double (for atomic min / max)
+__device__ __forceinline__ unsigned long long okey(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double okey_value(unsigned long long k) {
+  return __longlong_as_double(static_cast<long long>((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+
+// swept spheres of all particles; max rho over moving particles; static
+// particles listed with their pose at t_cur and an empty box
+__global__ void k_prep(int64_t n, const double *st, const uint8_t *is_static, Sphere4 *sph,
+                       unsigned long long *rho_max, int32_t *static_ids, int32_t *n_static, double *spose,
+                       unsigned long long *sbox) {
   __shared__ double red[8];
+  __shared__ double rc[POSE_TERMS + 1], rs[POSE_TERMS + 1];
+  if (threadIdx.x == 0) pose_reciprocals(rc, rs);
+  __syncthreads();
   double mx = 0.0;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
     const double hdt = D::mul(st[14 * n + p], 0.5);
@@ -35,7 +55,20 @@ __global__ void k_prep(int64_t n, const double *st, Sphere4 *sph, unsigned long 
     const double vv = D::add(D::add(D::mul(vx, vx), D::mul(vy, vy)), D::mul(vz, vz));
     s.w = D::add(D::add(st[16 * n + p], st[15 * n + p]), D::mul(D::sqrt(vv), hdt));
     sph[p] = s;
-    mx = fmax(mx, s.w);
+    if (is_static && is_static[p]) {
+      const int32_t q = atomicAdd(n_static, 1);
+      static_ids[q] = int32_t(p);
+      double R[9], X[3];
+      pose_exact(st, n, p, st[13 * n + p], rc, rs, R, X);
+      for (int k = 0; k < 9; ++k) spose[12 * (int64_t)q + k] = R[k];
+      for (int k = 0; k < 3; ++k) spose[12 * (int64_t)q + 9 + k] = X[k];
+      for (int k = 0; k < 3; ++k) {  // empty box: min = +inf, max = -inf
+        sbox[6 * (int64_t)q + k] = okey(OpsD::inf());
+        sbox[6 * (int64_t)q + 3 + k] = okey(-OpsD::inf());
+      }
+    } else {
+      mx = fmax(mx, s.w);
+    }
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -44,6 +77,51 @@ __global__ void k_prep(int64_t n, const double *st, Sphere4 *sph, unsigned long 
   if (threadIdx.x == 0) {
     for (int q = 1; q < (int)(blockDim.x >> 5); ++q) mx = fmax(mx, red[q]);
     atomicMax(rho_max, static_cast<unsigned long long>(__double_as_longlong(mx)));
+  }
+}
+
+// world-vertex extremes of every static particle at t_cur (binary64, the
+// same vertex transform as the exact narrow phase); min and max are exact,
+// so the order of the reduction does not matter
+__global__ void k_static_box(int64_t n, const int64_t *tri_off, const float4 *tris, int64_t n_tris,
+                             const int32_t *static_ids, const int32_t *n_static, const double *spose,
+                             unsigned long long *sbox, uint32_t *err) {
+  const int ns = *n_static;
+  const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, gstride = (int64_t)gridDim.x * blockDim.x;
+  for (int q = 0; q < ns; ++q) {
+    const int64_t p = static_ids[q];
+    const int64_t o = tri_off[p], cnt = tri_off[p + 1] - o;
+    if (cnt < 0 || o < 0 || o + cnt > n_tris) {
+      if (gid == 0) set_err(err, ERR_INDEX);
+      continue;
+    }
+    const double *R = spose + 12 * (int64_t)q, *X = R + 9;
+    double lo[3] = {OpsD::inf(), OpsD::inf(), OpsD::inf()}, hi[3] = {-OpsD::inf(), -OpsD::inf(), -OpsD::inf()};
+    for (int64_t k = gid; k < cnt; k += gstride)
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        const float4 f = tris[v * n_tris + o + k];
+        const V3<double> w = to_world_exact(R, X, f.x, f.y, f.z);
+        lo[0] = fmin(lo[0], w.x);
+        lo[1] = fmin(lo[1], w.y);
+        lo[2] = fmin(lo[2], w.z);
+        hi[0] = fmax(hi[0], w.x);
+        hi[1] = fmax(hi[1], w.y);
+        hi[2] = fmax(hi[2], w.z);
+      }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int sh = 16; sh; sh >>= 1) {
+        lo[k] = fmin(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], sh));
+        hi[k] = fmax(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], sh));
+      }
+    if ((threadIdx.x & 31) == 0 && lo[0] <= hi[0]) {
+      for (int k = 0; k < 3; ++k) {
+        atomicMin(&sbox[6 * (int64_t)q + k], okey(lo[k]));
+        atomicMax(&sbox[6 * (int64_t)q + 3 + k], okey(hi[k]));
+      }
+    }
   }
 }
 
@@ -63,10 +141,14 @@ __device__ __forceinline__ int cell_coord(double v, double ih) {
   return c > 1e9 ? 1000000000 : (c < -1e9 ? -1000000000 : int(c));
 }
 
-__global__ void k_count(int64_t n, const Sphere4 *sph, const unsigned long long *rho_max, uint32_t mask,
-                        int4 *cell, int32_t *bcnt) {
+__global__ void k_count(int64_t n, const Sphere4 *sph, const uint8_t *is_static,
+                        const unsigned long long *rho_max, uint32_t mask, int4 *cell, int32_t *bcnt) {
   const double ih = inv_cell(rho_max);
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    if (is_static && is_static[p]) {  // static particles are not binned
+      cell[p] = make_int4(0, 0, 0, -1);
+      continue;
+    }
     const Sphere4 s = sph[p];
     const int cx = cell_coord(s.x, ih), cy = cell_coord(s.y, ih), cz = cell_coord(s.z, ih);
     const uint32_t b = bucket_of(cx, cy, cz, mask);
@@ -78,25 +160,40 @@ __global__ void k_count(int64_t n, const Sphere4 *sph, const unsigned long long 
 __global__ void k_scatter(int64_t n, const int4 *cell, const int64_t *bstart, int32_t *bcur, int32_t *ids) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
     const int b = cell[p].w;
-    ids[bstart[b] + atomicAdd(&bcur[b], 1)] = int32_t(p);
+    if (b >= 0) ids[bstart[b] + atomicAdd(&bcur[b], 1)] = int32_t(p);
   }
 }
 
-// One warp per particle i: lane c < 27 scans neighbour cell c; counts are
-// combined with a warp prefix sum.  WRITE: the partners are written at the
-// particle's offset and sorted by j (bitonic in registers for up to 32).
+// One warp per moving particle i: lane c < 27 scans neighbour cell c, then
+// the lanes share the static boxes; counts are combined with warp prefix
+// sums.  WRITE: the partners are written at the particle's offset and sorted
+// by partner index (bitonic in registers for up to 32).
+__device__ __forceinline__ int warp_incl_sum(int v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  return v;
+}
+
 template <bool WRITE>
-__global__ void k_pairs(int64_t n, const Sphere4 *sph, const int4 *cell, const uint8_t *is_static,
-                        const int32_t *bcnt, const int64_t *bstart, const int32_t *ids, uint32_t mask,
-                        int64_t *pcnt, const int64_t *poff, int32_t *pairs, int64_t cap,
-                        const int64_t *n_pairs, uint32_t *err) {
+__global__ void k_pairs(int64_t n, const double *st, const Sphere4 *sph, const int4 *cell,
+                        const uint8_t *is_static, const int32_t *bcnt, const int64_t *bstart, const int32_t *ids,
+                        uint32_t mask, const int32_t *static_ids, const int32_t *n_static,
+                        const unsigned long long *sbox, int64_t *pcnt, const int64_t *poff, int32_t *pairs,
+                        int64_t cap, const int64_t *n_pairs, uint32_t *err) {
   if (WRITE && blockIdx.x == 0 && threadIdx.x == 0 && *n_pairs > cap) set_err(err, ERR_CAPACITY);
   const int lane = threadIdx.x & 31;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int ns = *n_static;
   for (int64_t i = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; i < n; i += nwarp) {
+    if (is_static && is_static[i]) {  // a static particle is never the first member
+      if (!WRITE && lane == 0) pcnt[i] = 0;
+      continue;
+    }
     const Sphere4 si = sph[i];
     const int4 ci = cell[i];
-    const bool sti = is_static && is_static[i];
     const int cx = ci.x + (lane % 3) - 1, cy = ci.y + ((lane / 3) % 3) - 1, cz = ci.z + (lane / 9) - 1;
     int64_t b0 = 0, b1 = 0;
     if (lane < 27) {
@@ -104,43 +201,57 @@ __global__ void k_pairs(int64_t n, const Sphere4 *sph, const int4 *cell, const u
       b0 = bstart[b];
       b1 = b0 + bcnt[b];
     }
-    // the binary64 candidate predicate (same operation order as the oracle)
+    // moving partner j > i (the binary64 sphere predicate, oracle order)
     auto is_pair = [&](int32_t j) {
       if (j <= i) return false;
       const int4 cj = cell[j];
       if (cj.x != cx || cj.y != cy || cj.z != cz) return false;  // other cell, same bucket
-      if (sti && is_static[j]) return false;
       const Sphere4 sj = sph[j];
       const double ddx = D::sub(si.x, sj.x), ddy = D::sub(si.y, sj.y), ddz = D::sub(si.z, sj.z);
       const double dd = D::add(D::add(D::mul(ddx, ddx), D::mul(ddy, ddy)), D::mul(ddz, ddz));
       const double rr = D::add(si.w, sj.w);
       return dd <= D::mul(rr, rr);
     };
-    int c = 0;
-    for (int64_t q = b0; q < b1; ++q) c += is_pair(ids[q]) ? 1 : 0;
-    int inc = c;
+    // static partner number q: the swept sphere meets the widened box
+    auto meets_box = [&](int q) {
+      const int64_t sp = static_ids[q];
+      const double e = st[15 * n + sp];
+      const double m[3] = {si.x, si.y, si.z};
+      double g[3];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
-    }
-    const int total = __shfl_sync(0xffffffffu, inc, 31);
+      for (int k = 0; k < 3; ++k) {
+        const double lo = D::sub(okey_value(sbox[6 * (int64_t)q + k]), e);
+        const double hi = D::add(okey_value(sbox[6 * (int64_t)q + 3 + k]), e);
+        g[k] = m[k] < lo ? D::sub(lo, m[k]) : (m[k] > hi ? D::sub(m[k], hi) : 0.0);
+      }
+      const double gg = D::add(D::add(D::mul(g[0], g[0]), D::mul(g[1], g[1])), D::mul(g[2], g[2]));
+      return gg <= D::mul(si.w, si.w);
+    };
+    int c = 0, cs = 0;
+    for (int64_t q = b0; q < b1; ++q) c += is_pair(ids[q]) ? 1 : 0;
+    for (int q = lane; q < ns; q += 32) cs += meets_box(q) ? 1 : 0;
+    const int inc = warp_incl_sum(c, lane), incs = warp_incl_sum(cs, lane);
+    const int tgrid = __shfl_sync(0xffffffffu, inc, 31);
+    const int total = tgrid + __shfl_sync(0xffffffffu, incs, 31);
     if (!WRITE) {
       if (lane == 0) pcnt[i] = total;
       continue;
     }
     const int64_t o = poff[i];
+    auto put = [&](int64_t pos, int32_t j) {
+      if (pos < cap) {
+        pairs[2 * pos] = int32_t(i);
+        pairs[2 * pos + 1] = j;
+      }
+    };
     int64_t pos = o + inc - c;
     for (int64_t q = b0; q < b1; ++q) {
       const int32_t j = ids[q];
-      if (is_pair(j)) {
-        if (pos < cap) {
-          pairs[2 * pos] = int32_t(i);
-          pairs[2 * pos + 1] = j;
-        }
-        ++pos;
-      }
+      if (is_pair(j)) put(pos++, j);
     }
+    pos = o + tgrid + incs - cs;
+    for (int q = lane; q < ns; q += 32)
+      if (meets_box(q)) put(pos++, static_ids[q]);
     __syncwarp();
     const int64_t e = o + total < cap ? o + total : cap;
     const int m = int(e > o ? e - o : 0);
@@ -175,22 +286,31 @@ cudaError_t launch_broad(const dem_particles &P, int32_t *pairs, int64_t cap, in
   const int64_t n = P.n;
   cudaError_t e;
   if ((e = cudaMemsetAsync(S.rho_max, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(S.n_static, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
   if (n <= 0) return cudaMemsetAsync(n_pairs, 0, sizeof(int64_t), s);
   const uint32_t mask = uint32_t(S.table_size - 1);
   const int tb = 256;
   const unsigned grid = (unsigned)((n + tb - 1) / tb);
   if ((e = cudaMemsetAsync(S.bucket_cnt, 0, sizeof(int32_t) * S.table_size, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(S.bucket_cur, 0, sizeof(int32_t) * S.table_size, s)) != cudaSuccess) return e;
-  k_prep<<<grid, tb, 0, s>>>(n, P.state, S.sph, S.rho_max);
-  k_count<<<grid, tb, 0, s>>>(n, S.sph, S.rho_max, mask, S.cell, S.bucket_cnt);
-  S.launches += 2 + scan_exclusive_i32_to_i64(S.bucket_cnt, S.bucket_start, S.table_size, S.scan_part, s);
+  k_prep<<<grid, tb, 0, s>>>(n, P.state, P.is_static, S.sph, S.rho_max, S.static_ids, S.n_static, S.spose, S.sbox);
+  S.launches += 1;
+  if (P.is_static) {
+    k_static_box<<<304, tb, 0, s>>>(n, P.tri_off, reinterpret_cast<const float4 *>(P.tris), P.n_tris,
+                                     S.static_ids, S.n_static, S.spose, S.sbox, S.err);
+    S.launches += 1;
+  }
+  k_count<<<grid, tb, 0, s>>>(n, S.sph, P.is_static, S.rho_max, mask, S.cell, S.bucket_cnt);
+  S.launches += 1 + scan_exclusive_i32_to_i64(S.bucket_cnt, S.bucket_start, S.table_size, S.scan_part, s);
   k_scatter<<<grid, tb, 0, s>>>(n, S.cell, S.bucket_start, S.bucket_cur, S.bucket_ids);
   const unsigned wgrid = (unsigned)((n + 7) / 8);  // one warp per particle
-  k_pairs<false><<<wgrid, tb, 0, s>>>(n, S.sph, S.cell, P.is_static, S.bucket_cnt, S.bucket_start, S.bucket_ids,
-                                      mask, S.pcnt, nullptr, nullptr, 0, nullptr, S.err);
+  k_pairs<false><<<wgrid, tb, 0, s>>>(n, P.state, S.sph, S.cell, P.is_static, S.bucket_cnt, S.bucket_start,
+                                      S.bucket_ids, mask, S.static_ids, S.n_static, S.sbox, S.pcnt, nullptr,
+                                      nullptr, 0, nullptr, S.err);
   S.launches += 2 + scan_exclusive_i64(S.pcnt, S.poff, n, n_pairs, S.scan_part, s);
-  k_pairs<true><<<wgrid, tb, 0, s>>>(n, S.sph, S.cell, P.is_static, S.bucket_cnt, S.bucket_start, S.bucket_ids,
-                                     mask, nullptr, S.poff, pairs, cap, n_pairs, S.err);
+  k_pairs<true><<<wgrid, tb, 0, s>>>(n, P.state, S.sph, S.cell, P.is_static, S.bucket_cnt, S.bucket_start,
+                                     S.bucket_ids, mask, S.static_ids, S.n_static, S.sbox, nullptr, S.poff, pairs,
+                                     cap, n_pairs, S.err);
   S.launches += 1;
   return cudaGetLastError();
 }

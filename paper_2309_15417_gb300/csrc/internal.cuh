@@ -53,6 +53,10 @@ struct Scratch {
   int64_t *pcnt;                  // [n] candidates per particle
   int64_t *poff;                  // [n]
   unsigned long long *rho_max;    // [1] (bits of a non-negative double)
+  int32_t *static_ids;            // [n] static particles, in order of discovery
+  int32_t *n_static;              // [1]
+  double *spose;                  // [n][12] rotation (row-major) and centre of each static at t_cur
+  unsigned long long *sbox;       // [n][6] order keys of its world-vertex extremes (min xyz, max xyz)
   // narrow phase
   int64_t cap_pairs;
   int64_t cap_contacts;
@@ -63,8 +67,15 @@ struct Scratch {
   int64_t *po;                    // [cap_pairs] exclusive offsets
   int32_t *pcur;                  // [cap_pairs] scatter cursors
   int32_t *sidx;                  // [cap_contacts] staging index per output slot
+  // bounding spheres of the TILE_TRIS-triangle tiles of particles with more
+  // than one tile (body frame: centre, radius); tile k of particle p is slot
+  // tri_off[p] / TILE_TRIS + p + k, distinct for every (p, k)
+  int64_t cap_triangles;
+  int64_t cap_tiles;
+  float4 *tile_sph;               // [cap_tiles]
 };
 
+constexpr int TILE_TRIS = 320;                 // triangles per shared-memory tile of the pair kernel
 constexpr int64_t SCAN_BLOCK = 2048;           // elements per scan block
 constexpr int64_t SCAN_PART_CAP = 4096;        // partial sums (=> up to 8M elements)
 

@@ -77,6 +77,7 @@ struct Cfg<1> {
   using T = double;
   using O = OpsD;
 };
+static_assert(Cfg<0>::TT == TILE_TRIS && Cfg<1>::TT == TILE_TRIS, "tile spheres assume one tile size");
 
 struct PairArgs {
   int64_t n;
@@ -104,6 +105,9 @@ struct PairArgs {
   int32_t *ct_ab;
   int K;
   double tol;
+  // bounding spheres of the tiles of particles with more than one tile
+  const float4 *tile_sph;
+  int64_t cap_tiles;
   // bookkeeping
   unsigned int *work;
   uint32_t *err;
@@ -154,6 +158,7 @@ struct __align__(128) Smem {
   unsigned long long best_key;
   double best_pa[3], best_pb[3];
   unsigned int work_item;
+  int tfirst;                         // nearest tile pair (argmin pass)
   unsigned long long cnt[ST_N];
 };
 
@@ -279,6 +284,97 @@ struct Cta {
   }
 
   __device__ int ntiles(int n) const { return (n + TT - 1) / TT; }
+
+  // --- tile culling (particles with more than one tile) ---------------------
+  // Bounding sphere of tile k of A or B in the evaluation frame: the stored
+  // body-frame tile sphere of a multi-tile particle, else the body origin with
+  // the particle radius; moved like the vertices (FP32: B into A's frame;
+  // FP64: both into the world frame).
+  __device__ void tile_sphere(bool isA, int k, T c[3], T &r) const {
+    const int64_t p = isA ? s.i : s.j, off = isA ? s.offA : s.offB;
+    const int n = isA ? s.nA : s.nB;
+    float4 f = make_float4(0.f, 0.f, 0.f, __double2float_ru(A.st[16 * A.n + p]));
+    const int64_t slot = off / TT + p + k;
+    if (n > TT && slot < A.cap_tiles) f = A.tile_sph[slot];
+    r = T(f.w);
+    if constexpr (PREC == 0) {
+      if (isA) {
+        c[0] = f.x;
+        c[1] = f.y;
+        c[2] = f.z;
+      } else {
+        const float *R = s.Rr;
+        c[0] = fmaf(R[0], f.x, fmaf(R[1], f.y, fmaf(R[2], f.z, s.tr[0])));
+        c[1] = fmaf(R[3], f.x, fmaf(R[4], f.y, fmaf(R[5], f.z, s.tr[1])));
+        c[2] = fmaf(R[6], f.x, fmaf(R[7], f.y, fmaf(R[8], f.z, s.tr[2])));
+      }
+    } else {
+      const V3<double> q = to_world_exact(isA ? s.RA : s.RB, isA ? s.XA : s.XB, f.x, f.y, f.z);
+      c[0] = q.x;
+      c[1] = q.y;
+      c[2] = q.z;
+    }
+  }
+  // distance between the centres of the tile spheres of (ta, tb)
+  __device__ T tile_gap(int ta, int tb, T &ra, T &rb) const {
+    T ca[3], cb[3];
+    tile_sphere(true, ta, ca, ra);
+    tile_sphere(false, tb, cb, rb);
+    const T dx = ca[0] - cb[0], dy = ca[1] - cb[1], dz = ca[2] - cb[2];
+    return O::sqrt(dx * dx + dy * dy + dz * dz);
+  }
+  // false only if no triangle pair of tiles (ta, tb) can come within thr
+  // (the margin 2 Elb covers the rounding of the sphere test, as for groups)
+  __device__ bool tile_near(int ta, int tb, double thr) const {
+    T ra, rb;
+    const T g = tile_gap(ta, tb, ra, rb);
+    return double(g - ra - rb) <= thr + 2.0 * s.Elb;
+  }
+  // Lower the shared bound with the upper bound every tile pair gives on the
+  // smallest triangle-pair distance (any point of one tile sphere is within
+  // gap + ra + rb of any point of the other), and return the tile pair
+  // q = ta * ntb + tb with the smallest lower bound (ties: smallest q).
+  __device__ int bound_by_tiles(int nta, int ntb) {
+    double best = OpsD::inf(), ub = OpsD::inf();
+    int bq = 0;
+    for (int q = tid; q < nta * ntb; q += NT) {
+      T ra, rb;
+      const T g = tile_gap(q / ntb, q % ntb, ra, rb);
+      const double lb = double(g - ra - rb);
+      ub = fmin(ub, double(g + ra + rb) + 2.0 * s.Elb + 4.0 * s.Ed);
+      if (lb < best) {
+        best = lb;
+        bq = q;
+      }
+    }
+    if (ub < OpsD::inf()) atomicMin(&s.bound, dbits(ub));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
+      if (ob < best || (ob == best && oq < bq)) {
+        best = ob;
+        bq = oq;
+      }
+    }
+    if (lane == 0) {
+      s.red_d[w] = best;
+      s.red_k[w] = (unsigned long long)bq;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double b = s.red_d[0];
+      int q = int(s.red_k[0]);
+      for (int k = 1; k < NW; ++k)
+        if (s.red_d[k] < b || (s.red_d[k] == b && int(s.red_k[k]) < q)) {
+          b = s.red_d[k];
+          q = int(s.red_k[k]);
+        }
+      s.tfirst = q;
+    }
+    __syncthreads();
+    return s.tfirst;
+  }
 
   // --- tiles -------------------------------------------------------------
   // Make body tile ta of A resident (B is read from global memory when its
@@ -1105,8 +1201,10 @@ struct Cta {
     }
     __syncthreads();
     bool stop = false;
+    const bool multi = nta > 1 || ntb > 1;
     for (int ta = 0; ta < nta && !stop; ++ta)
       for (int tb = 0; tb < ntb && !stop; ++tb) {
+        if (multi && !__syncthreads_or(tid == 0 && tile_near(ta, tb, double(th0)))) continue;
         if (!load_tiles(ta, tb)) return false;
         frames(ta, tb);
         scan_tiles<DECIDE, ARGMIN, CONTACTS>(ta, tb, false, th0, pk);
@@ -1125,12 +1223,18 @@ struct Cta {
       if (!complete && nta > 0 && ntb > 0) {
         if (tid == 0) s.bound = dbits(mh + 3.0 * s.Ed + s.Elb);  // inf if nothing seen
         __syncthreads();
-        for (int ta = 0; ta < nta; ++ta)
-          for (int tb = 0; tb < ntb; ++tb) {
-            if (!load_tiles(ta, tb)) return false;
-            frames(ta, tb);
-            scan_tiles<false, true, false>(ta, tb, true, th0, pk);
-          }
+        // the nearest tile pair first (it tightens the bound), then the others
+        const int nq = nta * ntb, q0 = multi ? bound_by_tiles(nta, ntb) : 0;
+        for (int r = 0; r < nq; ++r) {
+          const int q = r == 0 ? q0 : (r <= q0 ? r - 1 : r);
+          const int ta = q / ntb, tb = q - ta * ntb;
+          if (multi && r > 0 &&
+              !__syncthreads_or(tid == 0 && tile_near(ta, tb, bitsd(*(volatile unsigned long long *)&s.bound))))
+            continue;
+          if (!load_tiles(ta, tb)) return false;
+          frames(ta, tb);
+          scan_tiles<false, true, false>(ta, tb, true, th0, pk);
+        }
       }
       const double mh2 = block_min(double(mw));
       if (PREC == 0) argmin_list(mh2);
@@ -1668,6 +1772,70 @@ __global__ void contact_total(const int64_t *total, const unsigned long long *st
   if ((int64_t)*st_count > st_cap) set_err(err, ERR_CAPACITY);
 }
 
+// Bounding spheres of the tiles of every particle with more than one tile
+// (one warp per particle): centre = the middle of the vertices' bounding box,
+// radius = the largest centre-vertex distance, enlarged by 2^-20 relative
+// (and 1e-18 absolute) so that it covers every float32 vertex despite the
+// rounding of its own computation.
+__global__ void k_tile_spheres(int64_t n, const int64_t *tri_off, const float4 *tris, int64_t n_tris,
+                               float4 *tile_sph, int64_t cap_tiles, uint32_t *err) {
+  constexpr int TT = TILE_TRIS;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; p < n; p += nwarp) {
+    const int64_t o = tri_off[p], cnt = tri_off[p + 1] - o;
+    if (cnt <= TT) continue;
+    if (o < 0 || o + cnt > n_tris) {
+      if (lane == 0) set_err(err, ERR_INDEX);
+      continue;
+    }
+    const int64_t nt = (cnt + TT - 1) / TT;
+    for (int64_t k = 0; k < nt; ++k) {
+      const int64_t slot = o / TT + p + k;
+      if (slot >= cap_tiles) {
+        if (lane == 0) set_err(err, ERR_CAPACITY);
+        break;
+      }
+      const int64_t t0 = o + k * TT, m = cnt - k * TT < TT ? cnt - k * TT : TT;
+      float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+      for (int64_t t = lane; t < m; t += 32)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          const float4 f = tris[v * n_tris + t0 + t];
+          lo[0] = fminf(lo[0], f.x);
+          lo[1] = fminf(lo[1], f.y);
+          lo[2] = fminf(lo[2], f.z);
+          hi[0] = fmaxf(hi[0], f.x);
+          hi[1] = fmaxf(hi[1], f.y);
+          hi[2] = fmaxf(hi[2], f.z);
+        }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        lo[c] = seg_min(lo[c], 32);
+        hi[c] = seg_max(hi[c], 32);
+      }
+      const float cx = 0.5f * (lo[0] + hi[0]), cy = 0.5f * (lo[1] + hi[1]), cz = 0.5f * (lo[2] + hi[2]);
+      float r2 = 0.f;
+      for (int64_t t = lane; t < m; t += 32)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          const float4 f = tris[v * n_tris + t0 + t];
+          const float dx = f.x - cx, dy = f.y - cy, dz = f.z - cz;
+          r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
+        }
+      r2 = seg_max(r2, 32);
+      if (lane == 0) tile_sph[slot] = make_float4(cx, cy, cz, sqrtf(r2) * (1.0f + 0x1p-20f) + 1e-18f);
+    }
+  }
+}
+
+int prepare_tiles(const dem_particles &P, Scratch &S, cudaStream_t s) {
+  if (P.n <= 0) return 0;
+  k_tile_spheres<<<(unsigned)((P.n + 7) / 8), 256, 0, s>>>(P.n, P.tri_off, reinterpret_cast<const float4 *>(P.tris),
+                                                          P.n_tris, S.tile_sph, S.cap_tiles, S.err);
+  return 1;
+}
+
 template <int PREC, int MODE>
 cudaError_t launch_pairs(const PairArgs &a, int num_sms, cudaStream_t s) {
   const size_t smem = sizeof(Smem<PREC>);
@@ -1699,6 +1867,8 @@ PairArgs make_args(const dem_particles &P, const int32_t *pairs, int64_t max_pai
   a.pairs = pairs;
   a.max_pairs = max_pairs;
   a.n_pairs = n_pairs;
+  a.tile_sph = S.tile_sph;
+  a.cap_tiles = S.cap_tiles;
   a.work = S.work;
   a.err = S.err;
   a.stats = S.stats;
@@ -1718,6 +1888,7 @@ cudaError_t finish_narrow(int prec, PairArgs &a, const dem_particles &P, const i
   if (max_pairs > 0) {
     if ((e = cudaMemsetAsync(S.pc, 0, sizeof(int64_t) * max_pairs, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(S.pcur, 0, sizeof(int32_t) * max_pairs, s)) != cudaSuccess) return e;
+    S.launches += prepare_tiles(P, S, s);
     if (fused)
       e = prec == 0 ? launch_pairs<0, MODE_BOTH>(a, num_sms, s) : launch_pairs<1, MODE_BOTH>(a, num_sms, s);
     else
@@ -1799,7 +1970,7 @@ cudaError_t launch_ctime(int prec, const dem_particles &P, const int32_t *pairs,
   cudaError_t e;
   if ((e = cudaMemsetAsync(S.work, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
   if (max_pairs <= 0) return cudaSuccess;
-  S.launches += 1;
+  S.launches += 1 + prepare_tiles(P, S, s);
   return prec == 0 ? launch_pairs<0, MODE_CTIME>(a, num_sms, s) : launch_pairs<1, MODE_CTIME>(a, num_sms, s);
 }
 

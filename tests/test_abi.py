@@ -28,9 +28,25 @@ def test_library_builds_and_exports_every_symbol():
         assert hasattr(lib, name), name
 
 
-def test_struct_sizes_match_header():
-    # dem_stats: 16 int64; dem_config: 48 bytes with natural alignment
-    assert ctypes.sizeof(D.dem_stats) == 16 * 8
-    assert ctypes.sizeof(D.dem_config) == 48
-    assert ctypes.sizeof(D.dem_particles) == 48
-    assert ctypes.sizeof(D.dem_narrow_out) == 80
+def test_struct_layouts_match_header(tmp_path):
+    """Every field of the Python mirrors sits at the offset the C compiler
+    gives it for include/dem.h, and the structs have the same sizes."""
+    import subprocess
+    structs = [D.dem_config, D.dem_particles, D.dem_narrow_out, D.dem_stats]
+    lines = ['#include <stdio.h>', '#include "dem.h"', 'int main(void) {']
+    for S in structs:
+        name = S.__name__
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in S._fields_:
+            lines.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for S in structs:
+        name = S.__name__
+        assert int(got[name]) == ctypes.sizeof(S), name
+        for f, _ in S._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(S, f).offset, f"{name}.{f}"
