@@ -1195,8 +1195,13 @@ struct Cta {
     const int nta = ntiles(s.nA), ntb = ntiles(s.nB);
     const T th0 = T(s.eps) + T(s.Elb) + T(extra);
     if (tid == 0) {
-      s.nil = 0;
-      s.ilover = 0;
+      // only a collecting evaluation starts a new list; the others (samples
+      // after an overflow, the final argmin) leave the list and its overflow
+      // flag as they are
+      if (extra > 0.0) {
+        s.nil = 0;
+        s.ilover = 0;
+      }
       s.ilcol = extra > 0.0 ? 1 : 0;
     }
     __syncthreads();

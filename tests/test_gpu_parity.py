@@ -300,6 +300,29 @@ def test_ctime_head_on_closed_form(dem, prec):
         assert tstar - 1e-15 <= g["t_coll"][0] <= tstar + 1e-6 + 1e-15
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_ctime_after_interval_list_overflow(dem, prec):
+    """A fast head-on approach (320-triangle icospheres closing 0.8 over the
+    step) puts more triangle pairs within eps + delta at the pair start than
+    the pair-interval list holds: every sample and bisection step must then
+    decide on a full evaluation, in the separate and the fused call alike."""
+    for frac in (0.3, 0.6, 0.93):
+        gap = 0.1 + frac * 0.8
+        w = W.injected_head_on(gap, 800.0, 0.05, 1e-3, subdiv=2)
+        pairs = np.array([[0, 1]], np.int32)
+        o = oracle.collision_times(w, pairs)
+        assert o["status"][0] == 2
+        g = gpu_ctime(dem, w, pairs, prec)
+        assert np.array_equal(g["status"], o["status"]) and np.array_equal(g["t_coll"], o["t_coll"])
+        assert np.array_equal(g["tri_ab"], o["tri_ab"])
+        c = _ctx(dem, w, prec)
+        sc = dem.Scene.from_workload(w)
+        c.step_fused(sc)
+        c.check()
+        assert int(c.n_pairs.item()) == 1
+        assert c.status[0].item() == 2 and c.t_coll[0].item() == o["t_coll"][0]
+
+
 # ----------------------------------------------------------------------------- clusters
 
 def gpu_clusters(dem, n, edges, is_static):
