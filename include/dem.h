@@ -141,7 +141,8 @@ typedef struct {
   int64_t contacts;         /* contacts found */
   int64_t pairs_done;       /* pairs processed */
   int64_t kernel_launches;  /* kernels launched by this context (host-side count) */
-  int64_t reserved[6];
+  int64_t tile_pairs;       /* 320 x 320-triangle tile pairs scanned (not culled by tile spheres) */
+  int64_t reserved[5];
 } dem_stats;
 
 /* Create a context: validates and copies *cfg, allocates scratch for the

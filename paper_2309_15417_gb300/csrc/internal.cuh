@@ -24,6 +24,8 @@ enum {
   ST_BISECT,
   ST_CONTACTS,
   ST_PAIRS,
+  ST_HOST_LAUNCHES,  // slot of dem_stats.kernel_launches (host-side count)
+  ST_TILES,
   ST_N = 16
 };
 

@@ -145,7 +145,7 @@ struct __align__(128) Smem {
   int64_t i, j, offA, offB;
   int nA, nB, ngp, gpnext, found, resA, resB, frmA, frmB, bad, abort, nac, ngrid;
   int wcnt[NW];
-  uint32_t il[ILCAP];                 // pair-interval candidates (a << 16 | b)
+  unsigned long long il[ILCAP];       // pair-interval candidates (a << 32 | b, within the particles)
   int nil, ilover, ilcol;
   double delta;                       // bound on the change of any distance over the interval
   double gR[GRID_MAX][2][9], gX[GRID_MAX][2][3];  // poses at the sample times
@@ -823,8 +823,8 @@ struct Cta {
         if (have) {
           const int pos = base + __popc(m & lanemask_lt());
           const int ag = ta * TT + a, bg = tb * TT + b;
-          if (pos < ILCAP && ag < 65536 && bg < 65536)
-            s.il[pos] = (uint32_t(ag) << 16) | uint32_t(bg);
+          if (pos < ILCAP)
+            s.il[pos] = (static_cast<unsigned long long>(ag) << 32) | static_cast<uint32_t>(bg);
           else
             s.ilover = 1;
         }
@@ -1212,6 +1212,7 @@ struct Cta {
         if (multi && !__syncthreads_or(tid == 0 && tile_near(ta, tb, double(th0)))) continue;
         if (!load_tiles(ta, tb)) return false;
         frames(ta, tb);
+        if (tid == 0) stat(ST_TILES, 1);
         scan_tiles<DECIDE, ARGMIN, CONTACTS>(ta, tb, false, th0, pk);
         if (DECIDE && !ARGMIN && s.found) stop = true;
       }
@@ -1238,6 +1239,7 @@ struct Cta {
             continue;
           if (!load_tiles(ta, tb)) return false;
           frames(ta, tb);
+          if (tid == 0) stat(ST_TILES, 1);
           scan_tiles<false, true, false>(ta, tb, true, th0, pk);
         }
       }
@@ -1342,8 +1344,8 @@ struct Cta {
     for (int r0 = w * 32; r0 < n; r0 += NT) {
       const int k = r0 + lane;
       const bool have = k < n;
-      const uint32_t ent = have ? s.il[k] : 0u;
-      const int ag = int(ent >> 16), bg = int(ent & 0xffffu);
+      const unsigned long long ent = have ? s.il[k] : 0ull;
+      const int ag = int(ent >> 32), bg = int(ent & 0xffffffffu);
       T d = O::inf();
       if (have) {
         V X[3], Y[3];

@@ -1,7 +1,8 @@
 """Full-size parity cases: the 10,000-particle uneven-mesh batch (icospheres of
-80/320/1280 triangles and convex hulls, radii 0.5-4, clustered) and the
+80/320/1280 triangles and convex hulls, radii 0.5-4, clustered), the
 100,000-particle local-time-stepping layout (dense FCC blobs and free
-particles, per-particle steps log-uniform in [1e-5, 1e-2]).
+particles, per-particle steps log-uniform in [1e-5, 1e-2]) and the
+1,000,000-particle settling column over a static floor of 199,712 triangles.
 
 The GPU runs the whole step on all pairs; the oracle checks the candidate
 set (in full, or the partners of sampled particles where O(N^2) is too slow)
@@ -18,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 def _run(dem, w, prec=0, max_pairs=1 << 20):
     c = dem.Context(K=w.K, tol=w.tol, precision=prec, max_particles=w.n, max_pairs=max_pairs,
-                    max_contacts=1 << 22)
+                    max_contacts=1 << 22, max_triangles=w.n_tris)
     sc = dem.Scene.from_workload(w)
     c.step_fused(sc)
     c.check()
@@ -90,3 +91,38 @@ def test_lts_100k_full_size(dem):
     idx = np.unique(np.concatenate([np.where(g["status"] == 2)[0][:8], rng.choice(len(pairs), 16, replace=False)]))
     oc = _check_sampled_pairs(w, g, idx)
     assert set(np.unique(oc["status"])) >= {0, 1}
+
+
+def test_settling_column_full_size(dem):
+    """10^6 icospheres (80 / 320 triangles) on a jittered lattice over a static
+    316 x 316-quad floor: the whole step on the GPU; the floor's partners and
+    sampled particles' partners against brute force, clusters in full, and
+    sampled pairs (with and without the floor) one by one."""
+    w = W.settling_column(0)
+    floor = w.n - 1
+    g = _run(dem, w)
+    pairs = g["pairs"]
+    key = pairs[:, 0].astype(np.int64) * w.n + pairs[:, 1]
+    assert np.all(np.diff(key) > 0)
+    assert not np.any(pairs[:, 0] == floor)
+    # the floor pairs with the whole bottom layer
+    op = oracle.broad_partners(w, floor)
+    assert np.array_equal(pairs[pairs[:, 1] == floor], op)
+    assert len(op) == 100 * 100
+    rng = np.random.default_rng(2)
+    bottom = np.where(w.state[W.F_Z, :floor] < 1.5)[0]
+    for p in np.concatenate([rng.choice(bottom, 40, replace=False), rng.choice(floor, 60, replace=False)]):
+        gp = pairs[(pairs[:, 0] == p) | (pairs[:, 1] == p)]
+        assert np.array_equal(oracle.broad_partners(w, int(p)), gp), p
+    ids, nc = oracle.clusters(w.n, pairs, w.is_static)
+    assert np.array_equal(g["ids"], ids) and g["n_clusters"] == nc
+    # sampled pairs: floor pairs in contact at the start (status 1), two that
+    # are not, and pairs between lattice neighbours
+    fl = np.where(pairs[:, 1] == floor)[0]
+    touching = fl[g["flag"][fl] == 1]
+    apart = fl[g["flag"][fl] == 0]
+    assert len(touching) > 100
+    others = np.where(pairs[:, 1] != floor)[0]
+    idx = np.unique(np.concatenate([rng.choice(touching, 6, replace=False), rng.choice(apart, 2, replace=False),
+                                    rng.choice(others, 12, replace=False)]))
+    _check_sampled_pairs(w, g, idx)
