@@ -61,10 +61,10 @@ def lib():
             L.demo_broad_partners.argtypes = [dp, u8p, C.c_int64, i64p, fp, C.c_int64, C.c_int64, i32p,
                                               C.c_int64]
             L.demo_broad_partners.restype = C.c_int64
-            L.demo_narrow_phase.argtypes = [dp, C.c_int64, i64p, fp, C.c_int64, i32p, C.c_int64,
+            L.demo_narrow_phase.argtypes = [dp, u8p, C.c_int64, i64p, fp, C.c_int64, i32p, C.c_int64,
                                             dp, dp, dp, dp, i32p, u8p, i32p, dp, C.c_int64, C.c_int]
             L.demo_narrow_phase.restype = C.c_int64
-            L.demo_collision_times.argtypes = [dp, C.c_int64, i64p, fp, C.c_int64, i32p, C.c_int64,
+            L.demo_collision_times.argtypes = [dp, u8p, C.c_int64, i64p, fp, C.c_int64, i32p, C.c_int64,
                                                C.c_int, C.c_double, dp, u8p, i32p, i32p, C.c_int]
             L.demo_collision_times.restype = None
             L.demo_clusters.argtypes = [C.c_int64, i32p, C.c_int64, u8p, i32p]
@@ -153,9 +153,7 @@ def broad_partners(w, p):
 
 def narrow_phase(w, pairs, t_eval=None, n_threads=None, cap=None):
     """Returns dict(dmin, pa, pb, tri_ab, flag, contacts (c,3) int32, geom (c,7))."""
-    state = _c(w.state, np.float64)
-    off = _c(w.tri_off, np.int64)
-    tris = _c(w.tris, np.float32)
+    state, sta, off, tris = _geometry(w)
     pairs = _c(pairs, np.int32).reshape(-1, 2)
     m = len(pairs)
     te = None if t_eval is None else _c(t_eval, np.float64)
@@ -168,7 +166,8 @@ def narrow_phase(w, pairs, t_eval=None, n_threads=None, cap=None):
         contacts = np.zeros((cap, 3), np.int32)
         geom = np.zeros((cap, 7))
         nc = lib().demo_narrow_phase(
-            _p(state, C.c_double), state.shape[1], _p(off, C.c_int64), _p(tris, C.c_float), tris.shape[1],
+            _p(state, C.c_double), _p(sta, C.c_uint8), state.shape[1], _p(off, C.c_int64), _p(tris, C.c_float),
+            tris.shape[1],
             _p(pairs, C.c_int32), m, None if te is None else _p(te, C.c_double),
             _p(dmin, C.c_double), _p(pa, C.c_double), _p(pb, C.c_double), _p(tri_ab, C.c_int32),
             _p(flag, C.c_uint8), _p(contacts, C.c_int32), _p(geom, C.c_double), cap, nt)
@@ -180,9 +179,7 @@ def narrow_phase(w, pairs, t_eval=None, n_threads=None, cap=None):
 
 def collision_times(w, pairs, K=None, tol=None, n_threads=None):
     """Returns dict(t_coll, status, tri_ab, n_evals)."""
-    state = _c(w.state, np.float64)
-    off = _c(w.tri_off, np.int64)
-    tris = _c(w.tris, np.float32)
+    state, sta, off, tris = _geometry(w)
     pairs = _c(pairs, np.int32).reshape(-1, 2)
     m = len(pairs)
     K = w.K if K is None else K
@@ -192,7 +189,8 @@ def collision_times(w, pairs, K=None, tol=None, n_threads=None):
     tri_ab = np.zeros((m, 2), np.int32)
     ne = np.zeros(m, np.int32)
     lib().demo_collision_times(
-        _p(state, C.c_double), state.shape[1], _p(off, C.c_int64), _p(tris, C.c_float), tris.shape[1],
+        _p(state, C.c_double), _p(sta, C.c_uint8), state.shape[1], _p(off, C.c_int64), _p(tris, C.c_float),
+        tris.shape[1],
         _p(pairs, C.c_int32), m, int(K), float(tol), _p(t, C.c_double), _p(status, C.c_uint8),
         _p(tri_ab, C.c_int32), _p(ne, C.c_int32), n_threads or default_threads())
     return dict(t_coll=t, status=status, tri_ab=tri_ab, n_evals=ne)

@@ -487,11 +487,19 @@ static void eval_pair(const double *state, int64_t n, const int64_t *tri_off, co
   free(WB);
 }
 
-static double pair_start(const double *s, int64_t n, int64_t i, int64_t j) {
+/* Pair interval (Section 3, Eq. "max time span between two particles"):
+ * ts = min of the members' t_cur, T = min of their steps.  A static member
+ * has no time step of its own (static objects take no part in the
+ * extrapolation, Section 3): then the interval is the moving member's. */
+static double pair_start(const double *s, const uint8_t *sta, int64_t n, int64_t i, int64_t j) {
+  if (sta && sta[j] && !sta[i]) return s[FTCUR * n + i];
+  if (sta && sta[i] && !sta[j]) return s[FTCUR * n + j];
   double a = s[FTCUR * n + i], b = s[FTCUR * n + j];
   return a < b ? a : b;
 }
-static double pair_span(const double *s, int64_t n, int64_t i, int64_t j) {
+static double pair_span(const double *s, const uint8_t *sta, int64_t n, int64_t i, int64_t j) {
+  if (sta && sta[j] && !sta[i]) return s[FDT * n + i];
+  if (sta && sta[i] && !sta[j]) return s[FDT * n + j];
   double a = s[FDT * n + i], b = s[FDT * n + j];
   return a < b ? a : b;
 }
@@ -500,6 +508,7 @@ static double pair_span(const double *s, int64_t n, int64_t i, int64_t j) {
 /* threading over independent pairs */
 typedef struct {
   const double *state;
+  const uint8_t *is_static;
   int64_t n;
   const int64_t *tri_off;
   const float *tris;
@@ -534,7 +543,7 @@ static void collision_time_one(job *J, int64_t k) {
   const double *s = J->state;
   int64_t n = J->n;
   double eps = eps_pair(s, n, i, j);
-  double ts = pair_start(s, n, i, j), T = pair_span(s, n, i, j);
+  double ts = pair_start(s, J->is_static, n, i, j), T = pair_span(s, J->is_static, n, i, j);
   pair_eval e;
   memset(&e, 0, sizeof e);
   int evals = 0;
@@ -595,7 +604,7 @@ static void *worker(void *arg) {
     if (k >= J->m) break;
     if (J->mode == 0) {
       int64_t i = J->pairs[2 * k], j = J->pairs[2 * k + 1];
-      double t = J->t_eval ? J->t_eval[k] : pair_start(J->state, J->n, i, j);
+      double t = J->t_eval ? J->t_eval[k] : pair_start(J->state, J->is_static, J->n, i, j);
       eval_pair(J->state, J->n, J->tri_off, J->tris, J->n_tris, i, j, t, 1, &J->ev[k]);
     } else {
       collision_time_one(J, k);
@@ -619,13 +628,14 @@ static void run_job(job *J, int n_threads) {
   for (int k = 0; k < started; ++k) pthread_join(th[k], NULL);
 }
 
-int64_t demo_narrow_phase(const double *state, int64_t n, const int64_t *tri_off, const float *tris,
-                          int64_t n_tris, const int32_t *pairs, int64_t m, const double *t_eval,
-                          double *dmin, double *pa, double *pb, int32_t *tri_ab, uint8_t *flag,
-                          int32_t *contacts, double *geom, int64_t cap, int n_threads) {
+int64_t demo_narrow_phase(const double *state, const uint8_t *is_static, int64_t n, const int64_t *tri_off,
+                          const float *tris, int64_t n_tris, const int32_t *pairs, int64_t m,
+                          const double *t_eval, double *dmin, double *pa, double *pb, int32_t *tri_ab,
+                          uint8_t *flag, int32_t *contacts, double *geom, int64_t cap, int n_threads) {
   job J;
   memset(&J, 0, sizeof J);
   J.state = state;
+  J.is_static = is_static;
   J.n = n;
   J.tri_off = tri_off;
   J.tris = tris;
@@ -662,13 +672,14 @@ int64_t demo_narrow_phase(const double *state, int64_t n, const int64_t *tri_off
   return nc;
 }
 
-void demo_collision_times(const double *state, int64_t n, const int64_t *tri_off, const float *tris,
-                          int64_t n_tris, const int32_t *pairs, int64_t m, int K, double tol,
-                          double *t_coll, uint8_t *status, int32_t *tri_ab, int32_t *n_evals,
+void demo_collision_times(const double *state, const uint8_t *is_static, int64_t n, const int64_t *tri_off,
+                          const float *tris, int64_t n_tris, const int32_t *pairs, int64_t m, int K,
+                          double tol, double *t_coll, uint8_t *status, int32_t *tri_ab, int32_t *n_evals,
                           int n_threads) {
   job J;
   memset(&J, 0, sizeof J);
   J.state = state;
+  J.is_static = is_static;
   J.n = n;
   J.tri_off = tri_off;
   J.tris = tris;

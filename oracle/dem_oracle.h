@@ -53,26 +53,30 @@ int64_t demo_broad_partners(const double *state, const uint8_t *is_static, int64
                             const int64_t *tri_off, const float *tris, int64_t n_tris, int64_t p,
                             int32_t *pairs, int64_t cap);
 
-/* Narrow phase over m pairs at times t_eval[k] (NULL: the pair's start time).
+/* Pair interval of (i, j): ts = min(t_cur_i, t_cur_j), T = min(dt_i, dt_j);
+ * when one member is static (is_static may be NULL) the interval is the
+ * moving member's.
+ *
+ * Narrow phase over m pairs at times t_eval[k] (NULL: the pair's start time).
  * Per pair: dmin, pa[3], pb[3], tri_ab[2] (indices local to each particle),
  * flag (dmin <= eps_pair).  Contacts (all triangle pairs with d <= eps_pair)
  * in (pair, a, b) order: contacts[3*c] = (pair, a, b), geom[7*c] =
  * (d, pa, pb).  Returns the number of contacts (may exceed cap; then only
  * cap are written).  n_threads >= 1 splits the pairs over threads. */
-int64_t demo_narrow_phase(const double *state, int64_t n, const int64_t *tri_off,
-                          const float *tris, int64_t n_tris, const int32_t *pairs, int64_t m,
-                          const double *t_eval, double *dmin, double *pa, double *pb,
-                          int32_t *tri_ab, uint8_t *flag, int32_t *contacts, double *geom,
-                          int64_t cap, int n_threads);
+int64_t demo_narrow_phase(const double *state, const uint8_t *is_static, int64_t n,
+                          const int64_t *tri_off, const float *tris, int64_t n_tris,
+                          const int32_t *pairs, int64_t m, const double *t_eval, double *dmin,
+                          double *pa, double *pb, int32_t *tri_ab, uint8_t *flag,
+                          int32_t *contacts, double *geom, int64_t cap, int n_threads);
 
 /* Collision-time search over m pairs: K uniform samples, then bisection to
  * tol * T.  Outputs t_coll, status (0 none, 1 in contact at start, 2 proper),
  * tri_ab[2] of the closest triangles at the returned time (-1 for status 0),
  * n_evals (number of pair-distance evaluations the search made; may be NULL). */
-void demo_collision_times(const double *state, int64_t n, const int64_t *tri_off,
-                          const float *tris, int64_t n_tris, const int32_t *pairs, int64_t m,
-                          int K, double tol, double *t_coll, uint8_t *status, int32_t *tri_ab,
-                          int32_t *n_evals, int n_threads);
+void demo_collision_times(const double *state, const uint8_t *is_static, int64_t n,
+                          const int64_t *tri_off, const float *tris, int64_t n_tris,
+                          const int32_t *pairs, int64_t m, int K, double tol, double *t_coll,
+                          uint8_t *status, int32_t *tri_ab, int32_t *n_evals, int n_threads);
 
 /* Connected components of the graph over n particles with e edges (pairs of
  * indices, interleaved); edges with a static endpoint are ignored.  id[i] =

@@ -142,6 +142,28 @@ def test_broad_phase_static_is_conservative():
         assert hit <= cand
 
 
+def test_static_member_does_not_limit_the_pair_interval():
+    """A static object has no time step of its own (Section 3): a triangle
+    falling flat onto a static floor triangle collides at t* = (h - eps_pair) / v
+    in the moving particle's interval, although the floor's own t_cur (-1)
+    and step (1e-6) would give an interval that misses it.  Dyadic values."""
+    h, v, eps, dt = 0.25, 128.0, 2.0 ** -6, 2.0 ** -9
+    floor = np.array([[[-8, -8, 0], [8, -8, 0], [0, 8, 0]]], np.float32)
+    tri = np.array([[[-0.5, -0.5, 0], [0.5, -0.5, 0], [0, 0.5, 0]]], np.float32)
+    w = W._assemble("static-interval", [floor, tri], [0, 1], [(0, 0, 0), (0, 0, h)], [(0, 0, 0), (0, 0, -v)],
+                    [(1, 0, 0, 0)] * 2, np.zeros((2, 3)), 0.0, dt, eps, is_static=[1, 0])
+    w.state[W.F_TCUR, 0] = -1.0
+    w.state[W.F_DT, 0] = 1e-6
+    pairs = oracle.broad_phase(w)
+    assert pairs.tolist() == [[1, 0]]
+    r = oracle.narrow_phase(w, pairs)
+    assert r["dmin"][0] == h and r["flag"][0] == 0
+    c = oracle.collision_times(w, pairs)
+    tstar = (h - 2 * eps) / v
+    assert c["status"][0] == 2
+    assert tstar <= c["t_coll"][0] <= tstar + w.tol * dt
+
+
 # ----------------------------------------------------------------------------- narrow phase
 
 def test_narrow_contacts_are_exactly_the_close_triangle_pairs():
