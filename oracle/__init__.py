@@ -69,6 +69,10 @@ def lib():
             L.demo_collision_times.restype = None
             L.demo_clusters.argtypes = [C.c_int64, i32p, C.c_int64, u8p, i32p]
             L.demo_clusters.restype = C.c_int64
+            L.demo_lts_sweep.argtypes = [dp, dp, u8p, C.c_int64, i64p, fp, C.c_int64, C.c_int, C.c_double,
+                                         C.c_double, C.c_double, dp, C.c_int, i32p, C.c_int64, u8p, dp, i32p,
+                                         u8p, dp, i64p, i64p, C.c_int]
+            L.demo_lts_sweep.restype = C.c_int64
             _lib = L
     return _lib
 
@@ -203,3 +207,39 @@ def clusters(n, edges, is_static=None):
     ids = np.zeros(n, np.int32)
     c = lib().demo_clusters(n, _p(edges, C.c_int32), len(edges), _p(st, C.c_uint8), _p(ids, C.c_int32))
     return ids, int(c)
+
+
+def lts_sweep(w, old, dt_max, alpha=2.0, gravity=(0.0, 0.0, 0.0), zero_on_contact=True, n_threads=None):
+    """One local-time-stepping sweep; updates w.state (current snapshot) and
+    ``old`` (old snapshot, same layout) in place.  Returns dict(pairs, status,
+    t_coll, ids, active, t_global, rollbacks, rollbacks_before_old)."""
+    assert w.state.flags["C_CONTIGUOUS"] and w.state.dtype == np.float64
+    assert old.flags["C_CONTIGUOUS"] and old.dtype == np.float64 and old.shape == w.state.shape
+    _, sta, off, tris = _geometry(w)
+    n = w.n
+    g = np.asarray(gravity, np.float64)
+    ids = np.zeros(n, np.int32)
+    active = np.zeros(n, np.uint8)
+    tg = np.zeros(1)
+    rb = np.zeros(1, np.int64)
+    rbb = np.zeros(1, np.int64)
+    cap = 1024
+    while True:
+        cur0, old0 = w.state.copy(), old.copy()
+        pairs = np.zeros((cap, 2), np.int32)
+        status = np.zeros(cap, np.uint8)
+        tcol = np.zeros(cap)
+        m = lib().demo_lts_sweep(
+            _p(w.state, C.c_double), _p(old, C.c_double), _p(sta, C.c_uint8), n, _p(off, C.c_int64),
+            _p(tris, C.c_float), tris.shape[1], int(w.K), float(w.tol), float(dt_max), float(alpha),
+            _p(g, C.c_double), int(bool(zero_on_contact)), _p(pairs, C.c_int32), cap, _p(status, C.c_uint8),
+            _p(tcol, C.c_double), _p(ids, C.c_int32), _p(active, C.c_uint8), _p(tg, C.c_double),
+            _p(rb, C.c_int64), _p(rbb, C.c_int64), n_threads or default_threads())
+        if m <= cap:
+            return dict(pairs=pairs[:m].copy(), status=status[:m].copy(), t_coll=tcol[:m].copy(), ids=ids,
+                        active=active, t_global=float(tg[0]), rollbacks=int(rb[0]),
+                        rollbacks_before_old=int(rbb[0]))
+        # too many pairs for the outputs: undo and run again with room for all
+        w.state[...] = cur0
+        old[...] = old0
+        cap = int(m)

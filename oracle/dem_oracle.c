@@ -60,7 +60,8 @@ static void st(double *p, vec3 v) { p[0] = v.x; p[1] = v.y; p[2] = v.z; }
  * trigonometry.  Truncation error < 1e-17 for phi <= 1.5. */
 #define POSE_TERMS 10
 
-void demo_pose(const double *state, int64_t n, int64_t p, double t, double R[9], double X[3]) {
+/* unit quaternion (w, x, y, z) and centre of particle p at time t */
+static void pose_q(const double *state, int64_t n, int64_t p, double t, double Q[4], double X[3]) {
   const double *s = state;
   double h = t - s[FTCUR * n + p];
   vec3 w = mk(s[FWX * n + p], s[FWY * n + p], s[FWZ * n + p]);
@@ -82,6 +83,19 @@ void demo_pose(const double *state, int64_t n, int64_t p, double t, double R[9],
   double rx = pw * qx + px * qw + py * qz - pz * qy;
   double ry = pw * qy - px * qz + py * qw + pz * qx;
   double rz = pw * qz + px * qy - py * qx + pz * qw;
+  Q[0] = rw;
+  Q[1] = rx;
+  Q[2] = ry;
+  Q[3] = rz;
+  X[0] = s[FX * n + p] + s[FVX * n + p] * h;
+  X[1] = s[FY * n + p] + s[FVY * n + p] * h;
+  X[2] = s[FZ * n + p] + s[FVZ * n + p] * h;
+}
+
+void demo_pose(const double *state, int64_t n, int64_t p, double t, double R[9], double X[3]) {
+  double Q[4];
+  pose_q(state, n, p, t, Q, X);
+  double rw = Q[0], rx = Q[1], ry = Q[2], rz = Q[3];
   /* rotation matrix of the unit quaternion (row-major) */
   R[0] = 1.0 - 2.0 * (ry * ry + rz * rz);
   R[1] = 2.0 * (rx * ry - rw * rz);
@@ -92,9 +106,6 @@ void demo_pose(const double *state, int64_t n, int64_t p, double t, double R[9],
   R[6] = 2.0 * (rx * rz - rw * ry);
   R[7] = 2.0 * (ry * rz + rw * rx);
   R[8] = 1.0 - 2.0 * (rx * rx + ry * ry);
-  X[0] = s[FX * n + p] + s[FVX * n + p] * h;
-  X[1] = s[FY * n + p] + s[FVY * n + p] * h;
-  X[2] = s[FZ * n + p] + s[FVZ * n + p] * h;
 }
 
 /* world position of body-frame vertex b: R b + X, rows left to right */
@@ -722,4 +733,161 @@ int64_t demo_clusters(int64_t n, const int32_t *edges, int64_t e, const uint8_t 
   for (int64_t i = 0; i < n; ++i)
     if (id[i] == (int32_t)i) ++c;
   return c;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One sweep of the local-time-stepping cycle (paper Section 2.2, the
+ * substeps of a time step; Section 3, particle step sizes; Section 4, cluster
+ * consolidation; Section 5, time step size; cluster masking and snapshot
+ * roll-over).  Each substep below is written out as the paper orders them;
+ * the collision itself (the impulse solver) is outside the method's contact
+ * detection and replaced by a stand-in update (velocities zeroed on contact,
+ * gravity otherwise).
+ *
+ * cur[DEMO_NFIELDS][n]: current snapshot (x, v, q, w, t_cur; dt is written);
+ * old[DEMO_NFIELDS][n]: old snapshot (x, q, t_cur fields) with the v and w
+ * that carried the particle from it to the current snapshot (other fields
+ * unused).  Static particles are never changed. */
+int64_t demo_lts_sweep(double *cur, double *old, const uint8_t *is_static, int64_t n, const int64_t *tri_off,
+                       const float *tris, int64_t n_tris, int K, double tol, double dt_max, double alpha,
+                       const double gravity[3], int zero_on_contact, int32_t *pairs_out, int64_t cap,
+                       uint8_t *status_out, double *t_coll_out, int32_t *cluster_id, uint8_t *active,
+                       double *t_global, int64_t *rollbacks, int64_t *rollbacks_before_old, int n_threads) {
+  /* 1. particle step sizes (Eq. "damped particle time step size"): a creeping
+   *    average of the previous step, capped by the global span; no history
+   *    (t_old = t_cur) gives the global span */
+  for (int64_t p = 0; p < n; ++p) {
+    if (is_st(is_static, p)) continue;
+    double tc = cur[FTCUR * n + p], to = old[FTCUR * n + p];
+    double d = tc > to ? alpha * (tc - to) : dt_max;
+    cur[FDT * n + p] = d < dt_max ? d : dt_max;
+  }
+  /* 2. candidates over each particle's own step */
+  int64_t m = demo_broad_phase(cur, is_static, n, tri_off, tris, n_tris, pairs_out, 0);
+  int32_t *pairs = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)(m > 0 ? m : 1));
+  demo_broad_phase(cur, is_static, n, tri_off, tris, n_tris, pairs, m);
+  /* 3. clusters of the candidate graph */
+  demo_clusters(n, pairs, m, is_static, cluster_id);
+  /* 4. consolidation: every member of a cluster rolls back to the cluster's
+   *    earliest time stamp by interpolating between its old and current
+   *    snapshots (free flight from the old snapshot with the velocities that
+   *    produced the current one: linear in x, the slerp geodesic in q), and
+   *    takes the cluster's step (the smallest member step, Eq. "cluster time
+   *    step") */
+  double *tmin = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double *dtc = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double *tnew = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  for (int64_t c = 0; c < n; ++c) tmin[c] = dtc[c] = INFINITY;
+  for (int64_t p = 0; p < n; ++p) {
+    if (is_st(is_static, p)) continue;
+    int64_t c = cluster_id[p];
+    if (cur[FTCUR * n + p] < tmin[c]) tmin[c] = cur[FTCUR * n + p];
+    if (cur[FDT * n + p] < dtc[c]) dtc[c] = cur[FDT * n + p];
+  }
+  int64_t rb = 0, rb_bad = 0;
+  for (int64_t p = 0; p < n; ++p) {
+    if (is_st(is_static, p)) continue;
+    int64_t c = cluster_id[p];
+    if (cur[FTCUR * n + p] > tmin[c]) {
+      double Q[4], X[3];
+      pose_q(old, n, p, tmin[c], Q, X);
+      ++rb;
+      if (tmin[c] < old[FTCUR * n + p]) ++rb_bad; /* would contradict Theorem "valid snapshots" */
+      cur[FX * n + p] = X[0];
+      cur[FY * n + p] = X[1];
+      cur[FZ * n + p] = X[2];
+      cur[FQW * n + p] = Q[0];
+      cur[FQX * n + p] = Q[1];
+      cur[FQY * n + p] = Q[2];
+      cur[FQZ * n + p] = Q[3];
+      cur[FTCUR * n + p] = tmin[c];
+    }
+    cur[FDT * n + p] = dtc[c];
+  }
+  /* 5. collision time stamps of every candidate pair over the (now common)
+   *    cluster interval */
+  uint8_t *status = (uint8_t *)malloc((size_t)(m > 0 ? m : 1));
+  double *tcol = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+  int32_t *tab = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)(m > 0 ? m : 1));
+  demo_collision_times(cur, is_static, n, tri_off, tris, n_tris, pairs, m, K, tol, tcol, status, tab, NULL,
+                       n_threads);
+  /* 6. effective step of a cluster: its new time stamp is the earliest proper
+   *    collision of its pairs, else the end of its interval (statuses 0 and 1
+   *    do not constrain it) */
+  for (int64_t c = 0; c < n; ++c) tnew[c] = INFINITY;
+  for (int64_t p = 0; p < n; ++p) {
+    if (is_st(is_static, p)) continue;
+    int64_t c = cluster_id[p];
+    if (c == p) tnew[c] = tmin[c] + dtc[c];
+  }
+  for (int64_t k = 0; k < m; ++k) {
+    int64_t c = cluster_id[pairs[2 * k]];
+    if (status[k] == 2 && tcol[k] < tnew[c]) tnew[c] = tcol[k];
+  }
+  /* 7. masking (Eq. "cluster masking: min collision time"): the earliest new
+   *    time stamp over all clusters; clusters whose time stamp lies beyond it
+   *    do not advance */
+  double tg = INFINITY;
+  for (int64_t c = 0; c < n; ++c)
+    if (tnew[c] < tg) tg = tnew[c];
+  *t_global = tg;
+  /* 8. stand-in for the collision update: particles in contact at the end of
+   *    the step (touching at its start, or attaining the cluster's collision
+   *    time) stop; the others accelerate under gravity */
+  uint8_t *touch = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+  for (int64_t k = 0; k < m; ++k) {
+    int64_t i = pairs[2 * k], j = pairs[2 * k + 1];
+    int64_t c = cluster_id[i];
+    if (status[k] == 1 || (status[k] == 2 && tcol[k] == tnew[c])) {
+      touch[i] = 1;
+      if (!is_st(is_static, j)) touch[j] = 1;
+    }
+  }
+  /* 9. advance the active clusters to their new time stamp and roll the
+   *    snapshots over: old <- current, current <- new */
+  for (int64_t p = 0; p < n; ++p) {
+    active[p] = 0;
+    if (is_st(is_static, p)) continue;
+    int64_t c = cluster_id[p];
+    if (!(tmin[c] <= tg)) continue;
+    active[p] = 1;
+    double h = tnew[c] - cur[FTCUR * n + p];
+    const int f[] = {FX, FY, FZ, FVX, FVY, FVZ, FQW, FQX, FQY, FQZ, FWX, FWY, FWZ, FTCUR};
+    for (int q = 0; q < 14; ++q) old[f[q] * n + p] = cur[f[q] * n + p];
+    double Q[4], X[3];
+    pose_q(old, n, p, tnew[c], Q, X);
+    cur[FX * n + p] = X[0];
+    cur[FY * n + p] = X[1];
+    cur[FZ * n + p] = X[2];
+    cur[FQW * n + p] = Q[0];
+    cur[FQX * n + p] = Q[1];
+    cur[FQY * n + p] = Q[2];
+    cur[FQZ * n + p] = Q[3];
+    cur[FTCUR * n + p] = tnew[c];
+    if (zero_on_contact && touch[p]) {
+      for (int q = 3; q < 6; ++q) cur[q * n + p] = 0.0;
+      for (int q = 10; q < 13; ++q) cur[q * n + p] = 0.0;
+    } else {
+      cur[FVX * n + p] = cur[FVX * n + p] + gravity[0] * h;
+      cur[FVY * n + p] = cur[FVY * n + p] + gravity[1] * h;
+      cur[FVZ * n + p] = cur[FVZ * n + p] + gravity[2] * h;
+    }
+  }
+  for (int64_t k = 0; k < m && k < cap; ++k) {
+    pairs_out[2 * k] = pairs[2 * k];
+    pairs_out[2 * k + 1] = pairs[2 * k + 1];
+    status_out[k] = status[k];
+    t_coll_out[k] = tcol[k];
+  }
+  *rollbacks = rb;
+  *rollbacks_before_old = rb_bad;
+  free(pairs);
+  free(tmin);
+  free(dtc);
+  free(tnew);
+  free(status);
+  free(tcol);
+  free(tab);
+  free(touch);
+  return m;
 }

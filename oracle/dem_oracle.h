@@ -85,6 +85,27 @@ void demo_collision_times(const double *state, const uint8_t *is_static, int64_t
 int64_t demo_clusters(int64_t n, const int32_t *edges, int64_t e, const uint8_t *is_static,
                       int32_t *id);
 
+/* One sweep of the local-time-stepping cycle: particle steps
+ * dt_p = min(alpha (t_cur - t_old), dt_max) (dt_max without history), broad
+ * phase, clusters, consolidation (members roll back to the cluster's earliest
+ * t_cur by free flight from the old snapshot, and take the smallest member
+ * step), collision times, each cluster's new time stamp (earliest status-2
+ * time, else t_min + dt), masking (clusters with t_min > the global minimum
+ * of the new time stamps stay), advance and roll-over of the others, with the
+ * stand-in update: v, w zeroed for particles in contact, else
+ * v += gravity * step.  cur and old are [DEMO_NFIELDS][n] and are updated in
+ * place (old holds x, q, t_cur of the old snapshot and the v, w that carried
+ * the particle to cur).  Outputs: candidate pairs, their status and t_coll
+ * (up to cap), cluster ids, active[n], the global minimum, the number of
+ * roll-backs and of roll-backs to before a particle's old snapshot.  Returns
+ * the number of candidate pairs. */
+int64_t demo_lts_sweep(double *cur, double *old, const uint8_t *is_static, int64_t n,
+                       const int64_t *tri_off, const float *tris, int64_t n_tris, int K, double tol,
+                       double dt_max, double alpha, const double gravity[3], int zero_on_contact,
+                       int32_t *pairs, int64_t cap, uint8_t *status, double *t_coll,
+                       int32_t *cluster_id, uint8_t *active, double *t_global, int64_t *rollbacks,
+                       int64_t *rollbacks_before_old, int n_threads);
+
 #ifdef __cplusplus
 }
 #endif
