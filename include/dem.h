@@ -142,7 +142,9 @@ typedef struct {
   int64_t pairs_done;       /* pairs processed */
   int64_t kernel_launches;  /* kernels launched by this context (host-side count) */
   int64_t tile_pairs;       /* 320 x 320-triangle tile pairs scanned (not culled by tile spheres) */
-  int64_t reserved[5];
+  int64_t rollbacks;        /* local time stepping: particles rolled back by consolidation */
+  int64_t rollbacks_before_old; /* ... of which to before their old snapshot (0 if the theorem holds) */
+  int64_t reserved[3];
 } dem_stats;
 
 /* Create a context: validates and copies *cfg, allocates scratch for the
@@ -189,7 +191,9 @@ dem_status dem_narrow_phase(dem_ctx *ctx, const dem_particles *P, const int32_t 
 /* Collision time stamps (paper Section 5, "Time step size calculation": case
  * distinction, narrowing and widening; interval of Eq. "max time span between
  * two particles").  Pair interval [ts, ts + T], ts = min(t_cur_i, t_cur_j),
- * T = min(dt_i, dt_j); f(t) = minimum triangle-pair distance at t.
+ * T = min(dt_i, dt_j); with a static member (no step of its own, Section 3)
+ * the moving member's t_cur and dt.  f(t) = minimum triangle-pair distance
+ * at t.  (The narrow phase with t_eval = NULL evaluates at this ts.)
  *   f(ts) <= eps_pair                  -> status 1, t_coll = ts + T
  *   first k in 1..K: f(ts + T k/K) <= eps_pair -> bisection on
  *     [ts + T (k-1)/K, ts + T k/K] until the bracket is <= tol T,
@@ -222,6 +226,59 @@ dem_status dem_detect(dem_ctx *ctx, const dem_particles *P, const int32_t *pairs
 dem_status dem_clusters(dem_ctx *ctx, int64_t n, const int32_t *edges, int64_t max_edges,
                         const int64_t *n_edges, const uint8_t *is_static, int32_t *cluster_id,
                         int64_t *n_clusters, void *stream);
+
+/* Parameters of one local-time-stepping sweep. */
+typedef struct {
+  double dt_max;           /* the global admissible time span (> 0) */
+  double alpha;            /* damping of the particle step (Section 3; the paper uses 2) */
+  double gravity[3];       /* stand-in update: acceleration of particles not in contact */
+  int32_t zero_on_contact; /* stand-in update: particles in contact stop (v = w = 0) */
+  int32_t reserved;
+} dem_lts_params;
+
+/* Outputs of one sweep (caller-owned device arrays). */
+typedef struct {
+  int32_t *pairs;        /* [max_pairs][2] the sweep's candidate pairs */
+  int64_t max_pairs;
+  int64_t *n_pairs;      /* [1] */
+  double *t_coll;        /* [max_pairs] collision time stamps of the pairs */
+  uint8_t *status;       /* [max_pairs] their status (0, 1, 2) */
+  int32_t *tri_ab;       /* [max_pairs][2] */
+  int32_t *cluster_id;   /* [n] clusters of the candidate graph (-1: static) */
+  int64_t *n_clusters;   /* [1] */
+  uint8_t *active;       /* [n] 1 if the particle advanced in this sweep */
+  double *t_global;      /* [1] earliest new time stamp over all clusters (the masking bound) */
+} dem_lts_out;
+
+/* One sweep of the local-time-stepping cycle (paper Section 2.2 substeps,
+ * Sections 3-5).  In order, all on the stream, without host round trips:
+ *  1. particle steps dt_p = min(alpha (t_cur - t_old), dt_max), dt_max when
+ *     t_old = t_cur (Eq. "damped particle time step size"), written to cur;
+ *  2. candidate pairs (dem_build_candidates) and 3. their clusters;
+ *  4. consolidation (Section 4): every member of a cluster goes back to the
+ *     cluster's earliest t_cur by free flight from its old snapshot (the
+ *     interpolation between the snapshots) and takes the cluster step (the
+ *     smallest member step, Eq. "cluster time step");
+ *  5. collision times of every pair (dem_collision_times);
+ *  6. each cluster's new time stamp: its earliest status-2 time, else
+ *     t_min + step; 7. masking: t_global = the minimum over clusters;
+ *     clusters with t_min > t_global do not advance;
+ *  8. the others advance to their new time stamp in free flight and roll
+ *     their snapshots over (old <- current, current <- new), with the
+ *     stand-in for the collision update: particles in contact at the end of
+ *     the step (status 1, or status 2 at the cluster's time) stop when
+ *     zero_on_contact, the others gain gravity * (advanced time).
+ * cur, old: device [DEM_NFIELDS][n] binary64, read and written; cur is the
+ * current snapshot, old the previous one (x, q, t_cur fields) with the v, w
+ * that carried the particle to cur; start a run with old = cur.  P gives the
+ * geometry (n, is_static, tri_off, tris, n_tris); P->state must be NULL or
+ * cur.  Static particles are never changed.  The results equal the oracle's
+ * sweep bit for bit (every comparison and rounding is the binary64 one).
+ * Errors: DEM_ERR_ARG for bad arguments, DEM_ERR_CAPACITY when
+ * out->max_pairs exceeds the context's max_pairs; a device capacity overflow
+ * is reported by dem_check. */
+dem_status dem_lts_sweep(dem_ctx *ctx, const dem_particles *P, double *cur, double *old,
+                         const dem_lts_params *prm, const dem_lts_out *out, void *stream);
 
 /* Candidate pairs without any device allocation (no context needed).  The
  * paper has no counterpart: this is for callers that cannot allocate device

@@ -13,7 +13,7 @@ struct dem_ctx {
   int device;
   int num_sms;
   std::string last_error;
-  void *allocs[32];
+  void *allocs[48];
   int n_allocs;
 };
 
@@ -109,7 +109,9 @@ dem_status dem_create(const dem_config *cfg, dem_ctx **out) {
             alloc(c, &S.rho_max, 1) && alloc(c, &S.static_ids, np) && alloc(c, &S.n_static, 1) &&
             alloc(c, &S.spose, 12 * np) && alloc(c, &S.sbox, 6 * np) && alloc(c, &S.st_keys, 3 * nc) && alloc(c, &S.st_geom, 7 * nc) &&
             alloc(c, &S.st_count, 1) && alloc(c, &S.pc, nq) && alloc(c, &S.po, nq) && alloc(c, &S.pcur, nq) &&
-            alloc(c, &S.sidx, nc) && alloc(c, &S.tile_sph, S.cap_tiles);
+            alloc(c, &S.sidx, nc) && alloc(c, &S.tile_sph, S.cap_tiles) && alloc(c, &S.lts_tmin, np) &&
+            alloc(c, &S.lts_step, np) && alloc(c, &S.lts_tnew, np) && alloc(c, &S.lts_tglob, 1) &&
+            alloc(c, &S.lts_touch, np);
   if (!ok) {
     dem_destroy(c);
     return DEM_ERR_CUDA;
@@ -201,6 +203,28 @@ dem_status dem_clusters(dem_ctx *c, int64_t n, const int32_t *edges, int64_t max
   cudaError_t e = dem::launch_clusters(n, edges, max_edges, n_edges, is_static, cluster_id, n_clusters, c->S,
                                        static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(c, e, "clusters");
+  return DEM_OK;
+}
+
+dem_status dem_lts_sweep(dem_ctx *c, const dem_particles *P, double *cur, double *old, const dem_lts_params *prm,
+                         const dem_lts_out *out, void *stream) {
+  if (!c) return DEM_ERR_ARG;
+  if (!P || !prm || !out) return fail(c, DEM_ERR_ARG, "lts_sweep: null argument");
+  if (P->state && P->state != cur) return fail(c, DEM_ERR_ARG, "lts_sweep: P->state must be NULL or cur");
+  dem_particles G = *P;
+  G.state = cur;
+  dem_status st = check_particles(c, &G);
+  if (st != DEM_OK) return st;
+  if (P->n > 0 && (!cur || !old || !out->cluster_id || !out->active))
+    return fail(c, DEM_ERR_ARG, "lts_sweep: null state or per-particle output");
+  if (!out->n_pairs || !out->n_clusters || !out->t_global || out->max_pairs < 0 ||
+      (out->max_pairs > 0 && (!out->pairs || !out->t_coll || !out->status || !out->tri_ab)))
+    return fail(c, DEM_ERR_ARG, "lts_sweep: bad outputs");
+  if (out->max_pairs > c->S.cap_pairs) return fail(c, DEM_ERR_CAPACITY, "lts_sweep: max_pairs exceeds capacity");
+  if (!(prm->dt_max > 0.0) || !(prm->alpha > 0.0)) return fail(c, DEM_ERR_ARG, "lts_sweep: dt_max, alpha > 0");
+  cudaError_t e = dem::launch_lts(c->cfg.precision, c->cfg.K, c->cfg.bisect_tol, G, cur, old, *prm, *out, c->S,
+                                  c->num_sms, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "lts_sweep");
   return DEM_OK;
 }
 

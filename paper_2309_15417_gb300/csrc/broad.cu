@@ -26,15 +26,6 @@ namespace {
 
 using D = OpsD;
 
-// order-preserving unsigned key of a double (for atomic min / max)
-__device__ __forceinline__ unsigned long long okey(double x) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
-__device__ __forceinline__ double okey_value(unsigned long long k) {
-  return __longlong_as_double(static_cast<long long>((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
-}
-
 // swept spheres of all particles; max rho over moving particles; static
 // particles listed with their pose at t_cur and an empty box
 __global__ void k_prep(int64_t n, const double *st, const uint8_t *is_static, Sphere4 *sph,

@@ -259,8 +259,9 @@ __device__ __forceinline__ void pose_reciprocals(double *rc, double *rs) {
   }
 }
 
-__device__ __forceinline__ void pose_exact(const double *st, int64_t n, int64_t p, double t,
-                                           const double *rc, const double *rs, double R[9], double X[3]) {
+// quaternion (w, x, y, z) and centre of the free-flight pose at t
+__device__ __forceinline__ void pose_quat_exact(const double *st, int64_t n, int64_t p, double t,
+                                                const double *rc, const double *rs, double Q[4], double X[3]) {
   using O = OpsD;
   const double h = O::sub(t, st[13 * n + p]);
   const double wx = st[10 * n + p], wy = st[11 * n + p], wz = st[12 * n + p];
@@ -276,10 +277,21 @@ __device__ __forceinline__ void pose_exact(const double *st, int64_t n, int64_t 
   const double pw = c, px = O::mul(g, wx), py = O::mul(g, wy), pz = O::mul(g, wz);
   const double qw = st[6 * n + p], qx = st[7 * n + p], qy = st[8 * n + p], qz = st[9 * n + p];
   // Hamilton product dq (x) q0, each component summed left to right
-  const double rw = O::sub(O::sub(O::sub(O::mul(pw, qw), O::mul(px, qx)), O::mul(py, qy)), O::mul(pz, qz));
-  const double rx = O::sub(O::add(O::add(O::mul(pw, qx), O::mul(px, qw)), O::mul(py, qz)), O::mul(pz, qy));
-  const double ry = O::add(O::add(O::sub(O::mul(pw, qy), O::mul(px, qz)), O::mul(py, qw)), O::mul(pz, qx));
-  const double rz = O::add(O::sub(O::add(O::mul(pw, qz), O::mul(px, qy)), O::mul(py, qx)), O::mul(pz, qw));
+  Q[0] = O::sub(O::sub(O::sub(O::mul(pw, qw), O::mul(px, qx)), O::mul(py, qy)), O::mul(pz, qz));
+  Q[1] = O::sub(O::add(O::add(O::mul(pw, qx), O::mul(px, qw)), O::mul(py, qz)), O::mul(pz, qy));
+  Q[2] = O::add(O::add(O::sub(O::mul(pw, qy), O::mul(px, qz)), O::mul(py, qw)), O::mul(pz, qx));
+  Q[3] = O::add(O::sub(O::add(O::mul(pw, qz), O::mul(px, qy)), O::mul(py, qx)), O::mul(pz, qw));
+  X[0] = O::add(st[0 * n + p], O::mul(st[3 * n + p], h));
+  X[1] = O::add(st[1 * n + p], O::mul(st[4 * n + p], h));
+  X[2] = O::add(st[2 * n + p], O::mul(st[5 * n + p], h));
+}
+
+__device__ __forceinline__ void pose_exact(const double *st, int64_t n, int64_t p, double t,
+                                           const double *rc, const double *rs, double R[9], double X[3]) {
+  using O = OpsD;
+  double Q[4];
+  pose_quat_exact(st, n, p, t, rc, rs, Q, X);
+  const double rw = Q[0], rx = Q[1], ry = Q[2], rz = Q[3];
   R[0] = O::sub(1.0, O::mul(2.0, O::add(O::mul(ry, ry), O::mul(rz, rz))));
   R[1] = O::mul(2.0, O::sub(O::mul(rx, ry), O::mul(rw, rz)));
   R[2] = O::mul(2.0, O::add(O::mul(rx, rz), O::mul(rw, ry)));
@@ -289,9 +301,6 @@ __device__ __forceinline__ void pose_exact(const double *st, int64_t n, int64_t 
   R[6] = O::mul(2.0, O::sub(O::mul(rx, rz), O::mul(rw, ry)));
   R[7] = O::mul(2.0, O::add(O::mul(ry, rz), O::mul(rw, rx)));
   R[8] = O::sub(1.0, O::mul(2.0, O::add(O::mul(rx, rx), O::mul(ry, ry))));
-  X[0] = O::add(st[0 * n + p], O::mul(st[3 * n + p], h));
-  X[1] = O::add(st[1 * n + p], O::mul(st[4 * n + p], h));
-  X[2] = O::add(st[2 * n + p], O::mul(st[5 * n + p], h));
 }
 
 // World position R b + X of a body-frame vertex: ((R0 bx + R1 by) + R2 bz) + X0.

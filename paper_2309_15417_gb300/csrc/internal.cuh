@@ -26,6 +26,8 @@ enum {
   ST_PAIRS,
   ST_HOST_LAUNCHES,  // slot of dem_stats.kernel_launches (host-side count)
   ST_TILES,
+  ST_ROLLBACK,
+  ST_ROLLBACK_BAD,
   ST_N = 16
 };
 
@@ -75,6 +77,12 @@ struct Scratch {
   int64_t cap_triangles;
   int64_t cap_tiles;
   float4 *tile_sph;               // [cap_tiles]
+  // local time stepping: per-cluster order keys (indexed by cluster id)
+  unsigned long long *lts_tmin;   // [n] earliest t_cur of the cluster
+  unsigned long long *lts_step;   // [n] smallest member step
+  unsigned long long *lts_tnew;   // [n] new time stamp
+  unsigned long long *lts_tglob;  // [1] minimum of the new time stamps
+  uint8_t *lts_touch;             // [n] particle in contact at the end of its step
 };
 
 constexpr int TILE_TRIS = 320;                 // triangles per shared-memory tile of the pair kernel
@@ -105,7 +113,19 @@ cudaError_t launch_ctime(int prec, const dem_particles &P, const int32_t *pairs,
 cudaError_t launch_clusters(int64_t n, const int32_t *edges, int64_t max_edges,
                             const int64_t *n_edges, const uint8_t *is_static, int32_t *id,
                             int64_t *n_clusters, Scratch &S, cudaStream_t s);
+cudaError_t launch_lts(int prec, int K, double tol, const dem_particles &P, double *cur, double *old,
+                       const dem_lts_params &prm, const dem_lts_out &out, Scratch &S, int num_sms,
+                       cudaStream_t s);
 
 __device__ __forceinline__ void set_err(uint32_t *err, uint32_t bit) { atomicOr(err, bit); }
+
+// order-preserving unsigned key of a double (atomic min / max of doubles)
+__device__ __forceinline__ unsigned long long okey(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double okey_value(unsigned long long k) {
+  return __longlong_as_double(static_cast<long long>((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
 
 }  // namespace dem

@@ -82,6 +82,7 @@ static_assert(Cfg<0>::TT == TILE_TRIS && Cfg<1>::TT == TILE_TRIS, "tile spheres 
 struct PairArgs {
   int64_t n;
   const double *st;
+  const uint8_t *is_static;
   const int64_t *tri_off;
   const float4 *tris;
   int64_t n_tris;
@@ -1492,8 +1493,18 @@ struct Cta {
       s.eps = OpsD::add(st[15 * n + s.i], st[15 * n + s.j]);
       const double ti = st[13 * n + s.i], tj = st[13 * n + s.j];
       const double di = st[14 * n + s.i], dj = st[14 * n + s.j];
-      s.ts = ti < tj ? ti : tj;
-      s.T_ = di < dj ? di : dj;
+      // a static member has no step of its own: the moving member's interval
+      const bool si = A.is_static && A.is_static[s.i], sj = A.is_static && A.is_static[s.j];
+      if (sj && !si) {
+        s.ts = ti;
+        s.T_ = di;
+      } else if (si && !sj) {
+        s.ts = tj;
+        s.T_ = dj;
+      } else {
+        s.ts = ti < tj ? ti : tj;
+        s.T_ = di < dj ? di : dj;
+      }
       s.resA = s.resB = -1;
       s.frmA = s.frmB = -1;
     }
@@ -1868,6 +1879,7 @@ PairArgs make_args(const dem_particles &P, const int32_t *pairs, int64_t max_pai
   PairArgs a{};
   a.n = P.n;
   a.st = P.state;
+  a.is_static = P.is_static;
   a.tri_off = P.tri_off;
   a.tris = reinterpret_cast<const float4 *>(P.tris);
   a.n_tris = P.n_tris;

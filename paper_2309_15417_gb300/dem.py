@@ -30,7 +30,7 @@ STATUS = {0: "DEM_OK", -1: "DEM_ERR_ARG", -2: "DEM_ERR_CAPACITY", -3: "DEM_ERR_C
 
 # every symbol include/dem.h declares
 EXPORTS = ["dem_create", "dem_destroy", "dem_last_error", "dem_build_candidates", "dem_narrow_phase",
-           "dem_collision_times", "dem_detect", "dem_clusters", "dem_check", "dem_get_stats",
+           "dem_collision_times", "dem_detect", "dem_clusters", "dem_lts_sweep", "dem_check", "dem_get_stats",
            "dem_build_candidates_noalloc"]
 DEM_NOALLOC_MAX_PARTICLES = 16384
 
@@ -58,11 +58,23 @@ class dem_narrow_out(C.Structure):
                 ("contact_geom", C.c_void_p), ("contact_cap", C.c_int64), ("n_contacts", C.c_void_p)]
 
 
+class dem_lts_params(C.Structure):
+    _fields_ = [("dt_max", C.c_double), ("alpha", C.c_double), ("gravity", C.c_double * 3),
+                ("zero_on_contact", C.c_int32), ("reserved", C.c_int32)]
+
+
+class dem_lts_out(C.Structure):
+    _fields_ = [("pairs", C.c_void_p), ("max_pairs", C.c_int64), ("n_pairs", C.c_void_p), ("t_coll", C.c_void_p),
+                ("status", C.c_void_p), ("tri_ab", C.c_void_p), ("cluster_id", C.c_void_p),
+                ("n_clusters", C.c_void_p), ("active", C.c_void_p), ("t_global", C.c_void_p)]
+
+
 class dem_stats(C.Structure):
     _fields_ = [("sphere_tests", C.c_int64), ("group_tests", C.c_int64), ("dist_fp32", C.c_int64),
                 ("dist_fp64", C.c_int64), ("pair_evals", C.c_int64), ("method_checks", C.c_int64),
                 ("bisect_steps", C.c_int64), ("contacts", C.c_int64), ("pairs_done", C.c_int64),
-                ("kernel_launches", C.c_int64), ("tile_pairs", C.c_int64), ("reserved", C.c_int64 * 5)]
+                ("kernel_launches", C.c_int64), ("tile_pairs", C.c_int64), ("rollbacks", C.c_int64),
+                ("rollbacks_before_old", C.c_int64), ("reserved", C.c_int64 * 3)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
@@ -183,6 +195,11 @@ def dem_detect(ctx, P: dem_particles, pairs, max_pairs: int, n_pairs, out: dem_n
 def dem_clusters(ctx, n: int, edges, max_edges: int, n_edges, is_static, cluster_id, n_clusters, stream=None):
     _check(ctx, load().dem_clusters(ctx, int(n), _ptr(edges), int(max_edges), _ptr(n_edges), _ptr(is_static),
                                     _ptr(cluster_id), _ptr(n_clusters), _stream(stream)))
+
+
+def dem_lts_sweep(ctx, P: dem_particles, cur, old, prm: dem_lts_params, out: dem_lts_out, stream=None):
+    _check(ctx, load().dem_lts_sweep(ctx, C.byref(P), _ptr(cur), _ptr(old), C.byref(prm), C.byref(out),
+                                     _stream(stream)))
 
 
 def dem_build_candidates_noalloc(P: dem_particles, pairs, cap: int, n_pairs, stream=None) -> int:
@@ -320,6 +337,28 @@ class Context:
         self.build_candidates(scene, stream)
         self.detect(scene, stream=stream)
         self.clusters(scene, stream=stream)
+
+    def lts_sweep(self, scene: Scene, old, dt_max, alpha=2.0, gravity=(0.0, 0.0, 0.0), zero_on_contact=True,
+                  stream=None):
+        """One local-time-stepping sweep: scene.state is the current snapshot
+        and ``old`` (same shape) the old one; both are updated in place.
+        Outputs in this context's buffers (pairs, n_pairs, t_coll, status,
+        ct_ab, cluster_id, n_clusters, active, t_global)."""
+        import torch
+        if self.cluster_id is None or self.cluster_id.numel() < scene.n:
+            self.cluster_id = torch.zeros(max(scene.n, 1), dtype=torch.int32, device=self.device)
+        if getattr(self, "active", None) is None or self.active.numel() < scene.n:
+            self.active = torch.zeros(max(scene.n, 1), dtype=torch.uint8, device=self.device)
+            self.t_global = torch.zeros(1, dtype=torch.float64, device=self.device)
+        if old.dtype != torch.float64 or not old.is_contiguous() or old.shape != scene.state.shape:
+            raise ValueError("old must be a contiguous float64 tensor shaped like the state")
+        prm = dem_lts_params(dt_max=float(dt_max), alpha=float(alpha), gravity=(C.c_double * 3)(*gravity),
+                             zero_on_contact=int(bool(zero_on_contact)), reserved=0)
+        out = dem_lts_out(pairs=self.pairs.data_ptr(), max_pairs=self.max_pairs, n_pairs=self.n_pairs.data_ptr(),
+                          t_coll=self.t_coll.data_ptr(), status=self.status.data_ptr(), tri_ab=self.ct_ab.data_ptr(),
+                          cluster_id=self.cluster_id.data_ptr(), n_clusters=self.n_clusters.data_ptr(),
+                          active=self.active.data_ptr(), t_global=self.t_global.data_ptr())
+        dem_lts_sweep(self.h, scene.P, scene.state, old, prm, out, stream)
 
     def check(self, stream=None):
         dem_check(self.h, stream)
