@@ -71,6 +71,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     p.add_argument("--cpu-sample", type=int, default=96, help="candidate pairs per oracle sample")
+    p.add_argument("--no-lts", action="store_true", help="skip the local-time-stepping measurements")
+    p.add_argument("--column-sweeps", type=int, default=50, help="sweeps of the settling column per replay")
     return p.parse_args()
 
 
@@ -314,6 +316,104 @@ def gpu_arm(args, rank, world, local):
                launches=r32["stats"]["kernel_launches"], fp32_err=fp32_err, fp64=fp64, e2e=e2e,
                checks_step=checks_step, stats_step={k: v / K for k, v in r32["stats"].items()})
     ctx32.close()
+    del sc, flush
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_lts:
+        res["lts"] = lts_legs(args, dem, W, dev)
+    return res
+
+
+def lts_measure(dem, w, old_np, prec, sweeps, reps, dt_max, gravity, dev, max_pairs):
+    """Sweeps of the local-time-stepping cycle captured in one CUDA graph and
+    replayed `reps` times from the same starting snapshots (restored between
+    replays, outside the timed events).  Returns times, counters and the final
+    snapshots."""
+    import torch
+    sc = dem.Scene.from_workload(w, device=dev)
+    old = torch.from_numpy(old_np).to(dev)
+    cur0, old0 = sc.state.clone(), old.clone()
+    ctx = dem.Context(K=w.K, tol=w.tol, precision=prec, max_particles=w.n, max_pairs=max_pairs,
+                      max_contacts=1 << 16, max_triangles=w.n_tris, device=dev)
+    ctx.lts_sweep(sc, old, dt_max, gravity=gravity)  # first call outside the capture
+    torch.cuda.synchronize()
+    ctx.check()
+    l0 = ctx.stats()["kernel_launches"]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(sweeps):
+            ctx.lts_sweep(sc, old, dt_max, gravity=gravity)
+    launches = ctx.stats()["kernel_launches"] - l0
+    ms, st = [], {}
+    for r in range(reps + 1):  # the first replay warms up
+        sc.state.copy_(cur0)
+        old.copy_(old0)
+        torch.cuda.synchronize()
+        ctx.stats(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        if r:
+            ms.append(e0.elapsed_time(e1))
+            for k, v in ctx.stats(reset=True).items():  # counters of every timed replay
+                st[k] = st.get(k, 0) + v
+    ctx.check()
+    st = {k: v / reps for k, v in st.items()}  # per replay
+    out = dict(ms=float(np.mean(ms)), stats=st, launches=launches, pairs=int(ctx.n_pairs.item()),
+               clusters=int(ctx.n_clusters.item()), cur=sc.state.cpu().numpy(), old=old.cpu().numpy(),
+               t_min=float(sc.state[13][torch.from_numpy(w.is_static == 0).to(dev)].min().item()))
+    ctx.close()
+    del sc, old, cur0, old0, g
+    torch.cuda.empty_cache()
+    return out
+
+
+def lts_legs(args, dem, W, dev):
+    """The local-time-stepping measurements: one cycle on the 100,000-particle
+    mixed-step layout, and 50 sweeps of the 1,000,000-particle settling column
+    in FP32 + fixup and in all-FP64 (final snapshots compared bit for bit)."""
+    res = {}
+    # one cycle, 100k particles; the log-uniform steps are the particles'
+    # histories: t_old = t_cur - dt_p / alpha, so the damped step is dt_p
+    w = W.lts_mixed_steps(args.seed)
+    old = w.state.copy()
+    old[W.F_TCUR] = w.state[W.F_TCUR] - w.state[W.F_DT] / 2.0
+    r = lts_measure(dem, w, old, dem.DEM_PREC_FP32_FIXUP, 1, 5, 1e-2, (0.0, 0.0, 0.0), dev, 1 << 20)
+    st = r["stats"]
+    res["lts_cycle_100k"] = {
+        "workload": "lts-100k: 100,000 icospheres (320 triangles), 20% FCC blobs at volume fraction 0.55, 80% "
+                    "free at 0.02; particle steps log-uniform in [1e-5, 1e-2] as step histories "
+                    "(t_old = t_cur - dt/2, alpha = 2, dt_max = 1e-2)",
+        "ms_per_cycle": r["ms"], "cuda_graph": "one sweep (step sizes, candidates, clusters, consolidation, "
+                                               "collision times, masking, advance) captured as one graph",
+        "particle_steps_per_s": st["advances"] / (r["ms"] / 1e3),
+        "checks_per_s": st["method_checks"] / (r["ms"] / 1e3),
+        "advances_per_cycle": st["advances"], "candidate_pairs": r["pairs"], "clusters": r["clusters"],
+        "kernels_per_cycle": r["launches"]}
+    del w, old, r
+    # the settling column: sweeps in a graph, both precisions
+    S = args.column_sweeps
+    w = W.settling_column(args.seed)
+    col = {}
+    for prec, name in ((dem.DEM_PREC_FP32_FIXUP, "fp32_fixup"), (dem.DEM_PREC_FP64, "fp64")):
+        r = lts_measure(dem, w, w.state.copy(), prec, S, 1, 1e-3, (0.0, 0.0, -9.81), dev, 1 << 21)
+        st = r["stats"]
+        col[name] = dict(ms_per_sweep=r["ms"] / S, particle_steps_per_s=st["advances"] / (r["ms"] / 1e3),
+                         checks_per_s=st["method_checks"] / (r["ms"] / 1e3), advances=st["advances"],
+                         last_sweep_pairs=r["pairs"], earliest_t_after=r["t_min"], kernels=r["launches"],
+                         final=(r["cur"], r["old"]))
+    same = bool(np.array_equal(col["fp32_fixup"]["final"][0], col["fp64"]["final"][0]) and
+                np.array_equal(col["fp32_fixup"]["final"][1], col["fp64"]["final"][1]))
+    for v in col.values():
+        del v["final"]
+    res["settling_column_1m"] = {
+        "workload": "settling column: 100^3 icospheres (half 80, half 320 triangles), lattice spacing 2.2, "
+                    "jitter +-0.1, over a static 316x316-quad floor (199,712 triangles); eps = 0.01, "
+                    "dt_max = 1e-3, gravity (0,0,-9.81), particles in contact stop (stand-in update)",
+        "sweeps": S, "cuda_graph": f"{S} sweeps captured in one graph", **col,
+        "speedup_fp32_fixup_over_fp64": col["fp64"]["ms_per_sweep"] / col["fp32_fixup"]["ms_per_sweep"],
+        "final_snapshots_identical": same}
     return res
 
 
@@ -456,7 +556,7 @@ def main():
                               "one CUDA graph",
                 "roofline": roof, "cpu_baseline": cpu, "e2e": r["e2e"], "clocks": r["clocks"],
                 "gpu_launches": int(r["launches"]), "fp64_form": r["fp64"], "fp32_error": r["fp32_err"],
-                "counters_per_step": r["stats_step"]}
+                "counters_per_step": r["stats_step"], "local_time_stepping": r.get("lts")}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

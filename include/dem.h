@@ -144,7 +144,8 @@ typedef struct {
   int64_t tile_pairs;       /* 320 x 320-triangle tile pairs scanned (not culled by tile spheres) */
   int64_t rollbacks;        /* local time stepping: particles rolled back by consolidation */
   int64_t rollbacks_before_old; /* ... of which to before their old snapshot (0 if the theorem holds) */
-  int64_t reserved[3];
+  int64_t advances;         /* local time stepping: particle advances (particle-steps) */
+  int64_t reserved[2];
 } dem_stats;
 
 /* Create a context: validates and copies *cfg, allocates scratch for the

@@ -28,6 +28,7 @@ enum {
   ST_TILES,
   ST_ROLLBACK,
   ST_ROLLBACK_BAD,
+  ST_ADVANCE,
   ST_N = 16
 };
 

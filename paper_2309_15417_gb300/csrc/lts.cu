@@ -123,12 +123,13 @@ __global__ void k_lts_touch(int64_t n, const int32_t *pairs, const int64_t *n_pa
 __global__ void k_lts_advance(int64_t n, double *cur, double *old, const uint8_t *st, const int32_t *ids,
                               const unsigned long long *tmin, const unsigned long long *tnew,
                               const unsigned long long *tglob, const uint8_t *touch, double gx, double gy, double gz,
-                              int zero_on_contact, uint8_t *active, double *t_global) {
+                              int zero_on_contact, uint8_t *active, double *t_global, unsigned long long *stats) {
   __shared__ double rc[POSE_TERMS + 1], rs[POSE_TERMS + 1];
   if (threadIdx.x == 0) pose_reciprocals(rc, rs);
   __syncthreads();
   const double tg = okey_value(*tglob);
   if (blockIdx.x == 0 && threadIdx.x == 0) *t_global = *tglob == ~0ull ? OpsD::inf() : tg;
+  unsigned long long adv = 0;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
     active[p] = 0;
     if (is_st(st, p)) continue;
@@ -136,6 +137,7 @@ __global__ void k_lts_advance(int64_t n, double *cur, double *old, const uint8_t
     if (c < 0 || c >= n) continue;
     if (!(okey_value(tmin[c]) <= tg)) continue;
     active[p] = 1;
+    ++adv;
     const double tn = okey_value(tnew[c]);
     const double h = D::sub(tn, cur[13 * n + p]);
 #pragma unroll
@@ -154,6 +156,9 @@ __global__ void k_lts_advance(int64_t n, double *cur, double *old, const uint8_t
       cur[5 * n + p] = D::add(cur[5 * n + p], D::mul(gz, h));
     }
   }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) adv += __shfl_xor_sync(0xffffffffu, adv, o);
+  if ((threadIdx.x & 31) == 0 && adv) atomicAdd(&stats[ST_ADVANCE], adv);
 }
 
 }  // namespace
@@ -198,7 +203,7 @@ cudaError_t launch_lts(int prec, int K, double tol, const dem_particles &P, doub
   }
   k_lts_advance<<<grid, tb, 0, s>>>(n, cur, old, P.is_static, out.cluster_id, S.lts_tmin, S.lts_tnew, S.lts_tglob,
                                     S.lts_touch, prm.gravity[0], prm.gravity[1], prm.gravity[2],
-                                    prm.zero_on_contact, out.active, out.t_global);
+                                    prm.zero_on_contact, out.active, out.t_global, S.stats);
   S.launches += 1;
   return cudaGetLastError();
 }

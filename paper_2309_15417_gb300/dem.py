@@ -74,7 +74,7 @@ class dem_stats(C.Structure):
                 ("dist_fp64", C.c_int64), ("pair_evals", C.c_int64), ("method_checks", C.c_int64),
                 ("bisect_steps", C.c_int64), ("contacts", C.c_int64), ("pairs_done", C.c_int64),
                 ("kernel_launches", C.c_int64), ("tile_pairs", C.c_int64), ("rollbacks", C.c_int64),
-                ("rollbacks_before_old", C.c_int64), ("reserved", C.c_int64 * 3)]
+                ("rollbacks_before_old", C.c_int64), ("advances", C.c_int64), ("reserved", C.c_int64 * 2)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}

@@ -49,6 +49,7 @@ def _compare_sweeps(dem, w, old, prec, sweeps, dt_max, gravity, max_pairs=1 << 1
         assert np.array_equal(g_old.cpu().numpy(), o_old), s
         st = c.stats(reset=True)
         assert st["rollbacks"] == r["rollbacks"] and st["rollbacks_before_old"] == r["rollbacks_before_old"]
+        assert st["advances"] == int(r["active"].sum())
         seen |= set(r["status"].tolist())
     c.close()
     return seen
