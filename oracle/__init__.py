@@ -67,6 +67,9 @@ def lib():
             L.demo_collision_times.argtypes = [dp, u8p, C.c_int64, i64p, fp, C.c_int64, i32p, C.c_int64,
                                                C.c_int, C.c_double, dp, u8p, i32p, i32p, C.c_int]
             L.demo_collision_times.restype = None
+            L.demo_collision_times_narrowing.argtypes = [dp, u8p, C.c_int64, i64p, fp, C.c_int64, i32p,
+                                                         C.c_int64, C.c_double, dp, u8p, i32p, i32p, C.c_int]
+            L.demo_collision_times_narrowing.restype = None
             L.demo_clusters.argtypes = [C.c_int64, i32p, C.c_int64, u8p, i32p]
             L.demo_clusters.restype = C.c_int64
             L.demo_lts_sweep.argtypes = [dp, dp, u8p, C.c_int64, i64p, fp, C.c_int64, C.c_int, C.c_double,
@@ -198,6 +201,23 @@ def collision_times(w, pairs, K=None, tol=None, n_threads=None):
         _p(pairs, C.c_int32), m, int(K), float(tol), _p(t, C.c_double), _p(status, C.c_uint8),
         _p(tri_ab, C.c_int32), _p(ne, C.c_int32), n_threads or default_threads())
     return dict(t_coll=t, status=status, tri_ab=tri_ab, n_evals=ne)
+
+
+def collision_times_narrowing(w, pairs, tol=None, n_threads=None):
+    """The paper's narrowing procedure; returns dict(t_coll, status, tri_ab, n_iter)."""
+    state, sta, off, tris = _geometry(w)
+    pairs = _c(pairs, np.int32).reshape(-1, 2)
+    m = len(pairs)
+    tol = w.tol if tol is None else tol
+    t = np.zeros(m)
+    status = np.zeros(m, np.uint8)
+    tri_ab = np.zeros((m, 2), np.int32)
+    it = np.zeros(m, np.int32)
+    lib().demo_collision_times_narrowing(
+        _p(state, C.c_double), _p(sta, C.c_uint8), state.shape[1], _p(off, C.c_int64), _p(tris, C.c_float),
+        tris.shape[1], _p(pairs, C.c_int32), m, float(tol), _p(t, C.c_double), _p(status, C.c_uint8),
+        _p(tri_ab, C.c_int32), _p(it, C.c_int32), n_threads or default_threads())
+    return dict(t_coll=t, status=status, tri_ab=tri_ab, n_iter=it)
 
 
 def clusters(n, edges, is_static=None):

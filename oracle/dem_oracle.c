@@ -535,7 +535,7 @@ typedef struct {
   int32_t *tri_ab;
   int32_t *n_evals;
   atomic_llong next;
-  int mode;              /* 0 narrow, 1 collision times */
+  int mode;              /* 0 narrow, 1 collision times (samples), 2 collision times (narrowing) */
 } job;
 
 /* Collision time of one pair (paper Section 5, case distinction and the
@@ -608,6 +608,162 @@ static void collision_time_one(job *J, int64_t k) {
   if (J->n_evals) J->n_evals[k] = evals;
 }
 
+/* ------------------------------------------------------------------------ */
+/* The paper's narrowing (Section 5, "Collision time detection", definitions
+ * of narrowing and widening), as a second collision-time procedure.  It
+ * approximates the contact time per triangle pair over the current search
+ * span [ts, te] and narrows te to the earliest contact found:
+ *   vertex-triangle (each vertex of one triangle against the other triangle):
+ *     the vertex is taken into the body frame of the triangle's particle at
+ *     ts and at te (P0, P1: R^T (W - X) with the actual poses) and moves on
+ *     the straight segment P0 -> P1 in between (rotation neglected); its
+ *     distance to the triangle is checked at the end P1 (time te) and where
+ *     the segment crosses the triangle's plane, if it does (time
+ *     ts + s (te - ts), s = h0 / (h0 - h1) from the signed plane heights
+ *     h = n . (P - a), n = (b - a) x (c - a));
+ *   edge-edge (each edge pair): the distance with the actual poses at the
+ *     middle ts + 0.5 (te - ts) and at te;
+ *   a candidate is a time whose distance is <= eps_pair; the span's start
+ *   needs no check (the pair is apart there, or status 1 was returned).
+ * Iteration: tc = the earliest candidate over all triangle pairs; none ->
+ * stop; otherwise a contact is found, and if tc < te - w (w = tol T, the
+ * widening) the span narrows to te = tc + w and the tests rerun, else stop
+ * (at most 64 iterations).  Status 1 as in the sampling procedure (distance at
+ * ts <= eps_pair, t = ts + T); a found contact gives status 2 with t = te and
+ * the closest (smallest (a, b)) triangle pair of the earliest candidate of the
+ * last iteration; none gives status 0, t = ts + T. */
+#define NARROW_MAX_ITER 64
+
+/* body-frame position of world point W in the frame (R, X): R^T (W - X) */
+static vec3 rel_pos(const double R[9], const double X[3], vec3 W) {
+  vec3 d = sub(W, ld(X));
+  return mk(R[0] * d.x + R[3] * d.y + R[6] * d.z, R[1] * d.x + R[4] * d.y + R[7] * d.z,
+            R[2] * d.x + R[5] * d.y + R[8] * d.z);
+}
+
+/* earliest vertex-triangle candidate of world vertex (W0 at ts, W1 at te)
+ * against body triangle A of the particle with frames (R0, X0) at ts and
+ * (R1, X1) at te; INFINITY if none */
+static double vt_candidate(vec3 W0, vec3 W1, const double R0[9], const double X0[3], const double R1[9],
+                           const double X1[3], const vec3 A[3], double eps, double ts, double te) {
+  vec3 P0 = rel_pos(R0, X0, W0), P1 = rel_pos(R1, X1, W1), q;
+  double best = INFINITY;
+  if (sqrt(closest_pt_tri(P1, A[0], A[1], A[2], &q)) <= eps) best = te;
+  vec3 nrm = cross(sub(A[1], A[0]), sub(A[2], A[0]));
+  double h0 = dot(nrm, sub(P0, A[0])), h1 = dot(nrm, sub(P1, A[0]));
+  if ((h0 > 0.0 && h1 < 0.0) || (h0 < 0.0 && h1 > 0.0)) {
+    double s = h0 / (h0 - h1);
+    vec3 Ps = axpy(P0, sub(P1, P0), s);
+    double t = ts + s * (te - ts);
+    if (sqrt(closest_pt_tri(Ps, A[0], A[1], A[2], &q)) <= eps && t < best) best = t;
+  }
+  return best;
+}
+
+static void narrowing_one(job *J, int64_t k) {
+  int64_t i = J->pairs[2 * k], j = J->pairs[2 * k + 1];
+  const double *s = J->state;
+  int64_t n = J->n;
+  double eps = eps_pair(s, n, i, j);
+  double ts = pair_start(s, J->is_static, n, i, j), T = pair_span(s, J->is_static, n, i, j);
+  pair_eval e;
+  memset(&e, 0, sizeof e);
+  eval_pair(s, n, J->tri_off, J->tris, J->n_tris, i, j, ts, 0, &e);
+  int iters = 0;
+  if (sqrt(e.d2min) <= eps) {
+    J->t_coll[k] = ts + T;
+    J->status[k] = 1;
+    J->tri_ab[2 * k] = e.a;
+    J->tri_ab[2 * k + 1] = e.b;
+    if (J->n_evals) J->n_evals[k] = 0;
+    return;
+  }
+  int64_t na = J->tri_off[i + 1] - J->tri_off[i], nb = J->tri_off[j + 1] - J->tri_off[j];
+  /* body-frame triangles (float32 values promoted exactly) */
+  vec3 *BA = (vec3 *)malloc(sizeof(vec3) * 3 * (size_t)(na > 0 ? na : 1));
+  vec3 *BB = (vec3 *)malloc(sizeof(vec3) * 3 * (size_t)(nb > 0 ? nb : 1));
+  for (int64_t a = 0; a < na; ++a)
+    for (int q = 0; q < 3; ++q) {
+      const float *v = J->tris + ((size_t)q * (size_t)J->n_tris + (size_t)(J->tri_off[i] + a)) * 4;
+      BA[3 * a + q] = mk((double)v[0], (double)v[1], (double)v[2]);
+    }
+  for (int64_t b = 0; b < nb; ++b)
+    for (int q = 0; q < 3; ++q) {
+      const float *v = J->tris + ((size_t)q * (size_t)J->n_tris + (size_t)(J->tri_off[j] + b)) * 4;
+      BB[3 * b + q] = mk((double)v[0], (double)v[1], (double)v[2]);
+    }
+  double RA0[9], XA0[3], RB0[9], XB0[3];
+  demo_pose(s, n, i, ts, RA0, XA0);
+  demo_pose(s, n, j, ts, RB0, XB0);
+  vec3 *WA0 = world_verts(s, n, J->tri_off, J->tris, J->n_tris, i, ts);
+  vec3 *WB0 = world_verts(s, n, J->tri_off, J->tris, J->n_tris, j, ts);
+  double w = J->tol * T, te = ts + T;
+  int found = 0;
+  int32_t ta = -1, tb = -1;
+  for (;;) {
+    double tm = ts + 0.5 * (te - ts);
+    double RA1[9], XA1[3], RB1[9], XB1[3];
+    demo_pose(s, n, i, te, RA1, XA1);
+    demo_pose(s, n, j, te, RB1, XB1);
+    vec3 *WA1 = world_verts(s, n, J->tri_off, J->tris, J->n_tris, i, te);
+    vec3 *WB1 = world_verts(s, n, J->tri_off, J->tris, J->n_tris, j, te);
+    vec3 *WAm = world_verts(s, n, J->tri_off, J->tris, J->n_tris, i, tm);
+    vec3 *WBm = world_verts(s, n, J->tri_off, J->tris, J->n_tris, j, tm);
+    double best = INFINITY;
+    int32_t ba = -1, bb = -1;
+    for (int64_t a = 0; a < na; ++a)
+      for (int64_t b = 0; b < nb; ++b) {
+        double tab = INFINITY, t;
+        /* vertices of a against triangle b (frame of j), then of b against a */
+        for (int q = 0; q < 3; ++q) {
+          t = vt_candidate(WA0[3 * a + q], WA1[3 * a + q], RB0, XB0, RB1, XB1, BB + 3 * b, eps, ts, te);
+          if (t < tab) tab = t;
+        }
+        for (int q = 0; q < 3; ++q) {
+          t = vt_candidate(WB0[3 * b + q], WB1[3 * b + q], RA0, XA0, RA1, XA1, BA + 3 * a, eps, ts, te);
+          if (t < tab) tab = t;
+        }
+        /* edge pairs at the middle and the end of the span */
+        for (int p = 0; p < 3; ++p)
+          for (int q = 0; q < 3; ++q) {
+            vec3 c1, c2;
+            int p1 = p == 2 ? 0 : p + 1, q1 = q == 2 ? 0 : q + 1;
+            if (tm < tab && sqrt(seg_seg(WAm[3 * a + p], WAm[3 * a + p1], WBm[3 * b + q], WBm[3 * b + q1], &c1,
+                                         &c2)) <= eps)
+              tab = tm;
+            if (te < tab && sqrt(seg_seg(WA1[3 * a + p], WA1[3 * a + p1], WB1[3 * b + q], WB1[3 * b + q1], &c1,
+                                         &c2)) <= eps)
+              tab = te;
+          }
+        if (tab < best) {
+          best = tab;
+          ba = (int32_t)a;
+          bb = (int32_t)b;
+        }
+      }
+    free(WA1);
+    free(WB1);
+    free(WAm);
+    free(WBm);
+    ++iters;
+    if (best == INFINITY) break;
+    found = 1;
+    ta = ba;
+    tb = bb;
+    if (!(best < te - w) || iters >= NARROW_MAX_ITER) break;
+    te = best + w;
+  }
+  free(WA0);
+  free(WB0);
+  free(BA);
+  free(BB);
+  J->t_coll[k] = found ? te : ts + T;
+  J->status[k] = found ? 2 : 0;
+  J->tri_ab[2 * k] = found ? ta : -1;
+  J->tri_ab[2 * k + 1] = found ? tb : -1;
+  if (J->n_evals) J->n_evals[k] = iters;
+}
+
 static void *worker(void *arg) {
   job *J = (job *)arg;
   for (;;) {
@@ -617,8 +773,10 @@ static void *worker(void *arg) {
       int64_t i = J->pairs[2 * k], j = J->pairs[2 * k + 1];
       double t = J->t_eval ? J->t_eval[k] : pair_start(J->state, J->is_static, J->n, i, j);
       eval_pair(J->state, J->n, J->tri_off, J->tris, J->n_tris, i, j, t, 1, &J->ev[k]);
-    } else {
+    } else if (J->mode == 1) {
       collision_time_one(J, k);
+    } else {
+      narrowing_one(J, k);
     }
   }
   return NULL;
@@ -704,6 +862,30 @@ void demo_collision_times(const double *state, const uint8_t *is_static, int64_t
   J.tri_ab = tri_ab;
   J.n_evals = n_evals;
   J.mode = 1;
+  run_job(&J, n_threads);
+}
+
+void demo_collision_times_narrowing(const double *state, const uint8_t *is_static, int64_t n,
+                                    const int64_t *tri_off,
+                                    const float *tris, int64_t n_tris, const int32_t *pairs, int64_t m,
+                                    double tol, double *t_coll, uint8_t *status, int32_t *tri_ab,
+                                    int32_t *n_iter, int n_threads) {
+  job J;
+  memset(&J, 0, sizeof J);
+  J.state = state;
+  J.is_static = is_static;
+  J.n = n;
+  J.tri_off = tri_off;
+  J.tris = tris;
+  J.n_tris = n_tris;
+  J.pairs = pairs;
+  J.m = m;
+  J.tol = tol;
+  J.t_coll = t_coll;
+  J.status = status;
+  J.tri_ab = tri_ab;
+  J.n_evals = n_iter;
+  J.mode = 2;
   run_job(&J, n_threads);
 }
 
