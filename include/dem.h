@@ -53,6 +53,17 @@ typedef enum {
   DEM_ERR_TIMEOUT = -5    /* a bounded device wait ran out */
 } dem_status;
 
+/* Collision-time procedure of dem_collision_times, dem_detect and
+ * dem_lts_sweep. */
+enum {
+  DEM_CTIME_SAMPLES = 0,  /* K uniform samples, then bisection to bisect_tol * T */
+  DEM_CTIME_NARROWING = 1 /* the paper's narrowing (Section 5): vertex-triangle on the straight
+                             relative path (end point, plane crossing), edge-edge at the middle and
+                             end of the span; the span narrows to the earliest contact plus the
+                             widening bisect_tol * T while that shortens it (at most 64 times);
+                             binary64 throughout on the GPU */
+};
+
 /* Arithmetic of the triangle-pair distances. */
 enum {
   DEM_PREC_FP32_FIXUP = 0, /* FP32 bulk, FP64 recomputation within the FP32 error bound */
@@ -94,7 +105,7 @@ typedef struct {
   int32_t K;            /* collision-time samples per pair interval (>= 1; 0 -> 8) */
   double bisect_tol;    /* bisection stops at bracket <= bisect_tol * T (0 -> 1e-3) */
   int32_t precision;    /* DEM_PREC_* */
-  int32_t reserved;
+  int32_t ctime_method; /* DEM_CTIME_* */
   int64_t max_particles; /* capacity: particles per call (0 -> 65536) */
   int64_t max_pairs;     /* capacity: pairs / edges per call (0 -> 1<<20) */
   int64_t max_contacts;  /* capacity: contact staging per narrow-phase call (0 -> 1<<20) */

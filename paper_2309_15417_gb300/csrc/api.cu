@@ -79,6 +79,7 @@ dem_status dem_create(const dem_config *cfg, dem_ctx **out) {
   if (k.max_contacts == 0) k.max_contacts = 1 << 20;
   if (k.max_triangles == 0) k.max_triangles = 1280 * k.max_particles;
   if (k.K < 1 || !(k.bisect_tol > 0.0) || (k.precision != DEM_PREC_FP32_FIXUP && k.precision != DEM_PREC_FP64) ||
+      (k.ctime_method != DEM_CTIME_SAMPLES && k.ctime_method != DEM_CTIME_NARROWING) ||
       k.max_particles < 0 || k.max_pairs < 0 || k.max_contacts < 0 || k.max_triangles < 0 ||
       k.max_triangles > ((int64_t)1 << 40) ||
       k.max_particles > (int64_t)(dem::SCAN_BLOCK * dem::SCAN_PART_CAP / 2) ||
@@ -168,7 +169,8 @@ dem_status dem_collision_times(dem_ctx *c, const dem_particles *P, const int32_t
   if (st != DEM_OK) return st;
   if (max_pairs < 0 || (max_pairs > 0 && (!pairs || !t_coll || !status || !tri_ab)))
     return fail(c, DEM_ERR_ARG, "collision_times: bad arguments");
-  cudaError_t e = dem::launch_ctime(c->cfg.precision, *P, pairs, max_pairs, n_pairs, c->cfg.K, c->cfg.bisect_tol,
+  cudaError_t e = dem::launch_ctime(c->cfg.precision, c->cfg.ctime_method, *P, pairs, max_pairs, n_pairs, c->cfg.K,
+                                    c->cfg.bisect_tol,
                                     t_coll, status, tri_ab, c->S, c->num_sms, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(c, e, "collision_times");
   return DEM_OK;
@@ -187,9 +189,19 @@ dem_status dem_detect(dem_ctx *c, const dem_particles *P, const int32_t *pairs, 
       (max_pairs > 0 && (!out->dmin || !out->pa || !out->pb || !out->tri_ab || !out->flag)) ||
       (out->contact_cap > 0 && (!out->contacts || !out->contact_geom)))
     return fail(c, DEM_ERR_ARG, "detect: bad narrow-phase outputs");
-  cudaError_t e = dem::launch_detect(c->cfg.precision, *P, pairs, max_pairs, n_pairs, *out, c->cfg.K,
-                                     c->cfg.bisect_tol, t_coll, status, tri_ab, c->S, c->num_sms,
-                                     static_cast<cudaStream_t>(stream));
+  cudaError_t e;
+  if (c->cfg.ctime_method == DEM_CTIME_NARROWING) {
+    // the narrowing has no fused form: the two calls, same outputs
+    e = dem::launch_narrow(c->cfg.precision, *P, pairs, max_pairs, n_pairs, nullptr, *out, c->S, c->num_sms,
+                           static_cast<cudaStream_t>(stream));
+    if (e == cudaSuccess)
+      e = dem::launch_ctime(c->cfg.precision, c->cfg.ctime_method, *P, pairs, max_pairs, n_pairs, c->cfg.K,
+                            c->cfg.bisect_tol, t_coll, status, tri_ab, c->S, c->num_sms,
+                            static_cast<cudaStream_t>(stream));
+  } else {
+    e = dem::launch_detect(c->cfg.precision, *P, pairs, max_pairs, n_pairs, *out, c->cfg.K, c->cfg.bisect_tol,
+                           t_coll, status, tri_ab, c->S, c->num_sms, static_cast<cudaStream_t>(stream));
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "detect");
   return DEM_OK;
 }
@@ -222,7 +234,7 @@ dem_status dem_lts_sweep(dem_ctx *c, const dem_particles *P, double *cur, double
     return fail(c, DEM_ERR_ARG, "lts_sweep: bad outputs");
   if (out->max_pairs > c->S.cap_pairs) return fail(c, DEM_ERR_CAPACITY, "lts_sweep: max_pairs exceeds capacity");
   if (!(prm->dt_max > 0.0) || !(prm->alpha > 0.0)) return fail(c, DEM_ERR_ARG, "lts_sweep: dt_max, alpha > 0");
-  cudaError_t e = dem::launch_lts(c->cfg.precision, c->cfg.K, c->cfg.bisect_tol, G, cur, old, *prm, *out, c->S,
+  cudaError_t e = dem::launch_lts(c->cfg.precision, c->cfg.ctime_method, c->cfg.K, c->cfg.bisect_tol, G, cur, old, *prm, *out, c->S,
                                   c->num_sms, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(c, e, "lts_sweep");
   return DEM_OK;

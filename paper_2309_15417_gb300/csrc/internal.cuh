@@ -107,14 +107,14 @@ cudaError_t launch_narrow(int prec, const dem_particles &P, const int32_t *pairs
 cudaError_t launch_detect(int prec, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
                           const int64_t *n_pairs, const dem_narrow_out &out, int K, double tol, double *t_coll,
                           uint8_t *status, int32_t *tri_ab, Scratch &S, int num_sms, cudaStream_t s);
-cudaError_t launch_ctime(int prec, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
+cudaError_t launch_ctime(int prec, int method, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
                          const int64_t *n_pairs, int K, double tol, double *t_coll,
                          uint8_t *status, int32_t *tri_ab, Scratch &S, int num_sms,
                          cudaStream_t s);
 cudaError_t launch_clusters(int64_t n, const int32_t *edges, int64_t max_edges,
                             const int64_t *n_edges, const uint8_t *is_static, int32_t *id,
                             int64_t *n_clusters, Scratch &S, cudaStream_t s);
-cudaError_t launch_lts(int prec, int K, double tol, const dem_particles &P, double *cur, double *old,
+cudaError_t launch_lts(int prec, int method, int K, double tol, const dem_particles &P, double *cur, double *old,
                        const dem_lts_params &prm, const dem_lts_out &out, Scratch &S, int num_sms,
                        cudaStream_t s);
 

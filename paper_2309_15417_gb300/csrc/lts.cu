@@ -163,7 +163,7 @@ __global__ void k_lts_advance(int64_t n, double *cur, double *old, const uint8_t
 
 }  // namespace
 
-cudaError_t launch_lts(int prec, int K, double tol, const dem_particles &P, double *cur, double *old,
+cudaError_t launch_lts(int prec, int method, int K, double tol, const dem_particles &P, double *cur, double *old,
                        const dem_lts_params &prm, const dem_lts_out &out, Scratch &S, int num_sms, cudaStream_t s) {
   const int64_t n = P.n;
   cudaError_t e;
@@ -187,7 +187,7 @@ cudaError_t launch_lts(int prec, int K, double tol, const dem_particles &P, doub
                                         S.stats);
   S.launches += 2;
   if (out.max_pairs > 0) {
-    if ((e = launch_ctime(prec, P, out.pairs, out.max_pairs, out.n_pairs, K, tol, out.t_coll, out.status, out.tri_ab,
+    if ((e = launch_ctime(prec, method, P, out.pairs, out.max_pairs, out.n_pairs, K, tol, out.t_coll, out.status, out.tri_ab,
                           S, num_sms, s)) != cudaSuccess)
       return e;
     k_lts_tnew<<<pgrid, tb, 0, s>>>(n, out.pairs, out.n_pairs, out.max_pairs, out.status, out.t_coll,

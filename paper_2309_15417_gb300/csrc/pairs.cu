@@ -54,6 +54,8 @@ constexpr double ERR_REL64_LB = 9.094947017729282e-13;  // 2^-40: FP64 culling m
 constexpr int MODE_NARROW = 0;
 constexpr int MODE_CTIME = 1;
 constexpr int MODE_BOTH = 2;  // narrow phase at the pair start + collision times
+constexpr int MODE_NTIME = 3; // collision times by the paper's narrowing
+constexpr int NARROW_MAX_ITER = 64;
 
 constexpr int pow2_at_least(int v) { return v <= 1 ? 1 : 2 * pow2_at_least((v + 1) / 2); }
 
@@ -1462,6 +1464,157 @@ struct Cta {
     __syncthreads();
   }
 
+  // --- the paper's narrowing (second collision-time procedure) ------------
+  // Poses of the narrowing: gR/gX slot 0 = ts, 1 = span end te, 2 = middle.
+  using VD = V3<double>;
+  // body-frame position R^T (W - X), rows summed left to right
+  static __device__ __forceinline__ VD rel_pos(const double *R, const double *X, VD W) {
+    using O = OpsD;
+    const VD d = GD::sub(W, VD{X[0], X[1], X[2]});
+    return VD{O::add(O::add(O::mul(R[0], d.x), O::mul(R[3], d.y)), O::mul(R[6], d.z)),
+              O::add(O::add(O::mul(R[1], d.x), O::mul(R[4], d.y)), O::mul(R[7], d.z)),
+              O::add(O::add(O::mul(R[2], d.x), O::mul(R[5], d.y)), O::mul(R[8], d.z))};
+  }
+  // earliest vertex-triangle candidate: the vertex (world W0 at ts, W1 at te)
+  // on its straight path in the triangle particle's frame; the end point and
+  // the plane crossing (heights h = n . (P - a), n = (b - a) x (c - a))
+  static __device__ double vt_candidate(VD W0, VD W1, const double *R0, const double *X0, const double *R1,
+                                        const double *X1, const VD *Tr, double eps, double ts, double te) {
+    using O = OpsD;
+    const VD P0 = rel_pos(R0, X0, W0), P1 = rel_pos(R1, X1, W1);
+    VD q;
+    double best = O::inf();
+    if (O::sqrt(GD::closest_pt_tri(P1, Tr[0], Tr[1], Tr[2], q)) <= eps) best = te;
+    const VD nrm = GD::cross(GD::sub(Tr[1], Tr[0]), GD::sub(Tr[2], Tr[0]));
+    const double h0 = GD::dot(nrm, GD::sub(P0, Tr[0])), h1 = GD::dot(nrm, GD::sub(P1, Tr[0]));
+    if ((h0 > 0.0 && h1 < 0.0) || (h0 < 0.0 && h1 > 0.0)) {
+      const double sx = O::div(h0, O::sub(h0, h1));
+      const VD Ps = GD::axpy(P0, GD::sub(P1, P0), sx);
+      const double t = O::add(ts, O::mul(sx, O::sub(te, ts)));
+      if (O::sqrt(GD::closest_pt_tri(Ps, Tr[0], Tr[1], Tr[2], q)) <= eps && t < best) best = t;
+    }
+    return best;
+  }
+  // earliest candidate of triangle pair (a, b) over [ts, te] (binary64)
+  __device__ __noinline__ double narrow_pair(int a, int b, double ts, double te, double tm) const {
+    using O = OpsD;
+    VD BA[3], BB[3], WA0[3], WA1[3], WAm[3], WB0[3], WB1[3], WBm[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float4 f = A.tris[q * A.n_tris + s.offA + a], g = A.tris[q * A.n_tris + s.offB + b];
+      BA[q] = VD{f.x, f.y, f.z};
+      BB[q] = VD{g.x, g.y, g.z};
+      WA0[q] = to_world_exact(s.gR[0][0], s.gX[0][0], f.x, f.y, f.z);
+      WA1[q] = to_world_exact(s.gR[1][0], s.gX[1][0], f.x, f.y, f.z);
+      WAm[q] = to_world_exact(s.gR[2][0], s.gX[2][0], f.x, f.y, f.z);
+      WB0[q] = to_world_exact(s.gR[0][1], s.gX[0][1], g.x, g.y, g.z);
+      WB1[q] = to_world_exact(s.gR[1][1], s.gX[1][1], g.x, g.y, g.z);
+      WBm[q] = to_world_exact(s.gR[2][1], s.gX[2][1], g.x, g.y, g.z);
+    }
+    const double eps = s.eps;
+    double tab = O::inf();
+    for (int q = 0; q < 3; ++q)
+      tab = fmin(tab, vt_candidate(WA0[q], WA1[q], s.gR[0][1], s.gX[0][1], s.gR[1][1], s.gX[1][1], BB, eps, ts, te));
+    for (int q = 0; q < 3; ++q)
+      tab = fmin(tab, vt_candidate(WB0[q], WB1[q], s.gR[0][0], s.gX[0][0], s.gR[1][0], s.gX[1][0], BA, eps, ts, te));
+    for (int p = 0; p < 3; ++p)
+      for (int q = 0; q < 3; ++q) {
+        const int p1 = p == 2 ? 0 : p + 1, q1 = q == 2 ? 0 : q + 1;
+        VD c1, c2;
+        if (tm < tab && O::sqrt(GD::seg_seg(WAm[p], WAm[p1], WBm[q], WBm[q1], c1, c2)) <= eps) tab = tm;
+        if (te < tab && O::sqrt(GD::seg_seg(WA1[p], WA1[p1], WB1[q], WB1[q1], c1, c2)) <= eps) tab = te;
+      }
+    return tab;
+  }
+  // The narrowing loop after a false decision at ts.  The triangle pairs are
+  // those of the pair-interval list collected at ts with the narrowing's
+  // motion bound (all pairs if the list overflowed).  Returns the status and
+  // sets tc, ta, tb and the number of iterations.
+  __device__ uint8_t narrowing(int &iters, double &tc, int32_t &ta, int32_t &tb) {
+    using O = OpsD;
+    if (tid < 24) {  // keep the poses at ts (slot 0)
+      const int side = tid / 12, e = tid % 12;
+      if (e < 9)
+        s.gR[0][side][e] = side == 0 ? s.RA[e] : s.RB[e];
+      else
+        s.gX[0][side][e - 9] = side == 0 ? s.XA[e - 9] : s.XB[e - 9];
+    }
+    const double ts = s.ts, T = s.T_, wid = O::mul(A.tol, T);  // widening
+    double te = O::add(ts, T);
+    bool found = false;
+    iters = 0;
+    for (;;) {
+      const double tm = O::add(ts, O::mul(0.5, O::sub(te, ts)));
+      __syncthreads();
+      if (tid < 4) {
+        const int side = tid & 1, which = tid >> 1;
+        pose_exact(A.st, A.n, side ? s.j : s.i, which ? tm : te, s.rc, s.rs, s.gR[1 + which][side],
+                   s.gX[1 + which][side]);
+      }
+      __syncthreads();
+      const bool useL = s.ilover == 0;
+      const int64_t cnt = useL ? (int64_t)s.nil : (int64_t)s.nA * s.nB;
+      double best = O::inf();
+      unsigned long long bk = ~0ull;
+      for (int64_t q = tid; q < cnt; q += NT) {
+        int a, b;
+        if (useL) {
+          const unsigned long long ent = s.il[q];
+          a = int(ent >> 32);
+          b = int(ent & 0xffffffffu);
+        } else {
+          a = int(q / s.nB);
+          b = int(q - (int64_t)a * s.nB);
+        }
+        const double t = narrow_pair(a, b, ts, te, tm);
+        const unsigned long long key = (static_cast<unsigned long long>(a) << 32) | static_cast<uint32_t>(b);
+        if (t < best || (t == best && key < bk)) {
+          best = t;
+          bk = key;
+        }
+      }
+      if (tid == 0) stat(ST_FP64, (unsigned long long)cnt);
+      // block minimum of (time, key)
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        if (ob < best || (ob == best && ok < bk)) {
+          best = ob;
+          bk = ok;
+        }
+      }
+      __syncthreads();
+      if (lane == 0) {
+        s.red_d[w] = best;
+        s.red_k[w] = bk;
+      }
+      __syncthreads();
+      best = s.red_d[0];
+      bk = s.red_k[0];
+      for (int q = 1; q < NW; ++q)
+        if (s.red_d[q] < best || (s.red_d[q] == best && s.red_k[q] < bk)) {
+          best = s.red_d[q];
+          bk = s.red_k[q];
+        }
+      ++iters;
+      if (!(best < O::inf())) break;
+      found = true;
+      ta = int32_t(bk >> 32);
+      tb = int32_t(bk & 0xffffffffu);
+      if (!(best < O::sub(te, wid)) || iters >= NARROW_MAX_ITER) break;
+      te = O::add(best, wid);
+    }
+    __syncthreads();
+    if (!found) {
+      ta = tb = -1;
+      tc = O::add(ts, T);
+      return 0;
+    }
+    tc = te;
+    return 2;
+  }
+
   // --- per pair setup --------------------------------------------------------
   __device__ bool setup_pair(int64_t k) {
     if (tid == 0) {
@@ -1580,6 +1733,36 @@ __global__ void __launch_bounds__(Cfg<PREC>::NT, Cfg<PREC>::MINB) pair_kernel(Pa
       }
       __syncthreads();
     };
+    // Motion bound of the narrowing: how far a vertex can move in the other
+    // particle's frame, or any feature distance change, over the interval:
+    // (|v_i| + |v_j| + |w_i| R_i + |w_j| R_j
+    //  + (|w_i| + |w_j|) (R_i + R_j + D0 + (|v_i| + |v_j|) T)) T,
+    // D0 bounding the centre distance at ts (the frame's rotation moves a
+    // point at distance r from its centre by |w| r per time).
+    auto motion_bound_narrowing = [&]() {
+      if (c.tid == 0) {
+        const double *st = A.st;
+        const int64_t n = A.n;
+        double vs = 0.0, wr = 0.0, ws = 0.0, rs = 0.0, back = 0.0;
+        for (int side = 0; side < 2; ++side) {
+          const int64_t p = side == 0 ? s.i : s.j;
+          const double v = sqrt(st[3 * n + p] * st[3 * n + p] + st[4 * n + p] * st[4 * n + p] +
+                                st[5 * n + p] * st[5 * n + p]);
+          const double om = sqrt(st[10 * n + p] * st[10 * n + p] + st[11 * n + p] * st[11 * n + p] +
+                                 st[12 * n + p] * st[12 * n + p]);
+          vs += v;
+          ws += om;
+          wr += om * st[16 * n + p];
+          rs += st[16 * n + p];
+          back += v * fabs(s.ts - st[13 * n + p]);
+        }
+        const double dx = st[0 * n + s.i] - st[0 * n + s.j], dy = st[1 * n + s.i] - st[1 * n + s.j],
+                     dz = st[2 * n + s.i] - st[2 * n + s.j];
+        const double D0 = sqrt(dx * dx + dy * dy + dz * dz) + back;
+        s.delta = (vs + wr + ws * (rs + D0 + vs * s.T_)) * s.T_ * (1.0 + 1e-9) + 1e-300;
+      }
+      __syncthreads();
+    };
     // the K samples and the bisection after a false decision at ts
     // (binary64, operations in the order of the definition, each rounded on
     // its own); returns the status and sets tc / ta / tb
@@ -1638,6 +1821,24 @@ __global__ void __launch_bounds__(Cfg<PREC>::NT, Cfg<PREC>::MINB) pair_kernel(Pa
         atomicAdd(&s.cnt[ST_CHECKS], (unsigned long long)chk);
         atomicAdd(&s.cnt[ST_PAIRS], 1ull);
       }
+    } else if (MODE == MODE_NTIME) {
+      int iters = 0;
+      uint8_t status = 0;
+      double tc = D::add(s.ts, s.T_);
+      int32_t ta = -1, tb = -1;
+      if (ok && s.nA > 0 && s.nB > 0) {
+        motion_bound_narrowing();
+        if (c.template eval<true, true, false>(s.ts, k, -1, s.delta)) {
+          status = 1;
+          ta = int32_t(s.best_key >> 32);
+          tb = int32_t(s.best_key & 0xffffffffu);
+        } else {
+          status = c.narrowing(iters, tc, ta, tb);
+        }
+      }
+      // performed evaluations: the decision at ts and one per narrowing
+      // iteration, each over every triangle pair by the method's count
+      write_times(status, tc, ta, tb, 1 + iters, 1 + iters, 0);
     } else if (MODE == MODE_CTIME) {
       int evals = 0, bis = 0;
       uint8_t status = 0;
@@ -1977,7 +2178,7 @@ cudaError_t launch_detect(int prec, const dem_particles &P, const int32_t *pairs
   return finish_narrow(prec, a, P, pairs, max_pairs, n_pairs, out, S, num_sms, s, true);
 }
 
-cudaError_t launch_ctime(int prec, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
+cudaError_t launch_ctime(int prec, int method, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
                          const int64_t *n_pairs, int K, double tol, double *t_coll, uint8_t *status,
                          int32_t *tri_ab, Scratch &S, int num_sms, cudaStream_t s) {
   PairArgs a = make_args(P, pairs, max_pairs, n_pairs, S);
@@ -1990,6 +2191,8 @@ cudaError_t launch_ctime(int prec, const dem_particles &P, const int32_t *pairs,
   if ((e = cudaMemsetAsync(S.work, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
   if (max_pairs <= 0) return cudaSuccess;
   S.launches += 1 + prepare_tiles(P, S, s);
+  if (method == DEM_CTIME_NARROWING)
+    return prec == 0 ? launch_pairs<0, MODE_NTIME>(a, num_sms, s) : launch_pairs<1, MODE_NTIME>(a, num_sms, s);
   return prec == 0 ? launch_pairs<0, MODE_CTIME>(a, num_sms, s) : launch_pairs<1, MODE_CTIME>(a, num_sms, s);
 }
 

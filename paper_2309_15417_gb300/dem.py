@@ -33,6 +33,7 @@ EXPORTS = ["dem_create", "dem_destroy", "dem_last_error", "dem_build_candidates"
            "dem_collision_times", "dem_detect", "dem_clusters", "dem_lts_sweep", "dem_check", "dem_get_stats",
            "dem_build_candidates_noalloc"]
 DEM_NOALLOC_MAX_PARTICLES = 16384
+DEM_CTIME_SAMPLES, DEM_CTIME_NARROWING = 0, 1
 
 
 class DemError(RuntimeError):
@@ -43,7 +44,7 @@ class DemError(RuntimeError):
 
 class dem_config(C.Structure):
     _fields_ = [("K", C.c_int32), ("bisect_tol", C.c_double), ("precision", C.c_int32),
-                ("reserved", C.c_int32), ("max_particles", C.c_int64), ("max_pairs", C.c_int64),
+                ("ctime_method", C.c_int32), ("max_particles", C.c_int64), ("max_pairs", C.c_int64),
                 ("max_contacts", C.c_int64), ("max_triangles", C.c_int64)]
 
 
@@ -155,9 +156,10 @@ def _check(ctx, rc):
 # ------------------------------------------------------------------ C-ABI mirrors
 
 def dem_create(K=8, tol=1e-3, precision=DEM_PREC_FP32_FIXUP, max_particles=65536, max_pairs=1 << 20,
-               max_contacts=1 << 20, max_triangles=0):
+               max_contacts=1 << 20, max_triangles=0, ctime_method=0):
     L = load()
-    cfg = dem_config(K=K, bisect_tol=tol, precision=precision, reserved=0, max_particles=max_particles,
+    cfg = dem_config(K=K, bisect_tol=tol, precision=precision, ctime_method=ctime_method,
+                     max_particles=max_particles,
                      max_pairs=max_pairs, max_contacts=max_contacts, max_triangles=max_triangles)
     h = C.c_void_p()
     rc = L.dem_create(C.byref(cfg), C.byref(h))
@@ -246,12 +248,12 @@ class Context:
     """Owns a dem_ctx and output buffers sized for its capacities."""
 
     def __init__(self, K=8, tol=1e-3, precision=DEM_PREC_FP32_FIXUP, max_particles=65536, max_pairs=1 << 20,
-                 max_contacts=1 << 20, max_triangles=0, device="cuda"):
+                 max_contacts=1 << 20, max_triangles=0, ctime_method=0, device="cuda"):
         import torch
         self.device = torch.device(device)
         self.max_pairs = int(max_pairs)
         self.max_contacts = int(max_contacts)
-        self.h = dem_create(K, tol, precision, max_particles, max_pairs, max_contacts, max_triangles)
+        self.h = dem_create(K, tol, precision, max_particles, max_pairs, max_contacts, max_triangles, ctime_method)
         z = lambda *s, dt: torch.zeros(*s, dtype=dt, device=self.device)
         self.pairs = z(self.max_pairs, 2, dt=torch.int32)
         self.n_pairs = z(1, dt=torch.int64)
