@@ -72,6 +72,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     p.add_argument("--cpu-sample", type=int, default=96, help="candidate pairs per oracle sample")
     p.add_argument("--no-lts", action="store_true", help="skip the local-time-stepping measurements")
+    p.add_argument("--no-narrowing", action="store_true", help="skip the narrowing-vs-sampling comparison")
     p.add_argument("--column-sweeps", type=int, default=50, help="sweeps of the settling column per replay")
     return p.parse_args()
 
@@ -320,6 +321,8 @@ def gpu_arm(args, rank, world, local):
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_lts:
         res["lts"] = lts_legs(args, dem, W, dev)
+    if rank == 0 and not args.no_narrowing:
+        res["narrowing"] = narrowing_leg(args, dem, W, dev)
     return res
 
 
@@ -365,6 +368,64 @@ def lts_measure(dem, w, old_np, prec, sweeps, reps, dt_max, gravity, dev, max_pa
                t_min=float(sc.state[13][torch.from_numpy(w.is_static == 0).to(dev)].min().item()))
     ctx.close()
     del sc, old, cur0, old0, g
+    torch.cuda.empty_cache()
+    return out
+
+
+def narrowing_leg(args, dem, W, dev, reps=10):
+    """Collision times by the paper's narrowing against K samples + bisection
+    on the same candidate pairs: time per call (CUDA events, L2 flushed
+    between calls), method checks/s, and how the two procedures' answers
+    compare (statuses; for pairs with status 2 in both, the narrowing time
+    minus the sampling time, in units of the pair's step)."""
+    import torch
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = {}
+    cases = (("dense-packing-1000 (the benchmark workload)", W.dense_packing(args.seed)),
+             ("fast dense packing: 5^3 icospheres (320 triangles), v ~ N(0,150), w ~ N(0,150), dt = 1e-4",
+              W.dense_packing(args.seed + 3, nside=5, vsig=150.0, wsig=150.0)))
+    for name, w in cases:
+        sc = dem.Scene.from_workload(w, device=dev)
+        res = {}
+        for method, key in ((dem.DEM_CTIME_SAMPLES, "samples_bisection"), (dem.DEM_CTIME_NARROWING, "narrowing")):
+            ctx = dem.Context(K=w.K, tol=w.tol, precision=dem.DEM_PREC_FP32_FIXUP, max_particles=w.n,
+                              max_pairs=1 << 16, max_contacts=1 << 20, ctime_method=method, device=dev)
+            ctx.build_candidates(sc)
+            ctx.collision_times(sc)
+            torch.cuda.synchronize()
+            ctx.stats(reset=True)
+            ms = []
+            for k in range(reps):
+                flush.fill_(float(k))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ctx.collision_times(sc)
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            ctx.check()
+            st = ctx.stats(reset=True)
+            m = int(ctx.n_pairs.item())
+            res[key] = dict(ms=float(np.mean(ms)), checks_per_s=st["method_checks"] / (sum(ms) / 1e3),
+                            status=ctx.status[:m].cpu().numpy(), t=ctx.t_coll[:m].cpu().numpy(), pairs=m)
+            ctx.close()
+        a, b = res["samples_bisection"], res["narrowing"]
+        both2 = (a["status"] == 2) & (b["status"] == 2)
+        T = float(w.state[W.F_DT, 0])
+        d = (b["t"][both2] - a["t"][both2]) / T
+        out[name] = {
+            "candidate_pairs": a["pairs"],
+            "samples_bisection": {"ms": a["ms"], "checks_per_s": a["checks_per_s"],
+                                  "status_counts": np.bincount(a["status"], minlength=3).tolist()},
+            "narrowing": {"ms": b["ms"], "checks_per_s": b["checks_per_s"],
+                          "status_counts": np.bincount(b["status"], minlength=3).tolist()},
+            "same_status": int((a["status"] == b["status"]).sum()),
+            "status2_in_both": int(both2.sum()),
+            "t_narrowing_minus_t_sampling_over_T": {"mean": float(d.mean()) if d.size else None,
+                                                    "min": float(d.min()) if d.size else None,
+                                                    "max": float(d.max()) if d.size else None}}
+        del sc
+    del flush
     torch.cuda.empty_cache()
     return out
 
@@ -556,7 +617,8 @@ def main():
                               "one CUDA graph",
                 "roofline": roof, "cpu_baseline": cpu, "e2e": r["e2e"], "clocks": r["clocks"],
                 "gpu_launches": int(r["launches"]), "fp64_form": r["fp64"], "fp32_error": r["fp32_err"],
-                "counters_per_step": r["stats_step"], "local_time_stepping": r.get("lts")}
+                "counters_per_step": r["stats_step"], "local_time_stepping": r.get("lts"),
+                "narrowing_vs_sampling": r.get("narrowing")}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
