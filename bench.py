@@ -150,7 +150,7 @@ def _profile_traffic():
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
     if not m or not h:
         return None
-    src = open(os.path.join(ROOT, "paper_2309_15417_gb300", "csrc", "pairs.cu"), "rb").read()
+    src = open(os.path.join(ROOT, "paper_2309_15417_gb300", "csrc", "pair_kernel.cuh"), "rb").read()
     geo = open(os.path.join(ROOT, "paper_2309_15417_gb300", "csrc", "geom.cuh"), "rb").read()
     if hashlib.sha256(src + geo).hexdigest() != h.group(1):
         return None

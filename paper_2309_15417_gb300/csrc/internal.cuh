@@ -78,6 +78,7 @@ struct Scratch {
   int64_t cap_triangles;
   int64_t cap_tiles;
   float4 *tile_sph;               // [cap_tiles]
+  int2 *tile_list;                // [cap_tiles] (particle, tile) entries to compute
   // local time stepping: per-cluster order keys (indexed by cluster id)
   unsigned long long *lts_tmin;   // [n] earliest t_cur of the cluster
   unsigned long long *lts_step;   // [n] smallest member step
