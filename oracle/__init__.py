@@ -73,8 +73,10 @@ def lib():
             L.demo_clusters.argtypes = [C.c_int64, i32p, C.c_int64, u8p, i32p]
             L.demo_clusters.restype = C.c_int64
             L.demo_lts_sweep.argtypes = [dp, dp, u8p, C.c_int64, i64p, fp, C.c_int64, C.c_int, C.c_double,
-                                         C.c_double, C.c_double, dp, C.c_int, i32p, C.c_int64, u8p, dp, i32p,
-                                         u8p, dp, i64p, i64p, C.c_int]
+                                         C.c_double, C.c_double, dp, C.c_int, C.c_int, i32p, C.c_int64, u8p, dp,
+                                         i32p, u8p, dp, i64p, i64p, C.c_int]
+            L.demo_hose_meet.argtypes = [dp, dp, C.c_int64, C.c_int64, C.c_int64]
+            L.demo_hose_meet.restype = C.c_int
             L.demo_lts_sweep.restype = C.c_int64
             _lib = L
     return _lib
@@ -229,7 +231,15 @@ def clusters(n, edges, is_static=None):
     return ids, int(c)
 
 
-def lts_sweep(w, old, dt_max, alpha=2.0, gravity=(0.0, 0.0, 0.0), zero_on_contact=True, n_threads=None):
+def hose_meet(cur, old, i, j):
+    """Space-time hose test of moving particles i, j (cur, old: [17][n] float64)."""
+    cur = _c(cur, np.float64)
+    old = _c(old, np.float64)
+    return bool(lib().demo_hose_meet(_p(cur, C.c_double), _p(old, C.c_double), cur.shape[1], int(i), int(j)))
+
+
+def lts_sweep(w, old, dt_max, alpha=2.0, gravity=(0.0, 0.0, 0.0), zero_on_contact=True, hose=False,
+              n_threads=None):
     """One local-time-stepping sweep; updates w.state (current snapshot) and
     ``old`` (old snapshot, same layout) in place.  Returns dict(pairs, status,
     t_coll, ids, active, t_global, rollbacks, rollbacks_before_old)."""
@@ -252,7 +262,8 @@ def lts_sweep(w, old, dt_max, alpha=2.0, gravity=(0.0, 0.0, 0.0), zero_on_contac
         m = lib().demo_lts_sweep(
             _p(w.state, C.c_double), _p(old, C.c_double), _p(sta, C.c_uint8), n, _p(off, C.c_int64),
             _p(tris, C.c_float), tris.shape[1], int(w.K), float(w.tol), float(dt_max), float(alpha),
-            _p(g, C.c_double), int(bool(zero_on_contact)), _p(pairs, C.c_int32), cap, _p(status, C.c_uint8),
+            _p(g, C.c_double), int(bool(zero_on_contact)), int(bool(hose)), _p(pairs, C.c_int32), cap,
+            _p(status, C.c_uint8),
             _p(tcol, C.c_double), _p(ids, C.c_int32), _p(active, C.c_uint8), _p(tg, C.c_double),
             _p(rb, C.c_int64), _p(rbb, C.c_int64), n_threads or default_threads())
         if m <= cap:

@@ -393,6 +393,55 @@ int64_t demo_broad_phase(const double *state, const uint8_t *is_static, int64_t 
   return cnt;
 }
 
+/* Space-time hose test (Section 3, Check 2) of two moving particles over
+ * their pair interval [ts, ts + T] (ts = min t_cur, T = min dt): each
+ * bounding sphere (radius R + eps) moves on the straight segment from its old
+ * snapshot to its current one (x_old + v_old (t - t_old)) and then with its
+ * current velocity (x + v (t - t_cur)); the hoses meet iff the centres come
+ * within r_i + r_j at some time of the interval.  The interval is cut at the
+ * later t_cur if it lies inside; on each piece the relative position is
+ * d0 + u s (s = time into the piece), whose squared length is smallest at
+ * s = -(d0 . u) / (u . u) clamped to the piece (s = 0 when u = 0). */
+static vec3 hose_at(const double *cur, const double *old, int64_t n, int64_t p, double t, int on_old, vec3 *v) {
+  const double *s = on_old ? old : cur;
+  *v = mk(s[FVX * n + p], s[FVY * n + p], s[FVZ * n + p]);
+  double h = t - s[FTCUR * n + p];
+  return mk(s[FX * n + p] + v->x * h, s[FY * n + p] + v->y * h, s[FZ * n + p] + v->z * h);
+}
+
+static int hose_meet(const double *cur, const double *old, int64_t n, int64_t i, int64_t j) {
+  double ti = cur[FTCUR * n + i], tj = cur[FTCUR * n + j];
+  double ts = ti < tj ? ti : tj, t2 = ti < tj ? tj : ti;
+  double di = cur[FDT * n + i], dj = cur[FDT * n + j];
+  double te = ts + (di < dj ? di : dj);
+  double r = (cur[FRADIUS * n + i] + cur[FEPS * n + i]) + (cur[FRADIUS * n + j] + cur[FEPS * n + j]);
+  int nk = 0;
+  double kk[3];
+  kk[nk++] = ts;
+  if (t2 > ts && t2 < te) kk[nk++] = t2;
+  kk[nk++] = te;
+  for (int q = 0; q + 1 < nk; ++q) {
+    double a = kk[q], b = kk[q + 1];
+    vec3 vi, vj;
+    vec3 xi = hose_at(cur, old, n, i, a, b <= ti, &vi);
+    vec3 xj = hose_at(cur, old, n, j, a, b <= tj, &vj);
+    vec3 d0 = sub(xi, xj), u = sub(vi, vj);
+    double uu = dot(u, u), du = dot(d0, u), s = 0.0;
+    if (uu > 0.0) {
+      s = -du / uu;
+      if (s < 0.0) s = 0.0;
+      if (s > b - a) s = b - a;
+    }
+    vec3 dm = axpy(d0, u, s);
+    if (dot(dm, dm) <= r * r) return 1;
+  }
+  return 0;
+}
+
+int demo_hose_meet(const double *cur, const double *old, int64_t n, int64_t i, int64_t j) {
+  return hose_meet(cur, old, n, i, j);
+}
+
 static int cmp_pair(const void *x, const void *y) {
   const int32_t *a = (const int32_t *)x, *b = (const int32_t *)y;
   if (a[0] != b[0]) return a[0] < b[0] ? -1 : 1;
@@ -932,7 +981,7 @@ int64_t demo_clusters(int64_t n, const int32_t *edges, int64_t e, const uint8_t 
  * unused).  Static particles are never changed. */
 int64_t demo_lts_sweep(double *cur, double *old, const uint8_t *is_static, int64_t n, const int64_t *tri_off,
                        const float *tris, int64_t n_tris, int K, double tol, double dt_max, double alpha,
-                       const double gravity[3], int zero_on_contact, int32_t *pairs_out, int64_t cap,
+                       const double gravity[3], int zero_on_contact, int hose, int32_t *pairs_out, int64_t cap,
                        uint8_t *status_out, double *t_coll_out, int32_t *cluster_id, uint8_t *active,
                        double *t_global, int64_t *rollbacks, int64_t *rollbacks_before_old, int n_threads) {
   /* 1. particle step sizes (Eq. "damped particle time step size"): a creeping
@@ -944,10 +993,23 @@ int64_t demo_lts_sweep(double *cur, double *old, const uint8_t *is_static, int64
     double d = tc > to ? alpha * (tc - to) : dt_max;
     cur[FDT * n + p] = d < dt_max ? d : dt_max;
   }
-  /* 2. candidates over each particle's own step */
+  /* 2. candidates over each particle's own step; with the hose check, pairs
+   *    of two moving particles whose space-time hoses do not meet are
+   *    dropped (Section 3, Check 2) */
   int64_t m = demo_broad_phase(cur, is_static, n, tri_off, tris, n_tris, pairs_out, 0);
   int32_t *pairs = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)(m > 0 ? m : 1));
   demo_broad_phase(cur, is_static, n, tri_off, tris, n_tris, pairs, m);
+  if (hose) {
+    int64_t kept = 0;
+    for (int64_t k = 0; k < m; ++k) {
+      int64_t i = pairs[2 * k], j = pairs[2 * k + 1];
+      if (!is_st(is_static, j) && !hose_meet(cur, old, n, i, j)) continue;
+      pairs[2 * kept] = pairs[2 * k];
+      pairs[2 * kept + 1] = pairs[2 * k + 1];
+      ++kept;
+    }
+    m = kept;
+  }
   /* 3. clusters of the candidate graph */
   demo_clusters(n, pairs, m, is_static, cluster_id);
   /* 4. consolidation: every member of a cluster rolls back to the cluster's

@@ -98,7 +98,14 @@ void demo_collision_times_narrowing(const double *state, const uint8_t *is_stati
 int64_t demo_clusters(int64_t n, const int32_t *edges, int64_t e, const uint8_t *is_static,
                       int32_t *id);
 
-/* One sweep of the local-time-stepping cycle: particle steps
+/* Space-time hose test (Check 2 of the broad phase) of moving particles i
+ * and j over their pair interval: bounding spheres (R + eps) on the old ->
+ * current segment, then with the current velocity; 1 iff they overlap at some
+ * common time.  cur/old as in demo_lts_sweep. */
+int demo_hose_meet(const double *cur, const double *old, int64_t n, int64_t i, int64_t j);
+
+/* One sweep of the local-time-stepping cycle (hose != 0: candidates of two
+ * moving particles must also pass the hose test): particle steps
  * dt_p = min(alpha (t_cur - t_old), dt_max) (dt_max without history), broad
  * phase, clusters, consolidation (members roll back to the cluster's earliest
  * t_cur by free flight from the old snapshot, and take the smallest member
@@ -114,7 +121,7 @@ int64_t demo_clusters(int64_t n, const int32_t *edges, int64_t e, const uint8_t 
  * the number of candidate pairs. */
 int64_t demo_lts_sweep(double *cur, double *old, const uint8_t *is_static, int64_t n,
                        const int64_t *tri_off, const float *tris, int64_t n_tris, int K, double tol,
-                       double dt_max, double alpha, const double gravity[3], int zero_on_contact,
+                       double dt_max, double alpha, const double gravity[3], int zero_on_contact, int hose,
                        int32_t *pairs, int64_t cap, uint8_t *status, double *t_coll,
                        int32_t *cluster_id, uint8_t *active, double *t_global, int64_t *rollbacks,
                        int64_t *rollbacks_before_old, int n_threads);

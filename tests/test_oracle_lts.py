@@ -160,3 +160,84 @@ def test_invariants_over_sweeps():
             assert np.array_equal(w.state[:, w.is_static == 1], st0)
             adv = w.state[W.F_TCUR] != before[W.F_TCUR]
             assert np.array_equal(adv[mv], r["active"][mv].astype(bool))
+
+
+# ----------------------------------------------------------------------------- space-time hoses
+
+def _two_movers(p1, v1, p2, v2, R=0.5, eps=0.25, dt=2.0 ** -9):
+    w = W._assemble("two", [W.icosphere(1)], [0, 0], [p1, p2], [v1, v2], [(1, 0, 0, 0)] * 2, np.zeros((2, 3)),
+                    0.0, dt, eps)
+    w.state[W.F_RADIUS] = R
+    return w
+
+
+def test_hose_parallel_and_following_movers():
+    """The paper's motivating cases for Check 2: two fast particles moving in
+    parallel, and one following the other, have overlapping swept spheres but
+    hoses that never meet (constant separation above the radius sum)."""
+    v = (1024.0, 0.0, 0.0)  # moves 2 over the step
+    for w in (_two_movers((0, 0, 0), v, (0, 1.75, 0), v), _two_movers((0, 0, 0), v, (-1.75, 0, 0), v)):
+        assert oracle.broad_phase(w).tolist() == [[0, 1]]
+        assert not oracle.hose_meet(w.state, w.state, 0, 1)
+    # approaching head on they meet
+    w = _two_movers((0, 0, 0), v, (3.0, 0, 0), (-1024.0, 0.0, 0.0))
+    assert oracle.hose_meet(w.state, w.state, 0, 1)
+
+
+def test_hose_crossing_paths_closed_form():
+    """Paths crossing at right angles at heights h apart: the closest approach
+    is h at t = 1/k, so the hoses meet exactly when h <= r_i + r_j = 1.5."""
+    k = 1024.0
+    for h, expect in ((1.5, True), (1.5 + 2.0 ** -30, False), (1.0, True)):
+        w = _two_movers((-1.0, 0, 0), (k, 0, 0), (0, -1.0, h), (0, k, 0))
+        assert oracle.hose_meet(w.state, w.state, 0, 1) == expect, h
+
+
+def test_hose_follows_the_old_segment():
+    """Before its current time stamp a particle is on the straight segment
+    from its old snapshot (not on a backward extrapolation of its current
+    velocity): a particle that moved along +y during its previous step and now
+    moves along +x passes through a resting particle at t = T/4."""
+    T = 2.0 ** -9
+    c = 2.0 ** 11
+    w = _two_movers((0, 0, 0), (c, 0, 0), (0, -c * T / 4, 5.0), (0, 0, 0), R=0.125, eps=0.0625, dt=T)
+    cur = w.state.copy()
+    cur[W.F_TCUR, 0] = T / 2
+    cur[W.F_Z, 1] = 0.0
+    cur[W.F_Y, 1] = c * T / 4 - c * T / 2  # particle 0's position at T/4 on its old path
+    old = cur.copy()
+    old[W.F_TCUR, 0] = 0.0
+    old[W.F_X, 0], old[W.F_Y, 0] = 0.0, -c * T / 2
+    old[W.F_VX, 0], old[W.F_VY, 0] = 0.0, c
+    assert oracle.hose_meet(cur, old, 0, 1)
+    # the same current snapshot with a straight history (old = current) misses
+    assert not oracle.hose_meet(cur, cur, 0, 1)
+
+
+def test_hose_is_conservative():
+    """At a common time stamp every moving pair that touches at some sampled
+    time of its interval passes the hose test (the spheres cover the
+    particles and their halos)."""
+    for seed in range(2):
+        w = W.small_icospheres(seed)
+        w.state[W.F_VX:W.F_VZ + 1] *= 150.0
+        pairs = oracle.broad_phase(w)
+        hit = set()
+        for t in np.linspace(0.0, 1e-3, 6):
+            r = oracle.narrow_phase(w, pairs, t_eval=np.full(len(pairs), t))
+            hit |= {tuple(p) for p, f in zip(pairs, r["flag"]) if f}
+        kept = {tuple(p) for p in pairs if oracle.hose_meet(w.state, w.state, p[0], p[1])}
+        assert len(hit) > 2 and hit <= kept
+        assert len(kept) < len(pairs)  # the check removes some candidates
+
+
+def test_lts_sweep_with_hoses_keeps_invariants():
+    w = W.lts_mixed_steps(0, n=600)
+    old = w.state.copy()
+    last = None
+    for sweep in range(3):
+        r = oracle.lts_sweep(w, old, 4e-3, hose=True)
+        assert r["rollbacks_before_old"] == 0
+        now = float(np.min(w.state[W.F_TCUR]))
+        assert last is None or now > last
+        last = now
