@@ -326,7 +326,7 @@ def gpu_arm(args, rank, world, local):
     return res
 
 
-def lts_measure(dem, w, old_np, prec, sweeps, reps, dt_max, gravity, dev, max_pairs):
+def lts_measure(dem, w, old_np, prec, sweeps, reps, dt_max, gravity, dev, max_pairs, hose=False):
     """Sweeps of the local-time-stepping cycle captured in one CUDA graph and
     replayed `reps` times from the same starting snapshots (restored between
     replays, outside the timed events).  Returns times, counters and the final
@@ -337,14 +337,14 @@ def lts_measure(dem, w, old_np, prec, sweeps, reps, dt_max, gravity, dev, max_pa
     cur0, old0 = sc.state.clone(), old.clone()
     ctx = dem.Context(K=w.K, tol=w.tol, precision=prec, max_particles=w.n, max_pairs=max_pairs,
                       max_contacts=1 << 16, max_triangles=w.n_tris, device=dev)
-    ctx.lts_sweep(sc, old, dt_max, gravity=gravity)  # first call outside the capture
+    ctx.lts_sweep(sc, old, dt_max, gravity=gravity, hose=hose)  # first call outside the capture
     torch.cuda.synchronize()
     ctx.check()
     l0 = ctx.stats()["kernel_launches"]
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
         for _ in range(sweeps):
-            ctx.lts_sweep(sc, old, dt_max, gravity=gravity)
+            ctx.lts_sweep(sc, old, dt_max, gravity=gravity, hose=hose)
     launches = ctx.stats()["kernel_launches"] - l0
     ms, st = [], {}
     for r in range(reps + 1):  # the first replay warms up
@@ -452,7 +452,14 @@ def lts_legs(args, dem, W, dev):
         "checks_per_s": st["method_checks"] / (r["ms"] / 1e3),
         "advances_per_cycle": st["advances"], "candidate_pairs": r["pairs"], "clusters": r["clusters"],
         "kernels_per_cycle": r["launches"]}
-    del w, old, r
+    # the same cycle with the space-time hose check (Check 2) in the broad phase
+    rh = lts_measure(dem, w, old, dem.DEM_PREC_FP32_FIXUP, 1, 5, 1e-2, (0.0, 0.0, 0.0), dev, 1 << 20, hose=True)
+    res["lts_cycle_100k"]["with_hose_check"] = {
+        "ms_per_cycle": rh["ms"], "candidate_pairs": rh["pairs"], "clusters": rh["clusters"],
+        "advances_per_cycle": rh["stats"]["advances"],
+        "final_snapshots_identical_to_without": bool(np.array_equal(rh["cur"], r["cur"]) and
+                                                     np.array_equal(rh["old"], r["old"]))}
+    del w, old, r, rh
     # the settling column: sweeps in a graph, both precisions
     S = args.column_sweeps
     w = W.settling_column(args.seed)

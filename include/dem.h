@@ -245,7 +245,10 @@ typedef struct {
   double alpha;            /* damping of the particle step (Section 3; the paper uses 2) */
   double gravity[3];       /* stand-in update: acceleration of particles not in contact */
   int32_t zero_on_contact; /* stand-in update: particles in contact stop (v = w = 0) */
-  int32_t reserved;
+  int32_t hose;            /* 1: candidates of two moving particles must also pass the space-time
+                              hose test (Section 3, Check 2): bounding spheres (R + eps) on the
+                              old -> current segment, then with the current velocity, overlapping
+                              at some common time of the pair interval (binary64) */
 } dem_lts_params;
 
 /* Outputs of one sweep (caller-owned device arrays). */
@@ -266,7 +269,8 @@ typedef struct {
  * Sections 3-5).  In order, all on the stream, without host round trips:
  *  1. particle steps dt_p = min(alpha (t_cur - t_old), dt_max), dt_max when
  *     t_old = t_cur (Eq. "damped particle time step size"), written to cur;
- *  2. candidate pairs (dem_build_candidates) and 3. their clusters;
+ *  2. candidate pairs (dem_build_candidates; with prm->hose, moving pairs
+ *     whose space-time hoses do not meet are dropped) and 3. their clusters;
  *  4. consolidation (Section 4): every member of a cluster goes back to the
  *     cluster's earliest t_cur by free flight from its old snapshot (the
  *     interpolation between the snapshots) and takes the cluster step (the

@@ -155,6 +155,53 @@ __global__ void k_scatter(int64_t n, const int4 *cell, const int64_t *bstart, in
   }
 }
 
+// Space-time hose test (Check 2 of the paper's broad phase) of moving
+// particles i, j over their pair interval: bounding spheres (R + eps) on the
+// straight segment from the old snapshot to the current one, then with the
+// current velocity; true iff they overlap at some common time.  On each
+// piece between the knots the squared distance of the relative linear motion
+// d0 + u s is smallest at s = -(d0 . u) / (u . u), clamped to the piece.
+__device__ __forceinline__ V3<double> hose_at(const double *cur, const double *old, int64_t n, int64_t p, double t,
+                                              bool on_old, V3<double> &v) {
+  const double *s = on_old ? old : cur;
+  v = V3<double>{s[3 * n + p], s[4 * n + p], s[5 * n + p]};
+  const double h = D::sub(t, s[13 * n + p]);
+  return V3<double>{D::add(s[0 * n + p], D::mul(v.x, h)), D::add(s[1 * n + p], D::mul(v.y, h)),
+                    D::add(s[2 * n + p], D::mul(v.z, h))};
+}
+
+__device__ bool hose_meet(const double *cur, const double *old, int64_t n, int64_t i, int64_t j) {
+  using G = Geo<OpsD>;
+  const double ti = cur[13 * n + i], tj = cur[13 * n + j];
+  const double ts = ti < tj ? ti : tj, t2 = ti < tj ? tj : ti;
+  const double di = cur[14 * n + i], dj = cur[14 * n + j];
+  const double te = D::add(ts, di < dj ? di : dj);
+  const double r = D::add(D::add(cur[16 * n + i], cur[15 * n + i]), D::add(cur[16 * n + j], cur[15 * n + j]));
+  double kk[3];
+  int nk = 0;
+  kk[nk++] = ts;
+  if (t2 > ts && t2 < te) kk[nk++] = t2;
+  kk[nk++] = te;
+  for (int q = 0; q + 1 < nk; ++q) {
+    const double a = kk[q], b = kk[q + 1];
+    V3<double> vi, vj;
+    const V3<double> xi = hose_at(cur, old, n, i, a, b <= ti, vi);
+    const V3<double> xj = hose_at(cur, old, n, j, a, b <= tj, vj);
+    const V3<double> d0 = G::sub(xi, xj), u = G::sub(vi, vj);
+    const double uu = G::dot(u, u), du = G::dot(d0, u);
+    double s = 0.0;
+    if (uu > 0.0) {
+      s = D::div(-du, uu);
+      if (s < 0.0) s = 0.0;
+      const double ba = D::sub(b, a);
+      if (s > ba) s = ba;
+    }
+    const V3<double> dm = G::axpy(d0, u, s);
+    if (G::dot(dm, dm) <= D::mul(r, r)) return true;
+  }
+  return false;
+}
+
 // One warp per moving particle i: lane c < 27 scans neighbour cell c, then
 // the lanes share the static boxes; counts are combined with warp prefix
 // sums.  WRITE: the partners are written at the particle's offset and sorted
@@ -172,8 +219,8 @@ template <bool WRITE>
 __global__ void k_pairs(int64_t n, const double *st, const Sphere4 *sph, const int4 *cell,
                         const uint8_t *is_static, const int32_t *bcnt, const int64_t *bstart, const int32_t *ids,
                         uint32_t mask, const int32_t *static_ids, const int32_t *n_static,
-                        const unsigned long long *sbox, int64_t *pcnt, const int64_t *poff, int32_t *pairs,
-                        int64_t cap, const int64_t *n_pairs, uint32_t *err) {
+                        const unsigned long long *sbox, const double *hose_old, int64_t *pcnt,
+                        const int64_t *poff, int32_t *pairs, int64_t cap, const int64_t *n_pairs, uint32_t *err) {
   if (WRITE && blockIdx.x == 0 && threadIdx.x == 0 && *n_pairs > cap) set_err(err, ERR_CAPACITY);
   const int lane = threadIdx.x & 31;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -201,7 +248,8 @@ __global__ void k_pairs(int64_t n, const double *st, const Sphere4 *sph, const i
       const double ddx = D::sub(si.x, sj.x), ddy = D::sub(si.y, sj.y), ddz = D::sub(si.z, sj.z);
       const double dd = D::add(D::add(D::mul(ddx, ddx), D::mul(ddy, ddy)), D::mul(ddz, ddz));
       const double rr = D::add(si.w, sj.w);
-      return dd <= D::mul(rr, rr);
+      if (!(dd <= D::mul(rr, rr))) return false;
+      return hose_old == nullptr || hose_meet(st, hose_old, n, i, j);
     };
     // static partner number q: the swept sphere meets the widened box
     auto meets_box = [&](int q) {
@@ -273,7 +321,7 @@ __global__ void k_pairs(int64_t n, const double *st, const Sphere4 *sph, const i
 }  // namespace
 
 cudaError_t launch_broad(const dem_particles &P, int32_t *pairs, int64_t cap, int64_t *n_pairs, Scratch &S,
-                         cudaStream_t s) {
+                         cudaStream_t s, const double *hose_old) {
   const int64_t n = P.n;
   cudaError_t e;
   if ((e = cudaMemsetAsync(S.rho_max, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
@@ -296,12 +344,12 @@ cudaError_t launch_broad(const dem_particles &P, int32_t *pairs, int64_t cap, in
   k_scatter<<<grid, tb, 0, s>>>(n, S.cell, S.bucket_start, S.bucket_cur, S.bucket_ids);
   const unsigned wgrid = (unsigned)((n + 7) / 8);  // one warp per particle
   k_pairs<false><<<wgrid, tb, 0, s>>>(n, P.state, S.sph, S.cell, P.is_static, S.bucket_cnt, S.bucket_start,
-                                      S.bucket_ids, mask, S.static_ids, S.n_static, S.sbox, S.pcnt, nullptr,
-                                      nullptr, 0, nullptr, S.err);
+                                      S.bucket_ids, mask, S.static_ids, S.n_static, S.sbox, hose_old, S.pcnt,
+                                      nullptr, nullptr, 0, nullptr, S.err);
   S.launches += 2 + scan_exclusive_i64(S.pcnt, S.poff, n, n_pairs, S.scan_part, s);
   k_pairs<true><<<wgrid, tb, 0, s>>>(n, P.state, S.sph, S.cell, P.is_static, S.bucket_cnt, S.bucket_start,
-                                     S.bucket_ids, mask, S.static_ids, S.n_static, S.sbox, nullptr, S.poff, pairs,
-                                     cap, n_pairs, S.err);
+                                     S.bucket_ids, mask, S.static_ids, S.n_static, S.sbox, hose_old, nullptr,
+                                     S.poff, pairs, cap, n_pairs, S.err);
   S.launches += 1;
   return cudaGetLastError();
 }

@@ -100,8 +100,10 @@ int scan_exclusive_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_
                               cudaStream_t s);
 
 // launchers
+// hose_old: the old snapshots for the space-time hose test of moving pairs
+// (nullptr: the swept-sphere and box tests alone)
 cudaError_t launch_broad(const dem_particles &P, int32_t *pairs, int64_t cap, int64_t *n_pairs,
-                         Scratch &S, cudaStream_t s);
+                         Scratch &S, cudaStream_t s, const double *hose_old = nullptr);
 cudaError_t launch_narrow(int prec, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
                           const int64_t *n_pairs, const double *t_eval, const dem_narrow_out &out,
                           Scratch &S, int num_sms, cudaStream_t s);

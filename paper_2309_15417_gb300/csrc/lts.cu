@@ -178,7 +178,8 @@ cudaError_t launch_lts(int prec, int method, int K, double tol, const dem_partic
   const unsigned pgrid = (unsigned)(out.max_pairs > 0 ? (out.max_pairs + tb - 1) / tb : 1);
   k_lts_step<<<grid, tb, 0, s>>>(n, cur, old, P.is_static, prm.dt_max, prm.alpha);
   S.launches += 1;
-  if ((e = launch_broad(P, out.pairs, out.max_pairs, out.n_pairs, S, s)) != cudaSuccess) return e;
+  if ((e = launch_broad(P, out.pairs, out.max_pairs, out.n_pairs, S, s, prm.hose ? old : nullptr)) != cudaSuccess)
+    return e;
   if ((e = launch_clusters(n, out.pairs, out.max_pairs, out.n_pairs, P.is_static, out.cluster_id, out.n_clusters, S,
                            s)) != cudaSuccess)
     return e;

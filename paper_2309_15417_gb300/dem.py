@@ -61,7 +61,7 @@ class dem_narrow_out(C.Structure):
 
 class dem_lts_params(C.Structure):
     _fields_ = [("dt_max", C.c_double), ("alpha", C.c_double), ("gravity", C.c_double * 3),
-                ("zero_on_contact", C.c_int32), ("reserved", C.c_int32)]
+                ("zero_on_contact", C.c_int32), ("hose", C.c_int32)]
 
 
 class dem_lts_out(C.Structure):
@@ -341,7 +341,7 @@ class Context:
         self.clusters(scene, stream=stream)
 
     def lts_sweep(self, scene: Scene, old, dt_max, alpha=2.0, gravity=(0.0, 0.0, 0.0), zero_on_contact=True,
-                  stream=None):
+                  hose=False, stream=None):
         """One local-time-stepping sweep: scene.state is the current snapshot
         and ``old`` (same shape) the old one; both are updated in place.
         Outputs in this context's buffers (pairs, n_pairs, t_coll, status,
@@ -355,7 +355,7 @@ class Context:
         if old.dtype != torch.float64 or not old.is_contiguous() or old.shape != scene.state.shape:
             raise ValueError("old must be a contiguous float64 tensor shaped like the state")
         prm = dem_lts_params(dt_max=float(dt_max), alpha=float(alpha), gravity=(C.c_double * 3)(*gravity),
-                             zero_on_contact=int(bool(zero_on_contact)), reserved=0)
+                             zero_on_contact=int(bool(zero_on_contact)), hose=int(bool(hose)))
         out = dem_lts_out(pairs=self.pairs.data_ptr(), max_pairs=self.max_pairs, n_pairs=self.n_pairs.data_ptr(),
                           t_coll=self.t_coll.data_ptr(), status=self.status.data_ptr(), tri_ab=self.ct_ab.data_ptr(),
                           cluster_id=self.cluster_id.data_ptr(), n_clusters=self.n_clusters.data_ptr(),

@@ -25,7 +25,7 @@ def _mixed_time_stamps(w, dt_max, seed):
     return old
 
 
-def _compare_sweeps(dem, w, old, prec, sweeps, dt_max, gravity, max_pairs=1 << 16):
+def _compare_sweeps(dem, w, old, prec, sweeps, dt_max, gravity, max_pairs=1 << 16, hose=False):
     import torch
     c = dem.Context(K=w.K, tol=w.tol, precision=prec, max_particles=max(w.n, 16), max_pairs=max_pairs,
                     max_contacts=1 << 16, max_triangles=w.n_tris)
@@ -35,9 +35,9 @@ def _compare_sweeps(dem, w, old, prec, sweeps, dt_max, gravity, max_pairs=1 << 1
     o_old = old.copy()
     seen = set()
     for s in range(sweeps):
-        c.lts_sweep(sc, g_old, dt_max, gravity=gravity)
+        c.lts_sweep(sc, g_old, dt_max, gravity=gravity, hose=hose)
         c.check()
-        r = oracle.lts_sweep(o_w, o_old, dt_max, gravity=gravity)
+        r = oracle.lts_sweep(o_w, o_old, dt_max, gravity=gravity, hose=hose)
         m = int(c.n_pairs.item())
         assert np.array_equal(c.pairs[:m].cpu().numpy(), r["pairs"]), s
         assert np.array_equal(c.status[:m].cpu().numpy(), r["status"]), s
@@ -76,6 +76,19 @@ def test_lts_sweeps_floor_scene(dem, prec):
     w = W.floor_scene(1)
     seen = _compare_sweeps(dem, w, w.state.copy(), prec, 6, 1e-3, (0.0, 0.0, -9.81))
     assert 1 in seen
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_lts_sweeps_with_hoses(dem, prec):
+    """The space-time hose check in the broad phase: mixed time stamps (old
+    segments matter) and fast free particles."""
+    w = W.lts_mixed_steps(1, n=1500)
+    w.state[W.F_VX:W.F_VZ + 1] *= 20.0
+    old = _mixed_time_stamps(w, 4e-3, 2)
+    _compare_sweeps(dem, w, old, prec, 4, 4e-3, (0.0, 0.0, 0.0), hose=True)
+    w = W.small_icospheres(2)
+    w.state[W.F_VX:W.F_VZ + 1] *= 150.0
+    _compare_sweeps(dem, w, w.state.copy(), prec, 4, 1e-3, (0.0, 0.0, -9.81), hose=True)
 
 
 def test_lts_sweeps_settling_column(dem):
