@@ -123,6 +123,9 @@ def load(build_if_needed: bool = True):
         L.dem_get_stats.restype = C.c_int
         L.dem_build_candidates_noalloc.argtypes = [C.POINTER(dem_particles), vp, i64, vp, vp]
         L.dem_build_candidates_noalloc.restype = C.c_int
+        L.dem_lts_sweep.argtypes = [vp, C.POINTER(dem_particles), vp, vp, C.POINTER(dem_lts_params),
+                                    C.POINTER(dem_lts_out), vp]
+        L.dem_lts_sweep.restype = C.c_int
         _lib = L
         return L
 
