@@ -568,9 +568,12 @@ struct Cta {
   // is within 2E of the smallest one are then recomputed in binary64: every
   // feature that can attain the binary64 minimum is among them, so the
   // minimum and its first attaining feature (sequential order, strict "<")
-  // are those of Geo<OpsD>::tri_dist2.  a, b index triangles within
+  // are those of Geo<OpsD>::tri_dist2.  cross = false skips the crossing
+  // tests: the caller knows the FP32 distance of the pair exceeds 4E, so the
+  // binary64 distance is positive (|d32 - d64| <= E) and no crossing exists.
+  // a, b index triangles within
   // particles i, j.  Every lane returns the result.
-  __device__ __noinline__ double exact_warp(int a, int b, V3<double> &pa, V3<double> &pb) const {
+  __device__ __noinline__ double exact_warp(int a, int b, V3<double> &pa, V3<double> &pb, bool cross = true) const {
     using GF = Geo<OpsF>;
     V3<double> v{0.0, 0.0, 0.0};
     V3<float> vf{0.f, 0.f, 0.f};
@@ -608,7 +611,8 @@ struct Cta {
     // binary64 crossing tests
     bool hit = false;
     V3<double> p1{0.0, 0.0, 0.0}, p2{0.0, 0.0, 0.0};
-    if (lane < 3) {
+    if (!cross) {
+    } else if (lane < 3) {
       hit = GD::seg_tri_cross(X[lane], X[lane == 2 ? 0 : lane + 1], Y[0], Y[1], Y[2], p1);
     } else if (lane < 6) {
       const int j = lane - 3;
@@ -754,7 +758,8 @@ struct Cta {
           if (__shfl_sync(0xffffffffu, f, 0)) break;
         }
         V3<double> qa, qb;
-        const double e2 = exact_warp(ta * TT + a, tb * TT + b, qa, qb);
+        // decision and contact band entries have d32 >= eps - E
+        const double e2 = exact_warp(ta * TT + a, tb * TT + b, qa, qb, (why & WHY_ARG) || !(s.eps > 6.0 * s.Ed));
         ++n64;
         const double de = OpsD::sqrt(e2);
         if (DECIDE && (why & WHY_DEC) && de <= s.eps && lane == 0) s.found = 1;
@@ -1317,15 +1322,19 @@ struct Cta {
         }
     }
     unsigned long long n64 = 0;
-    // round 0: the smallest key alone (it settles most intersecting pairs);
-    // then NW candidates per round
-    for (int r0 = 0; r0 < n; r0 = (r0 == 0 ? 1 : r0 + NW)) {
-      const int q = r0 == 0 ? (w == 0 ? 0 : n) : r0 + w;
+    // a pair whose FP32 minimum exceeds 4E has no intersecting triangles:
+    // no crossing tests, and no zero distance that would end the rounds early
+    const bool may_touch = !(mh > 4.0 * s.Ed);
+    // round 0: the smallest key alone when it may be a zero distance (that
+    // settles most intersecting pairs); then NW candidates per round
+    const int first = may_touch ? 1 : 0;
+    for (int r0 = 0; r0 < n; r0 = (r0 == 0 && first ? 1 : r0 + NW)) {
+      const int q = (r0 == 0 && first) ? (w == 0 ? 0 : n) : r0 + w;
       const unsigned long long key = q < n ? s.ac_key[q] : ~0ull;
       double e2 = OpsD::inf();
       if (key != ~0ull) {
         V3<double> qa, qb;
-        e2 = exact_warp(int(key >> 32), int(key & 0xffffffffu), qa, qb);
+        e2 = exact_warp(int(key >> 32), int(key & 0xffffffffu), qa, qb, may_touch);
         update_best(e2, key, qa, qb);
         ++n64;
       }
@@ -1397,7 +1406,8 @@ struct Cta {
           const int src = __ffs(bm) - 1;
           bm &= bm - 1;
           V3<double> qa, qb;
-          const double e2 = exact_warp(__shfl_sync(0xffffffffu, ag, src), __shfl_sync(0xffffffffu, bg, src), qa, qb);
+          const double e2 = exact_warp(__shfl_sync(0xffffffffu, ag, src), __shfl_sync(0xffffffffu, bg, src), qa, qb,
+                                       !(s.eps > 6.0 * s.Ed));
           ++n64;
           if (OpsD::sqrt(e2) <= s.eps) yes_any = true;
         }
