@@ -152,6 +152,7 @@ struct __align__(128) Smem {
   int wcnt[NW];
   unsigned long long il[ILCAP];       // pair-interval candidates (a << 32 | b, within the particles)
   int nil, ilover, ilcol;
+  double ilthr;                       // distance threshold of the list (eps + delta + 2E)
   double delta;                       // bound on the change of any distance over the interval
   double gR[GRID_MAX][2][9], gX[GRID_MAX][2][3];  // poses at the sample times
   unsigned long long bound;           // bits of a non-negative double
@@ -824,21 +825,6 @@ struct Cta {
       const bool have = k < cnt;
       const uint32_t ent = have ? list[k] : 0u;
       const int a = int(ent >> 16), b = int(ent & 0xffffu);
-      if (s.ilcol) {
-        // remember the candidate for the rest of the pair interval
-        const uint32_t m = __ballot_sync(0xffffffffu, have);
-        int base = 0;
-        if (lane == 0) base = atomicAdd(&s.nil, __popc(m));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (have) {
-          const int pos = base + __popc(m & lanemask_lt());
-          const int ag = ta * TT + a, bg = tb * TT + b;
-          if (pos < ILCAP)
-            s.il[pos] = (static_cast<unsigned long long>(ag) << 32) | static_cast<uint32_t>(bg);
-          else
-            s.ilover = 1;
-        }
-      }
       T d2 = O::inf();
       V pa{}, pb{};
       if (have) {
@@ -863,6 +849,26 @@ struct Cta {
         ++n32;
       }
       const T d = O::sqrt(d2);
+      if (s.ilcol) {
+        // remember the triangle pair for the rest of the pair interval when
+        // its distance at ts is within the list threshold (eps + delta plus
+        // the FP32 band): no other pair can come within eps in the interval
+        const bool col = have && double(d) <= s.ilthr;
+        const uint32_t m = __ballot_sync(0xffffffffu, col);
+        if (m) {
+          int base = 0;
+          if (lane == 0) base = atomicAdd(&s.nil, __popc(m));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          if (col) {
+            const int pos = base + __popc(m & lanemask_lt());
+            const int ag = ta * TT + a, bg = tb * TT + b;
+            if (pos < ILCAP)
+              s.il[pos] = (static_cast<unsigned long long>(ag) << 32) | static_cast<uint32_t>(bg);
+            else
+              s.ilover = 1;
+          }
+        }
+      }
       const unsigned long long key = key_of(a, b, ta, tb);
       if constexpr (PREC == 0) {
         uint32_t why = 0;
@@ -1149,37 +1155,43 @@ struct Cta {
       pose_exact(A.st, A.n, p, t, s.rc, s.rs, tid == 0 ? s.RA : s.RB, tid == 0 ? s.XA : s.XB);
     }
     __syncthreads();
-    if (tid == 0) {
-      // relative pose of B in A's frame in FP32 (its error is inside the band)
-      const float d[3] = {float(s.XB[0] - s.XA[0]), float(s.XB[1] - s.XA[1]), float(s.XB[2] - s.XA[2])};
-      float ra[9], rb[9], tr[3];
-      for (int q = 0; q < 9; ++q) {
-        ra[q] = float(s.RA[q]);
-        rb[q] = float(s.RB[q]);
+    if (w == 0) {
+      // relative pose of B in A's frame in FP32 (its error is inside the
+      // band): lane 3r+c computes Rr[r][c], lane 9+r computes tr[r]
+      const int r = lane < 9 ? lane / 3 : (lane < 12 ? lane - 9 : 0), c = lane < 9 ? lane % 3 : 0;
+      const float ra0 = float(s.RA[r]), ra1 = float(s.RA[3 + r]), ra2 = float(s.RA[6 + r]);
+      float v;
+      if (lane < 9)
+        v = ra0 * float(s.RB[c]) + ra1 * float(s.RB[3 + c]) + ra2 * float(s.RB[6 + c]);
+      else
+        v = ra0 * float(s.XB[0] - s.XA[0]) + ra1 * float(s.XB[1] - s.XA[1]) + ra2 * float(s.XB[2] - s.XA[2]);
+      if (lane < 9)
+        s.Rr[lane] = v;
+      else if (lane < 12)
+        s.tr[lane - 9] = v;
+      const float tr0 = __shfl_sync(0xffffffffu, v, 9), tr1 = __shfl_sync(0xffffffffu, v, 10),
+                  tr2 = __shfl_sync(0xffffffffu, v, 11);
+      if (lane == 0) {
+        const float tr[3] = {tr0, tr1, tr2};
+        const double ri = A.st[16 * A.n + s.i], rj = A.st[16 * A.n + s.j];
+        if (PREC == 0) {
+          const double S = ri + rj + sqrtf(tr[0] * tr[0] + tr[1] * tr[1] + tr[2] * tr[2]);
+          s.Ed = S * ERR_REL32;
+          s.Elb = s.Ed;
+          // FP32 A-frame data stay valid; B moves
+          s.frmB = -1;
+        } else {
+          const double S = ri + rj + sqrt(s.XA[0] * s.XA[0] + s.XA[1] * s.XA[1] + s.XA[2] * s.XA[2]) +
+                           sqrt(s.XB[0] * s.XB[0] + s.XB[1] * s.XB[1] + s.XB[2] * s.XB[2]);
+          s.Ed = 0.0;
+          s.Elb = S * ERR_REL64_LB;
+          s.frmA = -1;
+          s.frmB = -1;
+        }
+        s.found = 0;
+        s.nac = 0;
+        s.bound = dbits(OpsD::inf());
       }
-      for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) s.Rr[r * 3 + c] = ra[r] * rb[c] + ra[3 + r] * rb[3 + c] + ra[6 + r] * rb[6 + c];
-        tr[r] = ra[r] * d[0] + ra[3 + r] * d[1] + ra[6 + r] * d[2];
-        s.tr[r] = tr[r];
-      }
-      const double ri = A.st[16 * A.n + s.i], rj = A.st[16 * A.n + s.j];
-      if (PREC == 0) {
-        const double S = ri + rj + sqrtf(tr[0] * tr[0] + tr[1] * tr[1] + tr[2] * tr[2]);
-        s.Ed = S * ERR_REL32;
-        s.Elb = s.Ed;
-        // FP32 A-frame data stay valid; B moves
-        s.frmB = -1;
-      } else {
-        const double S = ri + rj + sqrt(s.XA[0] * s.XA[0] + s.XA[1] * s.XA[1] + s.XA[2] * s.XA[2]) +
-                         sqrt(s.XB[0] * s.XB[0] + s.XB[1] * s.XB[1] + s.XB[2] * s.XB[2]);
-        s.Ed = 0.0;
-        s.Elb = S * ERR_REL64_LB;
-        s.frmA = -1;
-        s.frmB = -1;
-      }
-      s.found = 0;
-      s.nac = 0;
-      s.bound = dbits(OpsD::inf());
     }
     __syncthreads();
   }
@@ -1211,6 +1223,7 @@ struct Cta {
       if (extra > 0.0) {
         s.nil = 0;
         s.ilover = 0;
+        s.ilthr = double(th0) + s.Ed;
       }
       s.ilcol = extra > 0.0 ? 1 : 0;
     }
