@@ -1871,13 +1871,13 @@ __global__ void __launch_bounds__(Cfg<PREC>::NT, Cfg<PREC>::MINB) pair_kernel(Pa
       int32_t ta = -1, tb = -1;
       if (ok && s.nA > 0 && s.nB > 0) {
         ++evals;
-        c.pose_grid(A.K);
         motion_bound();
-        if (c.template eval<true, true, false>(s.ts, k, 0, s.delta)) {
+        if (c.template eval<true, true, false>(s.ts, k, -1, s.delta)) {
           status = 1;
           ta = int32_t(s.best_key >> 32);
           tb = int32_t(s.best_key & 0xffffffffu);
         } else {
+          c.pose_grid(A.K);  // the sample times' poses, only when the search runs
           status = search(evals, bis, tc, ta, tb);
         }
       }
@@ -1892,15 +1892,15 @@ __global__ void __launch_bounds__(Cfg<PREC>::NT, Cfg<PREC>::MINB) pair_kernel(Pa
       int32_t ta = -1, tb = -1;
       if (ok && s.nA > 0 && s.nB > 0) {
         ++evals;
-        c.pose_grid(A.K);
         motion_bound();
-        c.template eval<false, true, true>(s.ts, k, 0, s.delta);
+        c.template eval<false, true, true>(s.ts, k, -1, s.delta);
         write_narrow();
         if (s.best_key != ~0ull && OpsD::sqrt(s.best_d2) <= s.eps) {
           status = 1;
           ta = int32_t(s.best_key >> 32);
           tb = int32_t(s.best_key & 0xffffffffu);
         } else {
+          c.pose_grid(A.K);  // the sample times' poses, only when the search runs
           status = search(evals, bis, tc, ta, tb);
         }
       } else {
