@@ -319,9 +319,11 @@ def gpu_arm(args, rank, world, local):
     ctx32.close()
     del sc, flush
     torch.cuda.empty_cache()
-    if rank == 0 and not args.no_lts:
+    # the further legs (not part of the timed step) run on a single GPU only,
+    # so that a multi-GPU run does not hold its GPUs for them
+    if world == 1 and not args.no_lts:
         res["lts"] = lts_legs(args, dem, W, dev)
-    if rank == 0 and not args.no_narrowing:
+    if world == 1 and not args.no_narrowing:
         res["narrowing"] = narrowing_leg(args, dem, W, dev)
     return res
 
