@@ -150,7 +150,10 @@ struct __align__(128) Smem {
   int64_t i, j, offA, offB;
   int nA, nB, ngp, gpnext, found, resA, resB, frmA, frmB, bad, abort, nac, ngrid;
   int wcnt[NW];
-  unsigned long long il[ILCAP];       // pair-interval candidates (a << 32 | b, within the particles)
+  // pair-interval candidates: (dq << 48) | (a << 24) | b, a and b within the
+  // particles (< 2^24), dq the top 16 bits of a float not above the pair's
+  // binary64 distance at the pair start (a lower bound, for the narrowing)
+  unsigned long long il[ILCAP];
   int nil, ilover, ilcol;
   double ilthr;                       // distance threshold of the list (eps + delta + 2E)
   double delta;                       // bound on the change of any distance over the interval
@@ -862,8 +865,16 @@ struct Cta {
           if (col) {
             const int pos = base + __popc(m & lanemask_lt());
             const int ag = ta * TT + a, bg = tb * TT + b;
+            // lower bound of the binary64 distance (FP32: d32 - 2E, rounded
+            // down), truncated to 16 bits of its float pattern (rounds down)
+            float dlb;
+            if constexpr (PREC == 0)
+              dlb = __fsub_rd(float(d), 2.0f * float(s.Ed));
+            else
+              dlb = __double2float_rd(double(d));
+            const unsigned long long dq = __float_as_uint(dlb > 0.0f ? dlb : 0.0f) >> 16;
             if (pos < ILCAP)
-              s.il[pos] = (static_cast<unsigned long long>(ag) << 32) | static_cast<uint32_t>(bg);
+              s.il[pos] = (dq << 48) | (static_cast<unsigned long long>(ag) << 24) | static_cast<uint32_t>(bg);
             else
               s.ilover = 1;
           }
@@ -1372,7 +1383,7 @@ struct Cta {
       const int k = r0 + lane;
       const bool have = k < n;
       const unsigned long long ent = have ? s.il[k] : 0ull;
-      const int ag = int(ent >> 32), bg = int(ent & 0xffffffffu);
+      const int ag = int((ent >> 24) & 0xffffffu), bg = int(ent & 0xffffffu);
       T d = O::inf();
       if (have) {
         V X[3], Y[3];
@@ -1568,6 +1579,35 @@ struct Cta {
     double te = O::add(ts, T);
     bool found = false;
     iters = 0;
+    // Visit the listed triangle pairs nearest first: a pair whose distance
+    // at ts is d cannot meet (distance <= eps) before ts + (d - eps) / rate,
+    // rate = the motion bound per unit time; once that exceeds the earliest
+    // candidate time found so far (shared, atomic), the pair is skipped --
+    // the paper's unfolding constrained by a global contact time.
+    const bool useL0 = s.ilover == 0;
+    if (useL0) {
+      const int n = s.nil;
+      int n2 = 1;
+      while (n2 < n) n2 <<= 1;
+      for (int q = n + tid; q < n2; q += NT) s.il[q] = ~0ull;
+      __syncthreads();
+      for (int k = 2; k <= n2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          for (int q = tid; q < n2; q += NT) {
+            const int l = q ^ j;
+            if (l > q) {
+              const bool up = (q & k) == 0;
+              const unsigned long long kq = s.il[q], kl = s.il[l];
+              if ((kq > kl) == up) {
+                s.il[q] = kl;
+                s.il[l] = kq;
+              }
+            }
+          }
+          __syncthreads();
+        }
+    }
+    const double rate = s.delta / T;
     for (;;) {
       const double tm = O::add(ts, O::mul(0.5, O::sub(te, ts)));
       __syncthreads();
@@ -1577,28 +1617,36 @@ struct Cta {
                    s.gX[1 + which][side]);
       }
       __syncthreads();
-      const bool useL = s.ilover == 0;
+      const bool useL = useL0;
       const int64_t cnt = useL ? (int64_t)s.nil : (int64_t)s.nA * s.nB;
+      if (tid == 0) s.bound = okey(O::inf());  // earliest candidate time so far
+      __syncthreads();
       double best = O::inf();
-      unsigned long long bk = ~0ull;
+      unsigned long long bk = ~0ull, evaluated = 0;
       for (int64_t q = tid; q < cnt; q += NT) {
         int a, b;
         if (useL) {
           const unsigned long long ent = s.il[q];
-          a = int(ent >> 32);
-          b = int(ent & 0xffffffffu);
+          a = int((ent >> 24) & 0xffffffu);
+          b = int(ent & 0xffffffu);
+          const double dlb = double(__uint_as_float(uint32_t(ent >> 48) << 16));
+          const double tlb = dlb > s.eps ? ts + (dlb - s.eps) / rate * (1.0 - 1e-9) : -O::inf();
+          // sorted by distance: this thread's later entries cannot be earlier
+          if (tlb > okey_value(*(volatile unsigned long long *)&s.bound)) break;
         } else {
           a = int(q / s.nB);
           b = int(q - (int64_t)a * s.nB);
         }
         const double t = narrow_pair(a, b, ts, te, tm);
+        ++evaluated;
+        if (t < O::inf()) atomicMin(&s.bound, okey(t));
         const unsigned long long key = (static_cast<unsigned long long>(a) << 32) | static_cast<uint32_t>(b);
         if (t < best || (t == best && key < bk)) {
           best = t;
           bk = key;
         }
       }
-      if (tid == 0) stat(ST_FP64, (unsigned long long)cnt);
+      stat(ST_FP64, evaluated);
       // block minimum of (time, key)
 #pragma unroll
       for (int o = 16; o; o >>= 1) {
