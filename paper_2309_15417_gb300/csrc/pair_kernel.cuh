@@ -155,6 +155,7 @@ struct __align__(128) Smem {
   // binary64 distance at the pair start (a lower bound, for the narrowing)
   unsigned long long il[ILCAP];
   int nil, ilover, ilcol;
+  uint32_t tmask[NW];                 // near tile pairs of a chunk, one ballot per warp
   double ilthr;                       // distance threshold of the list (eps + delta + 2E)
   double delta;                       // bound on the change of any distance over the interval
   double gR[GRID_MAX][2][9], gX[GRID_MAX][2][3];  // poses at the sample times
@@ -1241,15 +1242,31 @@ struct Cta {
     __syncthreads();
     bool stop = false;
     const bool multi = nta > 1 || ntb > 1;
-    for (int ta = 0; ta < nta && !stop; ++ta)
-      for (int tb = 0; tb < ntb && !stop; ++tb) {
-        if (multi && !__syncthreads_or(tid == 0 && tile_near(ta, tb, double(th0)))) continue;
-        if (!load_tiles(ta, tb)) return false;
-        frames(ta, tb);
-        if (tid == 0) stat(ST_TILES, 1);
-        scan_tiles<DECIDE, ARGMIN, CONTACTS>(ta, tb, false, th0, pk);
-        if (DECIDE && !ARGMIN && s.found) stop = true;
+    const int nq = nta * ntb;
+    // tile pairs q = ta * ntb + tb in chunks of NT: every thread tests one
+    // pair's spheres, the warps publish ballots, then the CTA scans the near
+    // ones in order
+    for (int c0 = 0; c0 < nq && !stop; c0 += NT) {
+      const int q = c0 + tid;
+      const bool near = q < nq && (!multi || tile_near(q / ntb, q - (q / ntb) * ntb, double(th0)));
+      const uint32_t m = __ballot_sync(0xffffffffu, near);
+      if (lane == 0) s.tmask[w] = m;
+      __syncthreads();
+      for (int wq = 0; wq < NW && !stop; ++wq) {
+        uint32_t mm = s.tmask[wq];
+        while (mm && !stop) {
+          const int qq = c0 + wq * 32 + __ffs(mm) - 1;
+          mm &= mm - 1;
+          const int ta = qq / ntb, tb = qq - ta * ntb;
+          if (!load_tiles(ta, tb)) return false;
+          frames(ta, tb);
+          if (tid == 0) stat(ST_TILES, 1);
+          scan_tiles<DECIDE, ARGMIN, CONTACTS>(ta, tb, false, th0, pk);
+          if (DECIDE && !ARGMIN && s.found) stop = true;
+        }
       }
+      __syncthreads();  // the next chunk rewrites s.tmask
+    }
     if (tid == 0) s.ilcol = 0;
     if (DECIDE && ARGMIN) {
       const bool f = *(volatile int *)&s.found != 0;
@@ -1263,18 +1280,40 @@ struct Cta {
       if (!complete && nta > 0 && ntb > 0) {
         if (tid == 0) s.bound = dbits(mh + 3.0 * s.Ed + s.Elb);  // inf if nothing seen
         __syncthreads();
-        // the nearest tile pair first (it tightens the bound), then the others
-        const int nq = nta * ntb, q0 = multi ? bound_by_tiles(nta, ntb) : 0;
-        for (int r = 0; r < nq; ++r) {
-          const int q = r == 0 ? q0 : (r <= q0 ? r - 1 : r);
-          const int ta = q / ntb, tb = q - ta * ntb;
-          if (multi && r > 0 &&
-              !__syncthreads_or(tid == 0 && tile_near(ta, tb, bitsd(*(volatile unsigned long long *)&s.bound))))
-            continue;
+        // the nearest tile pair first (it tightens the bound), then the
+        // others in chunks tested in parallel against the bound at the chunk's
+        // start; a selected tile pair is tested again against the bound as it
+        // is when its turn comes
+        const int q0 = multi ? bound_by_tiles(nta, ntb) : 0;
+        {
+          const int ta = q0 / ntb, tb = q0 - (q0 / ntb) * ntb;
           if (!load_tiles(ta, tb)) return false;
           frames(ta, tb);
           if (tid == 0) stat(ST_TILES, 1);
           scan_tiles<false, true, false>(ta, tb, true, th0, pk);
+        }
+        for (int c0 = 0; multi && c0 < nq; c0 += NT) {
+          const int q = c0 + tid;
+          const bool near = q < nq && q != q0 &&
+                            tile_near(q / ntb, q - (q / ntb) * ntb, bitsd(*(volatile unsigned long long *)&s.bound));
+          const uint32_t m = __ballot_sync(0xffffffffu, near);
+          if (lane == 0) s.tmask[w] = m;
+          __syncthreads();
+          for (int wq = 0; wq < NW; ++wq) {
+            uint32_t mm = s.tmask[wq];
+            while (mm) {
+              const int qq = c0 + wq * 32 + __ffs(mm) - 1;
+              mm &= mm - 1;
+              const int ta = qq / ntb, tb = qq - ta * ntb;
+              if (!__syncthreads_or(tid == 0 && tile_near(ta, tb, bitsd(*(volatile unsigned long long *)&s.bound))))
+                continue;
+              if (!load_tiles(ta, tb)) return false;
+              frames(ta, tb);
+              if (tid == 0) stat(ST_TILES, 1);
+              scan_tiles<false, true, false>(ta, tb, true, th0, pk);
+            }
+          }
+          __syncthreads();
         }
       }
       const double mh2 = block_min(double(mw));
