@@ -303,7 +303,7 @@ dem_status dem_lts_sweep(dem_ctx *ctx, const dem_particles *P, double *cur, doub
  * allocation could block or fail.  Same predicate, output and order as
  * dem_build_candidates.  Scratch lives in a fixed device array inside the
  * library, sized for at most DEM_NOALLOC_MAX_PARTICLES particles (about
- * 3.9 MB, held on every GPU that loads the library until the process exits);
+ * 5.3 MB, held on every GPU that loads the library until the process exits);
  * larger inputs return DEM_ERR_CAPACITY without launching anything.  No
  * cudaMalloc / cudaFree is called.  The first call on each device looks up
  * the array's device address (cudaGetSymbolAddress, with that device

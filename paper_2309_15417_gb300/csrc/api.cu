@@ -106,9 +106,10 @@ dem_status dem_create(const dem_config *cfg, dem_ctx **out) {
             alloc(c, &S.scan_part, dem::SCAN_PART_CAP) && alloc(c, &S.tmp, 8) && alloc(c, &S.sph, np) &&
             alloc(c, &S.cell, np) && alloc(c, &S.bucket_cnt, S.table_size) &&
             alloc(c, &S.bucket_start, S.table_size) && alloc(c, &S.bucket_cur, S.table_size) &&
-            alloc(c, &S.bucket_ids, np) && alloc(c, &S.pcnt, np) && alloc(c, &S.poff, np) &&
+            alloc(c, &S.bucket_ids, np) && alloc(c, &S.bucket_sph, np) && alloc(c, &S.bucket_sph32, np) &&
+            alloc(c, &S.bucket_cell, np) && alloc(c, &S.pcnt, np) && alloc(c, &S.poff, np) &&
             alloc(c, &S.rho_max, 1) && alloc(c, &S.static_ids, np) && alloc(c, &S.n_static, 1) &&
-            alloc(c, &S.spose, 12 * np) && alloc(c, &S.sbox, 6 * np) && alloc(c, &S.st_keys, 3 * nc) && alloc(c, &S.st_geom, 7 * nc) &&
+            alloc(c, &S.spose, 12 * np) && alloc(c, &S.sbox, 6 * np) && alloc(c, &S.sbox32, 6 * np) && alloc(c, &S.st_keys, 3 * nc) && alloc(c, &S.st_geom, 7 * nc) &&
             alloc(c, &S.st_count, 1) && alloc(c, &S.pc, nq) && alloc(c, &S.po, nq) && alloc(c, &S.pcur, nq) &&
             alloc(c, &S.sidx, nc) && alloc(c, &S.tile_sph, S.cap_tiles) && alloc(c, &S.tile_list, S.cap_tiles) && alloc(c, &S.lts_tmin, np) &&
             alloc(c, &S.lts_step, np) && alloc(c, &S.lts_tnew, np) && alloc(c, &S.lts_tglob, 1) &&

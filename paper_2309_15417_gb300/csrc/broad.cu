@@ -148,11 +148,64 @@ __global__ void k_count(int64_t n, const Sphere4 *sph, const uint8_t *is_static,
   }
 }
 
-__global__ void k_scatter(int64_t n, const int4 *cell, const int64_t *bstart, int32_t *bcur, int32_t *ids) {
+// moving particles into bucket order, with copies of their sphere and cell
+// (the pair test then reads a partner's data without first reading its index)
+__global__ void k_scatter(int64_t n, const int4 *cell, const Sphere4 *sph, const int64_t *bstart, int32_t *bcur,
+                          int32_t *ids, Sphere4 *bsph, float4 *bsph32, int4 *bcell) {
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-    const int b = cell[p].w;
-    if (b >= 0) ids[bstart[b] + atomicAdd(&bcur[b], 1)] = int32_t(p);
+    const int4 c = cell[p];
+    if (c.w < 0) continue;
+    const int64_t q = bstart[c.w] + atomicAdd(&bcur[c.w], 1);
+    const Sphere4 s = sph[p];
+    ids[q] = int32_t(p);
+    bsph[q] = s;
+    bsph32[q] = make_float4(float(s.x), float(s.y), float(s.z), float(s.w));
+    bcell[q] = c;
   }
+}
+
+// The widened box of every static particle, once: lo = min - eps_s and
+// hi = max + eps_s in binary64 (the oracle's operations), stored as bits in
+// place of the order keys, and rounded outwards to FP32 for the screening.
+__global__ void k_static_fin(int64_t n, const double *st, const int32_t *static_ids, const int32_t *n_static,
+                             unsigned long long *sbox, float *sbox32) {
+  const int ns = *n_static;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < ns; q += gridDim.x * blockDim.x) {
+    const double e = st[15 * n + static_ids[q]];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double lo = D::sub(okey_value(sbox[6 * (int64_t)q + k]), e);
+      const double hi = D::add(okey_value(sbox[6 * (int64_t)q + 3 + k]), e);
+      sbox[6 * (int64_t)q + k] = static_cast<unsigned long long>(__double_as_longlong(lo));
+      sbox[6 * (int64_t)q + 3 + k] = static_cast<unsigned long long>(__double_as_longlong(hi));
+      sbox32[6 * (int64_t)q + k] = __double2float_rd(lo);
+      sbox32[6 * (int64_t)q + 3 + k] = __double2float_ru(hi);
+    }
+  }
+}
+
+// The sphere predicate dd <= rr^2 (binary64, oracle order) decided in FP32
+// where that is certain.  From FP32 copies (each coordinate and radius
+// rounded once, u = 2^-24) the computed dd^ and rr^2^ satisfy, with M the
+// largest coordinate magnitude of the two centres,
+//   |dd^ - dd|     <= 11 M u (sqrt(dd^) + 3 M u) + 27 M^2 u^2 + 4 u dd^,
+//   |rr^2^ - rr^2| <= 8 u rr^2^,
+// and the binary64 values differ from the exact ones by far less (1e-14
+// relative covers them); B is twice the sum.  Returns 1 (pair), 0 (no pair)
+// or -1 (within B: the binary64 predicate decides).
+__device__ __forceinline__ int sphere_test32(float4 a, float4 b) {
+  const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  const float dd = dx * dx + dy * dy + dz * dz;
+  const float rr = a.w + b.w, r2 = rr * rr;
+  const float M = fmaxf(fmaxf(fmaxf(fabsf(a.x), fabsf(b.x)), fmaxf(fabsf(a.y), fabsf(b.y))),
+                        fmaxf(fabsf(a.z), fabsf(b.z)));
+  const float u = 5.9604644775390625e-08f;  // 2^-24
+  const float Mu = M * u;
+  const float B = 2.0f * (11.0f * Mu * (sqrtf(dd) + 3.0f * Mu) + 27.0f * Mu * Mu + 4.0f * u * dd + 8.0f * u * r2 +
+                          1e-14f * (dd + r2));
+  if (dd + B < r2) return 1;
+  if (dd - B > r2) return 0;
+  return -1;
 }
 
 // Space-time hose test (Check 2 of the paper's broad phase) of moving
@@ -170,7 +223,7 @@ __device__ __forceinline__ V3<double> hose_at(const double *cur, const double *o
                     D::add(s[2 * n + p], D::mul(v.z, h))};
 }
 
-__device__ bool hose_meet(const double *cur, const double *old, int64_t n, int64_t i, int64_t j) {
+__device__ __noinline__ bool hose_meet(const double *cur, const double *old, int64_t n, int64_t i, int64_t j) {
   using G = Geo<OpsD>;
   const double ti = cur[13 * n + i], tj = cur[13 * n + j];
   const double ts = ti < tj ? ti : tj, t2 = ti < tj ? tj : ti;
@@ -202,10 +255,12 @@ __device__ bool hose_meet(const double *cur, const double *old, int64_t n, int64
   return false;
 }
 
-// One warp per moving particle i: lane c < 27 scans neighbour cell c, then
-// the lanes share the static boxes; counts are combined with warp prefix
-// sums.  WRITE: the partners are written at the particle's offset and sorted
-// by partner index (bitonic in registers for up to 32).
+// One warp per moving particle i, taken in bucket order (spatially coherent:
+// consecutive warps share neighbour buckets in cache): lane c < 27 scans
+// neighbour cell c, then the lanes share the static boxes; counts are
+// combined with warp prefix sums.  WRITE: the partners are written at the
+// particle's offset and sorted by partner index (bitonic in registers for up
+// to 32).
 __device__ __forceinline__ int warp_incl_sum(int v, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -216,8 +271,9 @@ __device__ __forceinline__ int warp_incl_sum(int v, int lane) {
 }
 
 template <bool WRITE>
-__global__ void k_pairs(int64_t n, const double *st, const Sphere4 *sph, const int4 *cell,
-                        const uint8_t *is_static, const int32_t *bcnt, const int64_t *bstart, const int32_t *ids,
+__global__ void __launch_bounds__(256, 6) k_pairs(int64_t n, const double *st, const Sphere4 *bsph,
+                                                  const float4 *bsph32, const int4 *bcell, const float *sbox32,
+                        const int32_t *bcnt, const int64_t *bstart, const int32_t *ids,
                         uint32_t mask, const int32_t *static_ids, const int32_t *n_static,
                         const unsigned long long *sbox, const double *hose_old, int64_t *pcnt,
                         const int64_t *poff, int32_t *pairs, int64_t cap, const int64_t *n_pairs, uint32_t *err) {
@@ -225,13 +281,12 @@ __global__ void k_pairs(int64_t n, const double *st, const Sphere4 *sph, const i
   const int lane = threadIdx.x & 31;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int ns = *n_static;
-  for (int64_t i = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; i < n; i += nwarp) {
-    if (is_static && is_static[i]) {  // a static particle is never the first member
-      if (!WRITE && lane == 0) pcnt[i] = 0;
-      continue;
-    }
-    const Sphere4 si = sph[i];
-    const int4 ci = cell[i];
+  const int64_t nm = n - ns;  // moving particles, all in bucket order
+  for (int64_t r = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; r < nm; r += nwarp) {
+    const int64_t i = ids[r];
+    const Sphere4 si = bsph[r];
+    const float4 si32 = bsph32[r];
+    const int4 ci = bcell[r];
     const int cx = ci.x + (lane % 3) - 1, cy = ci.y + ((lane / 3) % 3) - 1, cz = ci.z + (lane / 9) - 1;
     int64_t b0 = 0, b1 = 0;
     if (lane < 27) {
@@ -239,35 +294,58 @@ __global__ void k_pairs(int64_t n, const double *st, const Sphere4 *sph, const i
       b0 = bstart[b];
       b1 = b0 + bcnt[b];
     }
-    // moving partner j > i (the binary64 sphere predicate, oracle order)
-    auto is_pair = [&](int32_t j) {
+    // moving partner j > i at bucket position q (the binary64 sphere
+    // predicate, oracle order)
+    auto is_pair = [&](int64_t q, int32_t j) {
       if (j <= i) return false;
-      const int4 cj = cell[j];
+      // both loads issued together (q is in bounds either way)
+      const int4 cj = bcell[q];
+      const float4 sj32 = bsph32[q];
       if (cj.x != cx || cj.y != cy || cj.z != cz) return false;  // other cell, same bucket
-      const Sphere4 sj = sph[j];
-      const double ddx = D::sub(si.x, sj.x), ddy = D::sub(si.y, sj.y), ddz = D::sub(si.z, sj.z);
-      const double dd = D::add(D::add(D::mul(ddx, ddx), D::mul(ddy, ddy)), D::mul(ddz, ddz));
-      const double rr = D::add(si.w, sj.w);
-      if (!(dd <= D::mul(rr, rr))) return false;
+      const int t32 = sphere_test32(si32, sj32);
+      if (t32 == 0) return false;
+      if (t32 < 0) {
+        const Sphere4 sj = bsph[q];
+        const double ddx = D::sub(si.x, sj.x), ddy = D::sub(si.y, sj.y), ddz = D::sub(si.z, sj.z);
+        const double dd = D::add(D::add(D::mul(ddx, ddx), D::mul(ddy, ddy)), D::mul(ddz, ddz));
+        const double rr = D::add(si.w, sj.w);
+        if (!(dd <= D::mul(rr, rr))) return false;
+      }
       return hose_old == nullptr || hose_meet(st, hose_old, n, i, j);
     };
-    // static partner number q: the swept sphere meets the widened box
+    // static partner number q: the swept sphere meets the widened box.
+    // FP32 screen first: the box rounded outwards contains the binary64 box,
+    // and the FP32 rounding of the centre and of the few operations stays
+    // below 1e-6 (M + rho) (M the largest magnitude involved), far inside
+    // the margin 1e-4 (M + rho); a sphere that clears the FP32 box by more
+    // than the margin clears the binary64 box.
     auto meets_box = [&](int q) {
-      const int64_t sp = static_ids[q];
-      const double e = st[15 * n + sp];
+      {
+        const float *b32 = sbox32 + 6 * (int64_t)q;
+        const float c[3] = {si32.x, si32.y, si32.z};
+        float gg = 0.f, M = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float lo = b32[k], hi = b32[3 + k];
+          const float gk = c[k] < lo ? lo - c[k] : (c[k] > hi ? c[k] - hi : 0.f);
+          gg += gk * gk;
+          M = fmaxf(M, fmaxf(fabsf(c[k]), fmaxf(fabsf(lo), fabsf(hi))));
+        }
+        if (sqrtf(gg) > si32.w + 1e-4f * (M + si32.w)) return false;
+      }
       const double m[3] = {si.x, si.y, si.z};
       double g[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const double lo = D::sub(okey_value(sbox[6 * (int64_t)q + k]), e);
-        const double hi = D::add(okey_value(sbox[6 * (int64_t)q + 3 + k]), e);
+        const double lo = __longlong_as_double(static_cast<long long>(sbox[6 * (int64_t)q + k]));
+        const double hi = __longlong_as_double(static_cast<long long>(sbox[6 * (int64_t)q + 3 + k]));
         g[k] = m[k] < lo ? D::sub(lo, m[k]) : (m[k] > hi ? D::sub(m[k], hi) : 0.0);
       }
       const double gg = D::add(D::add(D::mul(g[0], g[0]), D::mul(g[1], g[1])), D::mul(g[2], g[2]));
       return gg <= D::mul(si.w, si.w);
     };
     int c = 0, cs = 0;
-    for (int64_t q = b0; q < b1; ++q) c += is_pair(ids[q]) ? 1 : 0;
+    for (int64_t q = b0; q < b1; ++q) c += is_pair(q, ids[q]) ? 1 : 0;
     for (int q = lane; q < ns; q += 32) cs += meets_box(q) ? 1 : 0;
     const int inc = warp_incl_sum(c, lane), incs = warp_incl_sum(cs, lane);
     const int tgrid = __shfl_sync(0xffffffffu, inc, 31);
@@ -286,7 +364,7 @@ __global__ void k_pairs(int64_t n, const double *st, const Sphere4 *sph, const i
     int64_t pos = o + inc - c;
     for (int64_t q = b0; q < b1; ++q) {
       const int32_t j = ids[q];
-      if (is_pair(j)) put(pos++, j);
+      if (is_pair(q, j)) put(pos++, j);
     }
     pos = o + tgrid + incs - cs;
     for (int q = lane; q < ns; q += 32)
@@ -337,17 +415,23 @@ cudaError_t launch_broad(const dem_particles &P, int32_t *pairs, int64_t cap, in
   if (P.is_static) {
     k_static_box<<<304, tb, 0, s>>>(n, P.tri_off, reinterpret_cast<const float4 *>(P.tris), P.n_tris,
                                      S.static_ids, S.n_static, S.spose, S.sbox, S.err);
-    S.launches += 1;
+    k_static_fin<<<grid, tb, 0, s>>>(n, P.state, S.static_ids, S.n_static, S.sbox, S.sbox32);
+    S.launches += 2;
   }
   k_count<<<grid, tb, 0, s>>>(n, S.sph, P.is_static, S.rho_max, mask, S.cell, S.bucket_cnt);
   S.launches += 1 + scan_exclusive_i32_to_i64(S.bucket_cnt, S.bucket_start, S.table_size, S.scan_part, s);
-  k_scatter<<<grid, tb, 0, s>>>(n, S.cell, S.bucket_start, S.bucket_cur, S.bucket_ids);
+  k_scatter<<<grid, tb, 0, s>>>(n, S.cell, S.sph, S.bucket_start, S.bucket_cur, S.bucket_ids, S.bucket_sph,
+                                S.bucket_sph32, S.bucket_cell);
+  // static particles never start a pair: their counts stay 0
+  if ((e = cudaMemsetAsync(S.pcnt, 0, sizeof(int64_t) * n, s)) != cudaSuccess) return e;
   const unsigned wgrid = (unsigned)((n + 7) / 8);  // one warp per particle
-  k_pairs<false><<<wgrid, tb, 0, s>>>(n, P.state, S.sph, S.cell, P.is_static, S.bucket_cnt, S.bucket_start,
+  k_pairs<false><<<wgrid, tb, 0, s>>>(n, P.state, S.bucket_sph, S.bucket_sph32, S.bucket_cell, S.sbox32,
+                                      S.bucket_cnt, S.bucket_start,
                                       S.bucket_ids, mask, S.static_ids, S.n_static, S.sbox, hose_old, S.pcnt,
                                       nullptr, nullptr, 0, nullptr, S.err);
   S.launches += 2 + scan_exclusive_i64(S.pcnt, S.poff, n, n_pairs, S.scan_part, s);
-  k_pairs<true><<<wgrid, tb, 0, s>>>(n, P.state, S.sph, S.cell, P.is_static, S.bucket_cnt, S.bucket_start,
+  k_pairs<true><<<wgrid, tb, 0, s>>>(n, P.state, S.bucket_sph, S.bucket_sph32, S.bucket_cell, S.sbox32,
+                                     S.bucket_cnt, S.bucket_start,
                                      S.bucket_ids, mask, S.static_ids, S.n_static, S.sbox, hose_old, nullptr,
                                      S.poff, pairs, cap, n_pairs, S.err);
   S.launches += 1;

@@ -54,14 +54,19 @@ struct Scratch {
   int32_t *bucket_cnt;            // [table]
   int64_t *bucket_start;          // [table]
   int32_t *bucket_cur;            // [table]
-  int32_t *bucket_ids;            // [n]
+  int32_t *bucket_ids;            // [n] moving particles in bucket order
+  Sphere4 *bucket_sph;            // [n] their swept spheres, same order
+  float4 *bucket_sph32;           // [n] the same spheres rounded to FP32
+  int4 *bucket_cell;              // [n] their cells, same order
   int64_t *pcnt;                  // [n] candidates per particle
   int64_t *poff;                  // [n]
   unsigned long long *rho_max;    // [1] (bits of a non-negative double)
   int32_t *static_ids;            // [n] static particles, in order of discovery
   int32_t *n_static;              // [1]
   double *spose;                  // [n][12] rotation (row-major) and centre of each static at t_cur
-  unsigned long long *sbox;       // [n][6] order keys of its world-vertex extremes (min xyz, max xyz)
+  unsigned long long *sbox;       // [n][6] order keys of its world-vertex extremes (min xyz, max xyz),
+                                  // then the bits of the widened box (lo xyz, hi xyz, binary64)
+  float *sbox32;                  // [n][6] the widened box rounded outwards to FP32
   // narrow phase
   int64_t cap_pairs;
   int64_t cap_contacts;

@@ -10,7 +10,7 @@
 // moment the library is loaded until the process exits (on every GPU that
 // loads the library).
 //
-// The array is sized for DEM_NOALLOC_MAX_PARTICLES particles (about 3.9 MB).
+// The array is sized for DEM_NOALLOC_MAX_PARTICLES particles (about 5.3 MB).
 // Larger inputs are rejected with DEM_ERR_CAPACITY before anything is
 // launched.  The first call on each device looks the array's device address
 // up with cudaGetSymbolAddress (with that device current); make that first
@@ -41,14 +41,18 @@ constexpr size_t OFF_BCNT = align256(OFF_CELL + sizeof(int4) * NA_MAX);
 constexpr size_t OFF_BSTART = align256(OFF_BCNT + sizeof(int32_t) * NA_TABLE);
 constexpr size_t OFF_BCUR = align256(OFF_BSTART + sizeof(int64_t) * NA_TABLE);
 constexpr size_t OFF_IDS = align256(OFF_BCUR + sizeof(int32_t) * NA_TABLE);
-constexpr size_t OFF_PCNT = align256(OFF_IDS + sizeof(int32_t) * NA_MAX);
+constexpr size_t OFF_BSPH = align256(OFF_IDS + sizeof(int32_t) * NA_MAX);
+constexpr size_t OFF_BSPH32 = align256(OFF_BSPH + sizeof(Sphere4) * NA_MAX);
+constexpr size_t OFF_BCELL = align256(OFF_BSPH32 + sizeof(float4) * NA_MAX);
+constexpr size_t OFF_PCNT = align256(OFF_BCELL + sizeof(int4) * NA_MAX);
 constexpr size_t OFF_POFF = align256(OFF_PCNT + sizeof(int64_t) * NA_MAX);
 constexpr size_t OFF_RHO = align256(OFF_POFF + sizeof(int64_t) * NA_MAX);
 constexpr size_t OFF_SIDS = align256(OFF_RHO + sizeof(unsigned long long));
 constexpr size_t OFF_NST = align256(OFF_SIDS + sizeof(int32_t) * NA_MAX);
 constexpr size_t OFF_SPOSE = align256(OFF_NST + sizeof(int32_t));
 constexpr size_t OFF_SBOX = align256(OFF_SPOSE + sizeof(double) * 12 * NA_MAX);
-constexpr size_t NA_BYTES = align256(OFF_SBOX + sizeof(unsigned long long) * 6 * NA_MAX);
+constexpr size_t OFF_SBOX32 = align256(OFF_SBOX + sizeof(unsigned long long) * 6 * NA_MAX);
+constexpr size_t NA_BYTES = align256(OFF_SBOX32 + sizeof(float) * 6 * NA_MAX);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
@@ -98,6 +102,9 @@ extern "C" dem_status dem_build_candidates_noalloc(const dem_particles *P, int32
   S.bucket_start = reinterpret_cast<int64_t *>(b + OFF_BSTART);
   S.bucket_cur = reinterpret_cast<int32_t *>(b + OFF_BCUR);
   S.bucket_ids = reinterpret_cast<int32_t *>(b + OFF_IDS);
+  S.bucket_sph = reinterpret_cast<Sphere4 *>(b + OFF_BSPH);
+  S.bucket_sph32 = reinterpret_cast<float4 *>(b + OFF_BSPH32);
+  S.bucket_cell = reinterpret_cast<int4 *>(b + OFF_BCELL);
   S.pcnt = reinterpret_cast<int64_t *>(b + OFF_PCNT);
   S.poff = reinterpret_cast<int64_t *>(b + OFF_POFF);
   S.rho_max = reinterpret_cast<unsigned long long *>(b + OFF_RHO);
@@ -105,6 +112,7 @@ extern "C" dem_status dem_build_candidates_noalloc(const dem_particles *P, int32
   S.n_static = reinterpret_cast<int32_t *>(b + OFF_NST);
   S.spose = reinterpret_cast<double *>(b + OFF_SPOSE);
   S.sbox = reinterpret_cast<unsigned long long *>(b + OFF_SBOX);
+  S.sbox32 = reinterpret_cast<float *>(b + OFF_SBOX32);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // the error word keeps the previous call's value: clear it
   if (cudaMemsetAsync(S.err, 0, sizeof(uint32_t), s) != cudaSuccess) return DEM_ERR_CUDA;
