@@ -111,7 +111,7 @@ dem_status dem_create(const dem_config *cfg, dem_ctx **out) {
             alloc(c, &S.rho_max, 1) && alloc(c, &S.static_ids, np) && alloc(c, &S.n_static, 1) &&
             alloc(c, &S.spose, 12 * np) && alloc(c, &S.sbox, 6 * np) && alloc(c, &S.sbox32, 6 * np) && alloc(c, &S.st_keys, 3 * nc) && alloc(c, &S.st_geom, 7 * nc) &&
             alloc(c, &S.st_count, 1) && alloc(c, &S.pc, nq) && alloc(c, &S.po, nq) && alloc(c, &S.pcur, nq) &&
-            alloc(c, &S.sidx, nc) && alloc(c, &S.tile_sph, S.cap_tiles) && alloc(c, &S.tile_list, S.cap_tiles) && alloc(c, &S.lts_tmin, np) &&
+            alloc(c, &S.sidx, nc) && alloc(c, &S.tile_sph, S.cap_tiles) && alloc(c, &S.tile_box, 2 * S.cap_tiles) && alloc(c, &S.tile_list, S.cap_tiles) && alloc(c, &S.lts_tmin, np) &&
             alloc(c, &S.lts_step, np) && alloc(c, &S.lts_tnew, np) && alloc(c, &S.lts_tglob, 1) &&
             alloc(c, &S.lts_touch, np);
   if (!ok) {

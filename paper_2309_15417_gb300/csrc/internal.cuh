@@ -83,6 +83,7 @@ struct Scratch {
   int64_t cap_triangles;
   int64_t cap_tiles;
   float4 *tile_sph;               // [cap_tiles]
+  float4 *tile_box;               // [cap_tiles][2] body-frame box (lo xyz, hi xyz) of the tile's vertices
   int2 *tile_list;                // [cap_tiles] (particle, tile) entries to compute
   // local time stepping: per-cluster order keys (indexed by cluster id)
   unsigned long long *lts_tmin;   // [n] earliest t_cur of the cluster

@@ -112,6 +112,7 @@ struct PairArgs {
   double tol;
   // bounding spheres of the tiles of particles with more than one tile
   const float4 *tile_sph;
+  const float4 *tile_box;
   int64_t cap_tiles;
   // bookkeeping
   unsigned int *work;
@@ -333,12 +334,66 @@ struct Cta {
     const T dx = ca[0] - cb[0], dy = ca[1] - cb[1], dz = ca[2] - cb[2];
     return O::sqrt(dx * dx + dy * dy + dz * dz);
   }
-  // false only if no triangle pair of tiles (ta, tb) can come within thr
-  // (the margin 2 Elb covers the rounding of the sphere test, as for groups)
+  // distance from point c (body frame of the particle) to its tile k's box
+  __device__ double box_gap(bool isA, int k, const double c[3]) const {
+    const int64_t p = isA ? s.i : s.j, off = isA ? s.offA : s.offB;
+    const int64_t slot = off / TT + p + k;
+    const float4 lo = A.tile_box[2 * slot], hi = A.tile_box[2 * slot + 1];
+    const double l[3] = {lo.x, lo.y, lo.z}, h[3] = {hi.x, hi.y, hi.z};
+    double gg = 0.0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const double g = c[q] < l[q] ? l[q] - c[q] : (c[q] > h[q] ? c[q] - h[q] : 0.0);
+      gg += g * g;
+    }
+    return sqrt(gg);
+  }
+  // the evaluation-frame point c in the body frame of A (isA) or B
+  __device__ void to_body(bool isA, const T c[3], double out[3]) const {
+    if constexpr (PREC == 0) {
+      if (isA) {  // A's body frame is the evaluation frame
+        out[0] = c[0];
+        out[1] = c[1];
+        out[2] = c[2];
+      } else {  // B's vertices are Rr v + tr: v = Rr^T (c - tr)
+        const float *R = s.Rr;
+        const float p0 = c[0] - s.tr[0], p1 = c[1] - s.tr[1], p2 = c[2] - s.tr[2];
+        out[0] = R[0] * p0 + R[3] * p1 + R[6] * p2;
+        out[1] = R[1] * p0 + R[4] * p1 + R[7] * p2;
+        out[2] = R[2] * p0 + R[5] * p1 + R[8] * p2;
+      }
+    } else {  // world frame: R^T (c - X)
+      const double *R = isA ? s.RA : s.RB, *X = isA ? s.XA : s.XB;
+      const double p0 = c[0] - X[0], p1 = c[1] - X[1], p2 = c[2] - X[2];
+      out[0] = R[0] * p0 + R[3] * p1 + R[6] * p2;
+      out[1] = R[1] * p0 + R[4] * p1 + R[7] * p2;
+      out[2] = R[2] * p0 + R[5] * p1 + R[8] * p2;
+    }
+  }
+  // false only if no triangle pair of tiles (ta, tb) can come within thr.
+  // Lower bounds: the distance of the two tile spheres, and for a tile of a
+  // multi-tile particle the distance from the other tile's sphere to its
+  // body-frame box (a floor's flat tiles are far tighter as boxes).  The
+  // margin 2 Elb covers the rounding of the sphere test (as for groups) and
+  // of moving a centre between frames.
   __device__ bool tile_near(int ta, int tb, double thr) const {
-    T ra, rb;
-    const T g = tile_gap(ta, tb, ra, rb);
-    return double(g - ra - rb) <= thr + 2.0 * s.Elb;
+    T ca[3], cb[3], ra, rb;
+    tile_sphere(true, ta, ca, ra);
+    tile_sphere(false, tb, cb, rb);
+    const T dx = ca[0] - cb[0], dy = ca[1] - cb[1], dz = ca[2] - cb[2];
+    double lb = double(O::sqrt(dx * dx + dy * dy + dz * dz) - ra - rb);
+    const int64_t slotA = s.offA / TT + s.i + ta, slotB = s.offB / TT + s.j + tb;
+    if (s.nB > TT && slotB < A.cap_tiles) {
+      double q[3];
+      to_body(false, ca, q);
+      lb = fmax(lb, box_gap(false, tb, q) - double(ra));
+    }
+    if (s.nA > TT && slotA < A.cap_tiles) {
+      double q[3];
+      to_body(true, cb, q);
+      lb = fmax(lb, box_gap(true, ta, q) - double(rb));
+    }
+    return lb <= thr + 2.0 * s.Elb;
   }
   // Lower the shared bound with the upper bound every tile pair gives on the
   // smallest triangle-pair distance (any point of one tile sphere is within

@@ -142,7 +142,8 @@ __global__ void k_tile_list(int64_t n, const int64_t *tri_off, int64_t n_tris, i
 // enlarged by 2^-20 relative (and 1e-18 absolute) so that it covers every
 // float32 vertex despite the rounding of its own computation.
 __global__ void k_tile_spheres(const int64_t *tri_off, const float4 *tris, int64_t n_tris, const int2 *list,
-                               const unsigned long long *count, float4 *tile_sph, int64_t cap_tiles) {
+                               const unsigned long long *count, float4 *tile_sph, float4 *tile_box,
+                               int64_t cap_tiles) {
   constexpr int TT = TILE_TRIS;
   const int lane = threadIdx.x & 31;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -181,7 +182,11 @@ __global__ void k_tile_spheres(const int64_t *tri_off, const float4 *tris, int64
         r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
       }
     r2 = seg_max(r2, 32);
-    if (lane == 0) tile_sph[slot] = make_float4(cx, cy, cz, sqrtf(r2) * (1.0f + 0x1p-20f) + 1e-18f);
+    if (lane == 0) {
+      tile_sph[slot] = make_float4(cx, cy, cz, sqrtf(r2) * (1.0f + 0x1p-20f) + 1e-18f);
+      tile_box[2 * slot] = make_float4(lo[0], lo[1], lo[2], 0.f);  // exact: extremes of float32 values
+      tile_box[2 * slot + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+    }
   }
 }
 
@@ -192,7 +197,7 @@ int prepare_tiles(const dem_particles &P, Scratch &S, cudaStream_t s) {
   const unsigned grid = (unsigned)((P.n + 255) / 256);
   k_tile_list<<<grid, 256, 0, s>>>(P.n, P.tri_off, P.n_tris, S.tile_list, S.cap_tiles, count, S.err);
   k_tile_spheres<<<1216, 256, 0, s>>>(P.tri_off, reinterpret_cast<const float4 *>(P.tris), P.n_tris, S.tile_list,
-                                      count, S.tile_sph, S.cap_tiles);
+                                      count, S.tile_sph, S.tile_box, S.cap_tiles);
   return 2;
 }
 
@@ -210,6 +215,7 @@ PairArgs make_args(const dem_particles &P, const int32_t *pairs, int64_t max_pai
   a.max_pairs = max_pairs;
   a.n_pairs = n_pairs;
   a.tile_sph = S.tile_sph;
+  a.tile_box = S.tile_box;
   a.cap_tiles = S.cap_tiles;
   a.work = S.work;
   a.err = S.err;
