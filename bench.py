@@ -305,6 +305,23 @@ def gpu_arm(args, rank, world, local):
         fp64 = {"value": c64 * k64 / t64, "unit": UNIT, "ms_per_step": t64 * 1e3 / k64,
                 "speedup_fp32_fixup_over_fp64": (checks_step * K / t_total) / (c64 * k64 / t64),
                 "results_identical": bool(same), "steps": k64}
+        if same:
+            # FP32 error of the contact list: the FP32+fixup run keeps the FP32
+            # distance and points of contacts outside the band; the FP64 run
+            # has the same contact keys with binary64 geometry (R = 1).  The
+            # points of (near-)parallel triangles are not unique, so a point
+            # difference can also be a different valid point.
+            nc = int(ctx32.n_contacts.item())
+            g32, g64 = ctx32.contact_geom[:nc], ctx64.contact_geom[:nc]
+            ed = (g32[:, 0] - g64[:, 0]).abs().cpu().numpy()
+            ep = torch.maximum((g32[:, 1:4] - g64[:, 1:4]).norm(dim=1),
+                               (g32[:, 4:7] - g64[:, 4:7]).norm(dim=1)).cpu().numpy()
+            if nc:
+                fp32_err["contact_distance"] = {"max_abs_over_R": float(ed.max()),
+                                                "p99_abs_over_R": float(np.percentile(ed, 99))}
+                fp32_err["contact_points"] = {"max_abs_over_R": float(ep.max()),
+                                              "p99_abs_over_R": float(np.percentile(ep, 99)),
+                                              "note": "largest of |pa32 - pa64|, |pb32 - pb64| per contact"}
         ctx64.close()
 
     # end to end through the public API from pinned host buffers
