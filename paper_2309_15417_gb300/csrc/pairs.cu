@@ -190,15 +190,18 @@ __global__ void k_tile_spheres(const int64_t *tri_off, const float4 *tris, int64
   }
 }
 
-int prepare_tiles(const dem_particles &P, Scratch &S, cudaStream_t s) {
-  if (P.n <= 0) return 0;
+// returns the error of the first call that failed
+cudaError_t prepare_tiles(const dem_particles &P, Scratch &S, cudaStream_t s) {
+  if (P.n <= 0) return cudaSuccess;
   unsigned long long *count = reinterpret_cast<unsigned long long *>(S.tmp + 4);
-  if (cudaMemsetAsync(count, 0, sizeof(unsigned long long), s) != cudaSuccess) return 0;
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)((P.n + 255) / 256);
   k_tile_list<<<grid, 256, 0, s>>>(P.n, P.tri_off, P.n_tris, S.tile_list, S.cap_tiles, count, S.err);
   k_tile_spheres<<<1216, 256, 0, s>>>(P.tri_off, reinterpret_cast<const float4 *>(P.tris), P.n_tris, S.tile_list,
                                       count, S.tile_sph, S.tile_box, S.cap_tiles);
-  return 2;
+  S.launches += 2;
+  return cudaGetLastError();
 }
 
 
@@ -238,7 +241,7 @@ cudaError_t finish_narrow(int prec, PairArgs &a, const dem_particles &P, const i
   if (max_pairs > 0) {
     if ((e = cudaMemsetAsync(S.pc, 0, sizeof(int64_t) * max_pairs, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(S.pcur, 0, sizeof(int32_t) * max_pairs, s)) != cudaSuccess) return e;
-    S.launches += prepare_tiles(P, S, s);
+    if ((e = prepare_tiles(P, S, s)) != cudaSuccess) return e;
     if (fused)
       e = prec == 0 ? launch_pairs<0, MODE_BOTH>(a, num_sms, s) : launch_pairs<1, MODE_BOTH>(a, num_sms, s);
     else
@@ -320,7 +323,8 @@ cudaError_t launch_ctime(int prec, int method, const dem_particles &P, const int
   cudaError_t e;
   if ((e = cudaMemsetAsync(S.work, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
   if (max_pairs <= 0) return cudaSuccess;
-  S.launches += 1 + prepare_tiles(P, S, s);
+  if ((e = prepare_tiles(P, S, s)) != cudaSuccess) return e;
+  S.launches += 1;
   if (method == DEM_CTIME_NARROWING)
     return prec == 0 ? launch_pairs<0, MODE_NTIME>(a, num_sms, s) : launch_pairs<1, MODE_NTIME>(a, num_sms, s);
   return prec == 0 ? launch_pairs<0, MODE_CTIME>(a, num_sms, s) : launch_pairs<1, MODE_CTIME>(a, num_sms, s);
