@@ -140,7 +140,7 @@ class ClockSampler:
 # ------------------------------------------------------------------ GPU arm
 
 def _profile_traffic():
-    """DRAM bytes per launch of the collision-time kernel from the committed
+    """DRAM bytes per launch of the fused pair kernel from the committed
     ncu summary, if it was taken on the current kernel source."""
     try:
         txt = open(PROFILE_SUMMARY).read()

@@ -1656,6 +1656,37 @@ struct Cta {
       }
     return tab;
   }
+  // Lower bound on the distance at ts of triangles a (particle i) and b
+  // (particle j) from their bounding spheres (centroid, largest vertex
+  // distance) in A's frame, B's centre moved by the FP32 relative pose at ts
+  // (Rr, tr).  The FP32 errors of the pose, the centres and the radii are
+  // below 2^-20 S; the margin mg = 2^-14 S covers them many times over.
+  __device__ double tri_sphere_gap(int a, int b, float mg) const {
+    float c[2][3], r[2];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int64_t o = side == 0 ? s.offA + a : s.offB + b;
+      const float4 v0 = A.tris[o], v1 = A.tris[A.n_tris + o], v2 = A.tris[2 * A.n_tris + o];
+      const float cx = (v0.x + v1.x + v2.x) * (1.0f / 3.0f), cy = (v0.y + v1.y + v2.y) * (1.0f / 3.0f),
+                  cz = (v0.z + v1.z + v2.z) * (1.0f / 3.0f);
+      const float e0 = (v0.x - cx) * (v0.x - cx) + (v0.y - cy) * (v0.y - cy) + (v0.z - cz) * (v0.z - cz);
+      const float e1 = (v1.x - cx) * (v1.x - cx) + (v1.y - cy) * (v1.y - cy) + (v1.z - cz) * (v1.z - cz);
+      const float e2 = (v2.x - cx) * (v2.x - cx) + (v2.y - cy) * (v2.y - cy) + (v2.z - cz) * (v2.z - cz);
+      r[side] = sqrtf(fmaxf(e0, fmaxf(e1, e2)));
+      if (side == 0) {
+        c[0][0] = cx;
+        c[0][1] = cy;
+        c[0][2] = cz;
+      } else {
+        const float *R = s.Rr;
+        c[1][0] = fmaf(R[0], cx, fmaf(R[1], cy, fmaf(R[2], cz, s.tr[0])));
+        c[1][1] = fmaf(R[3], cx, fmaf(R[4], cy, fmaf(R[5], cz, s.tr[1])));
+        c[1][2] = fmaf(R[6], cx, fmaf(R[7], cy, fmaf(R[8], cz, s.tr[2])));
+      }
+    }
+    const float dx = c[0][0] - c[1][0], dy = c[0][1] - c[1][1], dz = c[0][2] - c[1][2];
+    return double(sqrtf(dx * dx + dy * dy + dz * dz)) - double(r[0]) - double(r[1]) - double(mg);
+  }
   // The narrowing loop after a false decision at ts.  The triangle pairs are
   // those of the pair-interval list collected at ts with the narrowing's
   // motion bound (all pairs if the list overflowed).  Returns the status and
@@ -1702,6 +1733,11 @@ struct Cta {
         }
     }
     const double rate = s.delta / T;
+    // after an overflow every triangle pair is visited, each first bounded by
+    // its bounding spheres at ts (the same rate argument as for the list)
+    const float mg = float(8.0 * ERR_REL32 *
+                           (A.st[16 * A.n + s.i] + A.st[16 * A.n + s.j] +
+                            double(sqrtf(s.tr[0] * s.tr[0] + s.tr[1] * s.tr[1] + s.tr[2] * s.tr[2]))));
     for (;;) {
       const double tm = O::add(ts, O::mul(0.5, O::sub(te, ts)));
       __syncthreads();
@@ -1730,6 +1766,11 @@ struct Cta {
         } else {
           a = int(q / s.nB);
           b = int(q - (int64_t)a * s.nB);
+          // every candidate of the pair lies in [ts, te]; none can precede the
+          // earliest time its spheres allow
+          const double dlb = tri_sphere_gap(a, b, mg);
+          const double tlb = dlb > s.eps ? ts + (dlb - s.eps) / rate * (1.0 - 1e-9) : -O::inf();
+          if (tlb > te || tlb > okey_value(*(volatile unsigned long long *)&s.bound)) continue;
         }
         const double t = narrow_pair(a, b, ts, te, tm);
         ++evaluated;
