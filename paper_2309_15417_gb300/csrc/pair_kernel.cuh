@@ -1687,6 +1687,25 @@ struct Cta {
     const float dx = c[0][0] - c[1][0], dy = c[0][1] - c[1][1], dz = c[0][2] - c[1][2];
     return double(sqrtf(dx * dx + dy * dy + dz * dz)) - double(r[0]) - double(r[1]) - double(mg);
   }
+  // The FP32 distance of triangles a, b at ts in A's frame (B moved by the
+  // FP32 relative pose, as in the tile scan) less 2E, rounded down: the same
+  // lower bound the pair-interval list keeps.
+  __device__ double tri_dist32_lb(int a, int b) const {
+    using GF = Geo<OpsF>;
+    V3<float> X[3], Y[3];
+    const float *R = s.Rr;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float4 f = A.tris[q * A.n_tris + s.offA + a], g = A.tris[q * A.n_tris + s.offB + b];
+      X[q] = V3<float>{f.x, f.y, f.z};
+      Y[q] = V3<float>{fmaf(R[0], g.x, fmaf(R[1], g.y, fmaf(R[2], g.z, s.tr[0]))),
+                       fmaf(R[3], g.x, fmaf(R[4], g.y, fmaf(R[5], g.z, s.tr[1]))),
+                       fmaf(R[6], g.x, fmaf(R[7], g.y, fmaf(R[8], g.z, s.tr[2])))};
+    }
+    V3<float> pa, pb;
+    const float d = OpsF::sqrt(GF::tri_dist2(X, Y, pa, pb));
+    return double(__fsub_rd(d, 2.0f * float(s.Ed)));
+  }
   // The narrowing loop after a false decision at ts.  The triangle pairs are
   // those of the pair-interval list collected at ts with the narrowing's
   // motion bound (all pairs if the list overflowed).  Returns the status and
@@ -1767,10 +1786,15 @@ struct Cta {
           a = int(q / s.nB);
           b = int(q - (int64_t)a * s.nB);
           // every candidate of the pair lies in [ts, te]; none can precede the
-          // earliest time its spheres allow
+          // earliest time its spheres allow, nor (FP32 mode) the earliest
+          // time its FP32 distance allows
+          const double thr = fmin(te, okey_value(*(volatile unsigned long long *)&s.bound));
           const double dlb = tri_sphere_gap(a, b, mg);
-          const double tlb = dlb > s.eps ? ts + (dlb - s.eps) / rate * (1.0 - 1e-9) : -O::inf();
-          if (tlb > te || tlb > okey_value(*(volatile unsigned long long *)&s.bound)) continue;
+          if (dlb > s.eps && ts + (dlb - s.eps) / rate * (1.0 - 1e-9) > thr) continue;
+          if constexpr (PREC == 0) {
+            const double d32 = tri_dist32_lb(a, b);
+            if (d32 > s.eps && ts + (d32 - s.eps) / rate * (1.0 - 1e-9) > thr) continue;
+          }
         }
         const double t = narrow_pair(a, b, ts, te, tm);
         ++evaluated;

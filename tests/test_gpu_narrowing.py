@@ -79,6 +79,18 @@ def test_narrowing_list_overflow(dem, prec):
         assert o["status"][0] == 2
 
 
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("seed", [0, 1])
+def test_narrowing_fast_rotating_packing(dem, seed, prec):
+    """v, w ~ N(0, 150): the narrowing's motion bound (~0.3) lets far more
+    triangle pairs into the pair-interval list than it holds, so the
+    iterations visit every triangle pair, pruned by bounding spheres and (FP32
+    mode) FP32 distances at ts."""
+    w = W.dense_packing(seed, nside=4, vsig=150.0, wsig=150.0)
+    o = _check(dem, w, oracle.broad_phase(w), prec)
+    assert (o["status"] == 2).sum() >= 3
+
+
 def test_detect_with_narrowing_equals_separate_calls(dem):
     w = W.small_icospheres(1)
     c1 = dem.Context(K=w.K, tol=w.tol, max_particles=w.n, max_pairs=4096, ctime_method=dem.DEM_CTIME_NARROWING)
