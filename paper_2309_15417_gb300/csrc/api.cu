@@ -30,6 +30,8 @@ dem_status cuda_fail(dem_ctx *c, cudaError_t e, const char *where) {
 
 template <class T>
 bool alloc(dem_ctx *c, T **p, size_t count) {
+  constexpr int max_allocs = int(sizeof(c->allocs) / sizeof(c->allocs[0]));
+  if (c->n_allocs >= max_allocs) return false;
   const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
   void *q = nullptr;
   if (cudaMalloc(&q, bytes) != cudaSuccess) return false;
