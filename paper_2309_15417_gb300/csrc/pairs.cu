@@ -1,7 +1,7 @@
 // pairs.cu -- host side of the pair kernel (launchers for the narrow phase,
 // collision times and the fused form), the contact sort and the tile
 // bounding spheres.  The kernel itself is in pair_kernel.cuh; its
-// instantiations are compiled in pairs_fp32.cu and pairs_fp64.cu.
+// instantiations are compiled in pairs_fp32_*.cu and pairs_fp64_*.cu.
 #include "pair_kernel.cuh"
 
 namespace dem {
