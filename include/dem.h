@@ -21,9 +21,13 @@
  *    returned immediately as DEM_ERR_ARG / DEM_ERR_CAPACITY; nothing is
  *    launched then.
  *  - Conditions found on the device (an output capacity exceeded, an index
- *    out of range, a bounded wait that ran out) set a sticky error word in the
- *    context.  dem_check() synchronises the stream, returns the first such
- *    condition as a status and clears it.  Kernels never trap.
+ *    out of range, a non-finite input, a bounded wait that ran out) set a
+ *    sticky error word in the context.  dem_check() synchronises the stream,
+ *    returns the most severe such condition as a status (index, non-finite,
+ *    capacity, timeout, in that order) and clears the word.  Kernels never
+ *    trap and never read out of bounds: a bad index skips its pair.
+ *  - Every call is wrapped in an NVTX range named after it (visible in
+ *    profilers; a no-op otherwise).
  *  - Counts that kernels produce are written to device int64 scalars, and the
  *    consuming calls read them on the device (`n_pairs` below), so a whole
  *    step runs without host round trips.
@@ -49,8 +53,15 @@ typedef enum {
   DEM_ERR_ARG = -1,       /* invalid argument (detected on the host) */
   DEM_ERR_CAPACITY = -2,  /* a size exceeds a capacity (host or device) */
   DEM_ERR_CUDA = -3,      /* a CUDA runtime call failed; see dem_last_error */
-  DEM_ERR_INDEX = -4,     /* a device kernel met an index out of range */
-  DEM_ERR_TIMEOUT = -5    /* a bounded device wait ran out */
+  DEM_ERR_NONFINITE = -4, /* a particle's state or a triangle vertex is NaN or infinite; the
+                             pairs and particles concerned are skipped, other outputs stay valid */
+  DEM_ERR_TIMEOUT = -5,   /* a bounded device wait ran out.  Every output of the launch that
+                             reported it, and of every later launch on the same stream up to the
+                             dem_check that returns it, is invalid and must be discarded (a CTA
+                             that gave up may have left a tile copy unfinished).  dem_last_error
+                             says whether the wait for that copy to land also ran out. */
+  DEM_ERR_INDEX = -6      /* a device kernel met an index out of range (pairs, tri_off) and
+                             skipped the access */
 } dem_status;
 
 /* Collision-time procedure of dem_collision_times, dem_detect and
@@ -156,7 +167,10 @@ typedef struct {
   int64_t rollbacks;        /* local time stepping: particles rolled back by consolidation */
   int64_t rollbacks_before_old; /* ... of which to before their old snapshot (0 if the theorem holds) */
   int64_t advances;         /* local time stepping: particle advances (particle-steps) */
-  int64_t reserved[2];
+  int64_t cta_busy_ns;      /* pair kernel: sum over its CTAs of the time from start to the last pair */
+  int64_t cta_busy_ns_max;  /* ... the largest such time (mean / max = the launch's load balance) */
+  int64_t ctas;             /* ... CTAs counted */
+  int64_t reserved[1];
 } dem_stats;
 
 /* Create a context: validates and copies *cfg, allocates scratch for the
@@ -263,6 +277,9 @@ typedef struct {
   int64_t *n_clusters;   /* [1] */
   uint8_t *active;       /* [n] 1 if the particle advanced in this sweep */
   double *t_global;      /* [1] earliest new time stamp over all clusters (the masking bound) */
+  const dem_narrow_out *narrow; /* optional (NULL: none): the narrow phase of the sweep's pairs at
+                                   their start time after consolidation (dem_narrow_phase's outputs,
+                                   computed in the same launch as the collision times) */
 } dem_lts_out;
 
 /* One sweep of the local-time-stepping cycle (paper Section 2.2 substeps,
@@ -275,7 +292,8 @@ typedef struct {
  *     cluster's earliest t_cur by free flight from its old snapshot (the
  *     interpolation between the snapshots) and takes the cluster step (the
  *     smallest member step, Eq. "cluster time step");
- *  5. collision times of every pair (dem_collision_times);
+ *  5. collision times of every pair (dem_collision_times; with out->narrow,
+ *     dem_detect: also the narrow phase of every pair at its start time);
  *  6. each cluster's new time stamp: its earliest status-2 time, else
  *     t_min + step; 7. masking: t_global = the minimum over clusters;
  *     clusters with t_min > t_global do not advance;
@@ -310,14 +328,57 @@ dem_status dem_lts_sweep(dem_ctx *ctx, const dem_particles *P, double *cur, doub
  * current): make that first call before any stream capture.  All calls share
  * the array and it keeps the last call's contents; each call clears what must
  * start at zero, and calls that overlap on the GPU race, so serialise them.
- * Capacity overflow shows as *n_pairs > cap (only cap pairs are written). */
+ * Capacity overflow shows as *n_pairs > cap (only cap pairs are written).
+ * Conditions met on the device (a bad static tri_off range, a non-finite
+ * state, the capacity overflow) accumulate in an error word of the array
+ * until dem_noalloc_check reads and clears it. */
 #define DEM_NOALLOC_MAX_PARTICLES 16384
 dem_status dem_build_candidates_noalloc(const dem_particles *P, int32_t *pairs, int64_t cap,
                                         int64_t *n_pairs, void *stream);
 
+/* Error word of dem_build_candidates_noalloc (no context): synchronise
+ * `stream`, return (and clear) the conditions its kernels met since the
+ * previous dem_noalloc_check, as dem_check does for a context (DEM_ERR_INDEX
+ * for a static particle whose tri_off range leaves the triangles,
+ * DEM_ERR_NONFINITE for a non-finite state, DEM_ERR_CAPACITY when *n_pairs
+ * exceeded cap).  Allocates nothing. */
+dem_status dem_noalloc_check(void *stream);
+
 /* Synchronise `stream`, return (and clear) the sticky device error as a
  * status (DEM_OK if none). */
 dem_status dem_check(dem_ctx *ctx, void *stream);
+
+/* Polls of the first bounded wait on a pair-kernel tile copy (default
+ * DEM_WAIT_POLLS_DEFAULT).  polls = 0 makes every such wait run out at once
+ * (the launch then reports DEM_ERR_TIMEOUT; the wait for the copy in flight
+ * keeps its full length, so no copy is abandoned): a way to exercise the
+ * timeout path without a fault.  DEM_ERR_ARG if polls is outside
+ * [0, 2^32 - 1]. */
+#define DEM_WAIT_POLLS_DEFAULT 4194304
+dem_status dem_set_wait_polls(dem_ctx *ctx, int64_t polls);
+
+/* Launch-group timing.  dem_trace(ctx, cap) with cap > 0 starts (or
+ * restarts) recording: every later launch group of a call made with ctx takes
+ * one record -- a CUDA event on the call's stream before and after the group,
+ * recorded as event-record nodes when the stream is being captured into a
+ * graph, so replays of the graph re-time them -- until cap records are taken.
+ * cap = 0 stops and frees the events (do not do that while a graph captured
+ * with the trace on may still be replayed).  Start the trace outside a
+ * capture.  dem_trace_read synchronises the recorded events and copies
+ * min(n, cap) records to the host arrays site[] (DEM_TR_*) and ms[]
+ * (milliseconds between the two events, as of the latest launch or replay);
+ * *n = records taken. */
+enum {
+  DEM_TR_BROAD = 0,   /* dem_build_candidates' kernels (and the sweep's broad phase) */
+  DEM_TR_TILES = 1,   /* tile list and tile bounding spheres before a pair-kernel launch */
+  DEM_TR_PAIRS = 2,   /* the pair kernel (narrow phase / collision times / both) */
+  DEM_TR_CONTACTS = 3,/* contact offsets, scatter and sort after a narrow phase */
+  DEM_TR_CLUSTERS = 4,/* connected components */
+  DEM_TR_LTS = 5      /* the bookkeeping kernels of a local-time-stepping sweep */
+};
+dem_status dem_trace(dem_ctx *ctx, int32_t cap);
+dem_status dem_trace_read(dem_ctx *ctx, int32_t *site /* host */, float *ms /* host */, int32_t cap,
+                          int32_t *n /* host */);
 
 /* Synchronise the device, copy the counters to host *out; reset them if
  * `reset` is nonzero. */

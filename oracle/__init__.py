@@ -74,7 +74,7 @@ def lib():
             L.demo_clusters.restype = C.c_int64
             L.demo_lts_sweep.argtypes = [dp, dp, u8p, C.c_int64, i64p, fp, C.c_int64, C.c_int, C.c_double,
                                          C.c_double, C.c_double, dp, C.c_int, C.c_int, i32p, C.c_int64, u8p, dp,
-                                         i32p, u8p, dp, i64p, i64p, C.c_int]
+                                         i32p, u8p, dp, i64p, i64p, C.c_int, dp]
             L.demo_hose_meet.argtypes = [dp, dp, C.c_int64, C.c_int64, C.c_int64]
             L.demo_hose_meet.restype = C.c_int
             L.demo_lts_sweep.restype = C.c_int64
@@ -242,7 +242,9 @@ def lts_sweep(w, old, dt_max, alpha=2.0, gravity=(0.0, 0.0, 0.0), zero_on_contac
               n_threads=None):
     """One local-time-stepping sweep; updates w.state (current snapshot) and
     ``old`` (old snapshot, same layout) in place.  Returns dict(pairs, status,
-    t_coll, ids, active, t_global, rollbacks, rollbacks_before_old)."""
+    t_coll, ids, active, t_global, rollbacks, rollbacks_before_old,
+    consolidated), consolidated = the current snapshot after the
+    consolidation (the state the collision times are evaluated on)."""
     assert w.state.flags["C_CONTIGUOUS"] and w.state.dtype == np.float64
     assert old.flags["C_CONTIGUOUS"] and old.dtype == np.float64 and old.shape == w.state.shape
     _, sta, off, tris = _geometry(w)
@@ -259,17 +261,18 @@ def lts_sweep(w, old, dt_max, alpha=2.0, gravity=(0.0, 0.0, 0.0), zero_on_contac
         pairs = np.zeros((cap, 2), np.int32)
         status = np.zeros(cap, np.uint8)
         tcol = np.zeros(cap)
+        cons = np.zeros_like(w.state)
         m = lib().demo_lts_sweep(
             _p(w.state, C.c_double), _p(old, C.c_double), _p(sta, C.c_uint8), n, _p(off, C.c_int64),
             _p(tris, C.c_float), tris.shape[1], int(w.K), float(w.tol), float(dt_max), float(alpha),
             _p(g, C.c_double), int(bool(zero_on_contact)), int(bool(hose)), _p(pairs, C.c_int32), cap,
             _p(status, C.c_uint8),
             _p(tcol, C.c_double), _p(ids, C.c_int32), _p(active, C.c_uint8), _p(tg, C.c_double),
-            _p(rb, C.c_int64), _p(rbb, C.c_int64), n_threads or default_threads())
+            _p(rb, C.c_int64), _p(rbb, C.c_int64), n_threads or default_threads(), _p(cons, C.c_double))
         if m <= cap:
             return dict(pairs=pairs[:m].copy(), status=status[:m].copy(), t_coll=tcol[:m].copy(), ids=ids,
                         active=active, t_global=float(tg[0]), rollbacks=int(rb[0]),
-                        rollbacks_before_old=int(rbb[0]))
+                        rollbacks_before_old=int(rbb[0]), consolidated=cons)
         # too many pairs for the outputs: undo and run again with room for all
         w.state[...] = cur0
         old[...] = old0

@@ -983,7 +983,8 @@ int64_t demo_lts_sweep(double *cur, double *old, const uint8_t *is_static, int64
                        const float *tris, int64_t n_tris, int K, double tol, double dt_max, double alpha,
                        const double gravity[3], int zero_on_contact, int hose, int32_t *pairs_out, int64_t cap,
                        uint8_t *status_out, double *t_coll_out, int32_t *cluster_id, uint8_t *active,
-                       double *t_global, int64_t *rollbacks, int64_t *rollbacks_before_old, int n_threads) {
+                       double *t_global, int64_t *rollbacks, int64_t *rollbacks_before_old, int n_threads,
+                       double *consolidated) {
   /* 1. particle step sizes (Eq. "damped particle time step size"): a creeping
    *    average of the previous step, capped by the global span; no history
    *    (t_old = t_cur) gives the global span */
@@ -1048,6 +1049,9 @@ int64_t demo_lts_sweep(double *cur, double *old, const uint8_t *is_static, int64
     }
     cur[FDT * n + p] = dtc[c];
   }
+  /* the snapshot the collision times (and a narrow phase at the pair start)
+   * are evaluated on */
+  if (consolidated) memcpy(consolidated, cur, sizeof(double) * DEMO_NFIELDS * (size_t)n);
   /* 5. collision time stamps of every candidate pair over the (now common)
    *    cluster interval */
   uint8_t *status = (uint8_t *)malloc((size_t)(m > 0 ? m : 1));

@@ -117,14 +117,16 @@ int demo_hose_meet(const double *cur, const double *old, int64_t n, int64_t i, i
  * place (old holds x, q, t_cur of the old snapshot and the v, w that carried
  * the particle to cur).  Outputs: candidate pairs, their status and t_coll
  * (up to cap), cluster ids, active[n], the global minimum, the number of
- * roll-backs and of roll-backs to before a particle's old snapshot.  Returns
+ * roll-backs and of roll-backs to before a particle's old snapshot, and
+ * (consolidated, [DEMO_NFIELDS][n], NULL to skip) the current snapshot after
+ * the consolidation, on which the collision times are evaluated.  Returns
  * the number of candidate pairs. */
 int64_t demo_lts_sweep(double *cur, double *old, const uint8_t *is_static, int64_t n,
                        const int64_t *tri_off, const float *tris, int64_t n_tris, int K, double tol,
                        double dt_max, double alpha, const double gravity[3], int zero_on_contact, int hose,
                        int32_t *pairs, int64_t cap, uint8_t *status, double *t_coll,
                        int32_t *cluster_id, uint8_t *active, double *t_global, int64_t *rollbacks,
-                       int64_t *rollbacks_before_old, int n_threads);
+                       int64_t *rollbacks_before_old, int n_threads, double *consolidated);
 
 #ifdef __cplusplus
 }

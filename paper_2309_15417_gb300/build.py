@@ -37,7 +37,7 @@ def sources():
 
 def _inputs():
     return sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + \
-        [os.path.join(INCLUDE, "dem.h"), os.path.abspath(__file__)]
+        sorted(glob.glob(os.path.join(INCLUDE, "*.h"))) + [os.path.abspath(__file__)]
 
 
 def up_to_date() -> bool:

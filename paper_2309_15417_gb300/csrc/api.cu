@@ -5,11 +5,14 @@
 #include <cstring>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.cuh"
 
 struct dem_ctx {
   dem_config cfg;
   dem::Scratch S;
+  dem::Trace trace;
   int device;
   int num_sms;
   std::string last_error;
@@ -17,7 +20,56 @@ struct dem_ctx {
   int n_allocs;
 };
 
+static_assert(DEM_WAIT_POLLS_DEFAULT == dem::WAIT_POLLS_DEFAULT, "default wait polls");
+static_assert(sizeof(dem_stats) == sizeof(int64_t) * dem::ST_N, "dem_stats mirrors the device counters");
+
+namespace dem {
+
+int trace_begin(Scratch &S, int site, cudaStream_t s) {
+  Trace *t = S.trace;
+  if (!t || t->n >= t->cap) return -1;
+  const int r = t->n++;
+  t->site[r] = site;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  // inside a capture the record becomes an event-record node of the graph
+  if (cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(t->ev[2 * r], s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(t->ev[2 * r], s);
+  return r;
+}
+
+void trace_end(Scratch &S, int rec, cudaStream_t s) {
+  Trace *t = S.trace;
+  if (!t || rec < 0) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(t->ev[2 * rec + 1], s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(t->ev[2 * rec + 1], s);
+}
+
+}  // namespace dem
+
 namespace {
+
+// NVTX range around one C-ABI call
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+
+void trace_free(dem_ctx *c) {
+  dem::Trace &t = c->trace;
+  for (int q = 0; q < 2 * t.cap; ++q)
+    if (t.ev[q]) cudaEventDestroy(t.ev[q]);
+  delete[] t.ev;
+  delete[] t.site;
+  t = dem::Trace{};
+  c->S.trace = nullptr;
+}
 
 dem_status fail(dem_ctx *c, dem_status st, const std::string &msg) {
   if (c) c->last_error = msg;
@@ -126,6 +178,7 @@ dem_status dem_create(const dem_config *cfg, dem_ctx **out) {
 
 void dem_destroy(dem_ctx *c) {
   if (!c) return;
+  trace_free(c);
   for (int q = 0; q < c->n_allocs; ++q) cudaFree(c->allocs[q]);
   delete c;
 }
@@ -137,6 +190,7 @@ const char *dem_last_error(const dem_ctx *c) {
 
 dem_status dem_build_candidates(dem_ctx *c, const dem_particles *P, int32_t *pairs, int64_t cap,
                                 int64_t *n_pairs, void *stream) {
+  Range range("dem_build_candidates");
   if (!c) return DEM_ERR_ARG;
   dem_status st = check_particles(c, P);
   if (st != DEM_OK) return st;
@@ -149,6 +203,7 @@ dem_status dem_build_candidates(dem_ctx *c, const dem_particles *P, int32_t *pai
 dem_status dem_narrow_phase(dem_ctx *c, const dem_particles *P, const int32_t *pairs, int64_t max_pairs,
                             const int64_t *n_pairs, const double *t_eval, const dem_narrow_out *out,
                             void *stream) {
+  Range range("dem_narrow_phase");
   if (!c) return DEM_ERR_ARG;
   dem_status st = check_particles(c, P);
   if (st != DEM_OK) return st;
@@ -167,11 +222,13 @@ dem_status dem_narrow_phase(dem_ctx *c, const dem_particles *P, const int32_t *p
 dem_status dem_collision_times(dem_ctx *c, const dem_particles *P, const int32_t *pairs, int64_t max_pairs,
                                const int64_t *n_pairs, double *t_coll, uint8_t *status, int32_t *tri_ab,
                                void *stream) {
+  Range range("dem_collision_times");
   if (!c) return DEM_ERR_ARG;
   dem_status st = check_particles(c, P);
   if (st != DEM_OK) return st;
   if (max_pairs < 0 || (max_pairs > 0 && (!pairs || !t_coll || !status || !tri_ab)))
     return fail(c, DEM_ERR_ARG, "collision_times: bad arguments");
+  if (max_pairs > c->S.cap_pairs) return fail(c, DEM_ERR_CAPACITY, "collision_times: max_pairs exceeds capacity");
   cudaError_t e = dem::launch_ctime(c->cfg.precision, c->cfg.ctime_method, *P, pairs, max_pairs, n_pairs, c->cfg.K,
                                     c->cfg.bisect_tol,
                                     t_coll, status, tri_ab, c->S, c->num_sms, static_cast<cudaStream_t>(stream));
@@ -182,6 +239,7 @@ dem_status dem_collision_times(dem_ctx *c, const dem_particles *P, const int32_t
 dem_status dem_detect(dem_ctx *c, const dem_particles *P, const int32_t *pairs, int64_t max_pairs,
                       const int64_t *n_pairs, const dem_narrow_out *out, double *t_coll, uint8_t *status,
                       int32_t *tri_ab, void *stream) {
+  Range range("dem_detect");
   if (!c) return DEM_ERR_ARG;
   dem_status st = check_particles(c, P);
   if (st != DEM_OK) return st;
@@ -211,6 +269,7 @@ dem_status dem_detect(dem_ctx *c, const dem_particles *P, const int32_t *pairs, 
 
 dem_status dem_clusters(dem_ctx *c, int64_t n, const int32_t *edges, int64_t max_edges, const int64_t *n_edges,
                         const uint8_t *is_static, int32_t *cluster_id, int64_t *n_clusters, void *stream) {
+  Range range("dem_clusters");
   if (!c) return DEM_ERR_ARG;
   if (n < 0 || max_edges < 0 || (max_edges > 0 && !edges) || (n > 0 && !cluster_id) || !n_clusters)
     return fail(c, DEM_ERR_ARG, "clusters: bad arguments");
@@ -223,6 +282,7 @@ dem_status dem_clusters(dem_ctx *c, int64_t n, const int32_t *edges, int64_t max
 
 dem_status dem_lts_sweep(dem_ctx *c, const dem_particles *P, double *cur, double *old, const dem_lts_params *prm,
                          const dem_lts_out *out, void *stream) {
+  Range range("dem_lts_sweep");
   if (!c) return DEM_ERR_ARG;
   if (!P || !prm || !out) return fail(c, DEM_ERR_ARG, "lts_sweep: null argument");
   if (P->state && P->state != cur) return fail(c, DEM_ERR_ARG, "lts_sweep: P->state must be NULL or cur");
@@ -236,6 +296,11 @@ dem_status dem_lts_sweep(dem_ctx *c, const dem_particles *P, double *cur, double
       (out->max_pairs > 0 && (!out->pairs || !out->t_coll || !out->status || !out->tri_ab)))
     return fail(c, DEM_ERR_ARG, "lts_sweep: bad outputs");
   if (out->max_pairs > c->S.cap_pairs) return fail(c, DEM_ERR_CAPACITY, "lts_sweep: max_pairs exceeds capacity");
+  const dem_narrow_out *nw = out->narrow;
+  if (nw && (!nw->n_contacts || nw->contact_cap < 0 ||
+             (out->max_pairs > 0 && (!nw->dmin || !nw->pa || !nw->pb || !nw->tri_ab || !nw->flag)) ||
+             (nw->contact_cap > 0 && (!nw->contacts || !nw->contact_geom))))
+    return fail(c, DEM_ERR_ARG, "lts_sweep: bad narrow-phase outputs");
   if (!(prm->dt_max > 0.0) || !(prm->alpha > 0.0)) return fail(c, DEM_ERR_ARG, "lts_sweep: dt_max, alpha > 0");
   cudaError_t e = dem::launch_lts(c->cfg.precision, c->cfg.ctime_method, c->cfg.K, c->cfg.bisect_tol, G, cur, old, *prm, *out, c->S,
                                   c->num_sms, static_cast<cudaStream_t>(stream));
@@ -244,6 +309,7 @@ dem_status dem_lts_sweep(dem_ctx *c, const dem_particles *P, double *cur, double
 }
 
 dem_status dem_check(dem_ctx *c, void *stream) {
+  Range range("dem_check");
   if (!c) return DEM_ERR_ARG;
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(c, e, "check: stream");
@@ -254,11 +320,62 @@ dem_status dem_check(dem_ctx *c, void *stream) {
   e = cudaMemset(c->S.err, 0, sizeof(uint32_t));
   if (e != cudaSuccess) return cuda_fail(c, e, "check: clear error word");
   if (bits & dem::ERR_INDEX) return fail(c, DEM_ERR_INDEX, "device: index out of range");
+  if (bits & dem::ERR_NONFINITE) return fail(c, DEM_ERR_NONFINITE, "device: non-finite state or vertex");
   if (bits & dem::ERR_CAPACITY) return fail(c, DEM_ERR_CAPACITY, "device: output capacity exceeded");
-  return fail(c, DEM_ERR_TIMEOUT, "device: bounded wait ran out");
+  if (bits & dem::ERR_DRAIN)
+    return fail(c, DEM_ERR_TIMEOUT, "device: bounded wait ran out, and so did the wait for the copy in flight");
+  return fail(c, DEM_ERR_TIMEOUT, "device: bounded wait ran out (the copy in flight landed)");
+}
+
+dem_status dem_set_wait_polls(dem_ctx *c, int64_t polls) {
+  if (!c) return DEM_ERR_ARG;
+  if (polls < 0 || polls > (int64_t)UINT32_MAX) return fail(c, DEM_ERR_ARG, "set_wait_polls: out of range");
+  c->S.wait_polls = polls == 0 ? 0u : (uint32_t)polls;
+  return DEM_OK;
+}
+
+dem_status dem_trace(dem_ctx *c, int32_t capacity) {
+  if (!c || capacity < 0) return DEM_ERR_ARG;
+  if (capacity == 0) {
+    trace_free(c);
+    return DEM_OK;
+  }
+  dem::Trace &t = c->trace;
+  if (t.cap != capacity) {
+    trace_free(c);
+    t.ev = new cudaEvent_t[2 * (size_t)capacity]();
+    t.site = new int32_t[capacity]();
+    t.cap = capacity;
+    for (int q = 0; q < 2 * capacity; ++q) {
+      cudaError_t e = cudaEventCreate(&t.ev[q]);
+      if (e != cudaSuccess) {
+        t.ev[q] = nullptr;
+        trace_free(c);
+        return cuda_fail(c, e, "trace: event");
+      }
+    }
+  }
+  t.n = 0;
+  c->S.trace = &t;
+  return DEM_OK;
+}
+
+dem_status dem_trace_read(dem_ctx *c, int32_t *site, float *ms, int32_t cap, int32_t *n) {
+  if (!c || !n || cap < 0 || (cap > 0 && (!site || !ms))) return DEM_ERR_ARG;
+  const dem::Trace &t = c->trace;
+  *n = t.n;
+  const int m = t.n < cap ? t.n : cap;
+  for (int r = 0; r < m; ++r) {
+    site[r] = t.site[r];
+    cudaError_t e = cudaEventSynchronize(t.ev[2 * r + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms[r], t.ev[2 * r], t.ev[2 * r + 1]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "trace_read");
+  }
+  return DEM_OK;
 }
 
 dem_status dem_get_stats(dem_ctx *c, dem_stats *out, int reset) {
+  Range range("dem_get_stats");
   if (!c || !out) return DEM_ERR_ARG;
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_fail(c, e, "get_stats");

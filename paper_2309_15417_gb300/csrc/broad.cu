@@ -27,16 +27,27 @@ namespace {
 using D = OpsD;
 
 // swept spheres of all particles; max rho over moving particles; static
-// particles listed with their pose at t_cur and an empty box
+// particles listed with their pose at t_cur and an empty box.  A particle
+// with a non-finite state field sets ERR_NONFINITE and gets a NaN sphere and
+// no static entry: it takes part in no pair.
 __global__ void k_prep(int64_t n, const double *st, const uint8_t *is_static, Sphere4 *sph,
                        unsigned long long *rho_max, int32_t *static_ids, int32_t *n_static, double *spose,
-                       unsigned long long *sbox) {
+                       unsigned long long *sbox, uint32_t *err) {
   __shared__ double red[8];
   __shared__ double rc[POSE_TERMS + 1], rs[POSE_TERMS + 1];
   if (threadIdx.x == 0) pose_reciprocals(rc, rs);
   __syncthreads();
   double mx = 0.0;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    bool fin = true;
+#pragma unroll
+    for (int f = 0; f < DEM_NFIELDS; ++f) fin = fin && isfinite(st[f * n + p]);
+    if (!fin) {
+      set_err(err, ERR_NONFINITE);
+      const double nan = __longlong_as_double(0x7ff8000000000000LL);
+      sph[p] = Sphere4{nan, nan, nan, nan};
+      continue;
+    }
     const double hdt = D::mul(st[14 * n + p], 0.5);
     const double vx = st[3 * n + p], vy = st[4 * n + p], vz = st[5 * n + p];
     Sphere4 s;
@@ -136,11 +147,11 @@ __global__ void k_count(int64_t n, const Sphere4 *sph, const uint8_t *is_static,
                         const unsigned long long *rho_max, uint32_t mask, int4 *cell, int32_t *bcnt) {
   const double ih = inv_cell(rho_max);
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-    if (is_static && is_static[p]) {  // static particles are not binned
+    const Sphere4 s = sph[p];
+    if ((is_static && is_static[p]) || !(s.w >= 0.0)) {  // static and non-finite particles are not binned
       cell[p] = make_int4(0, 0, 0, -1);
       continue;
     }
-    const Sphere4 s = sph[p];
     const int cx = cell_coord(s.x, ih), cy = cell_coord(s.y, ih), cz = cell_coord(s.z, ih);
     const uint32_t b = bucket_of(cx, cy, cz, mask);
     cell[p] = make_int4(cx, cy, cz, int(b));
@@ -408,9 +419,11 @@ cudaError_t launch_broad(const dem_particles &P, int32_t *pairs, int64_t cap, in
   const uint32_t mask = uint32_t(S.table_size - 1);
   const int tb = 256;
   const unsigned grid = (unsigned)((n + tb - 1) / tb);
+  const int rec = trace_begin(S, TR_BROAD, s);
   if ((e = cudaMemsetAsync(S.bucket_cnt, 0, sizeof(int32_t) * S.table_size, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(S.bucket_cur, 0, sizeof(int32_t) * S.table_size, s)) != cudaSuccess) return e;
-  k_prep<<<grid, tb, 0, s>>>(n, P.state, P.is_static, S.sph, S.rho_max, S.static_ids, S.n_static, S.spose, S.sbox);
+  k_prep<<<grid, tb, 0, s>>>(n, P.state, P.is_static, S.sph, S.rho_max, S.static_ids, S.n_static, S.spose, S.sbox,
+                             S.err);
   S.launches += 1;
   if (P.is_static) {
     k_static_box<<<304, tb, 0, s>>>(n, P.tri_off, reinterpret_cast<const float4 *>(P.tris), P.n_tris,
@@ -435,6 +448,7 @@ cudaError_t launch_broad(const dem_particles &P, int32_t *pairs, int64_t cap, in
                                      S.bucket_ids, mask, S.static_ids, S.n_static, S.sbox, hose_old, nullptr,
                                      S.poff, pairs, cap, n_pairs, S.err);
   S.launches += 1;
+  trace_end(S, rec, s);
   return cudaGetLastError();
 }
 

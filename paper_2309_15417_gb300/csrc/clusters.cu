@@ -92,6 +92,7 @@ cudaError_t launch_clusters(int64_t n, const int32_t *edges, int64_t max_edges, 
   if (n <= 0) return cudaSuccess;
   const int tb = 256;
   const unsigned g = (unsigned)((n + tb - 1) / tb);
+  const int rec = trace_begin(S, TR_CLUSTERS, s);
   k_cc_init<<<g, tb, 0, s>>>(n, is_static, id);
   if (max_edges > 0) {
     const unsigned ge = (unsigned)((max_edges + tb - 1) / tb);
@@ -101,6 +102,7 @@ cudaError_t launch_clusters(int64_t n, const int32_t *edges, int64_t max_edges, 
   S.launches += 3;
   k_cc_final<<<g, tb, 0, s>>>(n, id, reinterpret_cast<unsigned long long *>(n_clusters));
   k_cc_flatten<<<g, tb, 0, s>>>(n, id);
+  trace_end(S, rec, s);
   return cudaGetLastError();
 }
 

@@ -9,9 +9,15 @@
 namespace dem {
 
 // sticky device error bits (context error word)
-constexpr uint32_t ERR_CAPACITY = 1u;  // an output capacity was exceeded
-constexpr uint32_t ERR_TIMEOUT = 2u;   // a bounded wait ran out
-constexpr uint32_t ERR_INDEX = 4u;     // an index out of range was met
+constexpr uint32_t ERR_CAPACITY = 1u;   // an output capacity was exceeded
+constexpr uint32_t ERR_TIMEOUT = 2u;    // a bounded wait ran out
+constexpr uint32_t ERR_INDEX = 4u;      // an index out of range was met
+constexpr uint32_t ERR_NONFINITE = 8u;  // a state field or a vertex is NaN or infinite
+constexpr uint32_t ERR_DRAIN = 16u;     // after a timeout, the wait for the copy in flight also ran out
+
+// polls of the first bounded wait on a tile copy (the wait that follows a
+// timeout, for the copy in flight to land, always uses this default)
+constexpr uint32_t WAIT_POLLS_DEFAULT = 1u << 22;
 
 // counters, same order as dem_stats
 enum {
@@ -29,7 +35,10 @@ enum {
   ST_ROLLBACK,
   ST_ROLLBACK_BAD,
   ST_ADVANCE,
-  ST_N = 16
+  ST_BUSY,      // pair kernel: CTA busy time (ns), summed
+  ST_BUSYMAX,   // ... its maximum (atomicMax)
+  ST_CTAS,      // ... CTAs counted
+  ST_N = 18
 };
 
 // swept sphere of a particle (centre, radius), binary64
@@ -37,8 +46,29 @@ struct __align__(32) Sphere4 {
   double x, y, z, w;
 };
 
+// Launch groups timed by the trace (dem_trace): CUDA events recorded on the
+// launching stream before and after each group, also inside a stream capture
+// (as event-record nodes of the graph).
+enum {
+  TR_BROAD = DEM_TR_BROAD,
+  TR_TILES = DEM_TR_TILES,
+  TR_PAIRS = DEM_TR_PAIRS,
+  TR_CONTACTS = DEM_TR_CONTACTS,
+  TR_CLUSTERS = DEM_TR_CLUSTERS,
+  TR_LTS = DEM_TR_LTS
+};
+
+struct Trace {
+  int cap = 0;                    // records available
+  int n = 0;                      // records taken since the trace was (re)started
+  cudaEvent_t *ev = nullptr;      // [2 * cap] begin / end of each record
+  int32_t *site = nullptr;        // [cap] launch group of each record
+};
+
 struct Scratch {
+  Trace *trace = nullptr;         // launch-group timing (null: off)
   int64_t launches = 0;           // host-side count of kernel launches issued
+  uint32_t wait_polls = WAIT_POLLS_DEFAULT;  // first bounded wait of the pair kernel's tile copies
   // common
   uint32_t *err;                  // [1]
   unsigned long long *stats;      // [ST_N]
@@ -104,6 +134,11 @@ int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, int64_t *tota
                        int64_t *part, cudaStream_t s);
 int scan_exclusive_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, int64_t *part,
                               cudaStream_t s);
+
+// trace records around a launch group (no-ops when the trace is off or
+// full); trace_begin returns the record index or -1
+int trace_begin(Scratch &S, int site, cudaStream_t s);
+void trace_end(Scratch &S, int rec, cudaStream_t s);
 
 // launchers
 // hose_old: the old snapshots for the space-time hose test of moving pairs

@@ -176,21 +176,37 @@ cudaError_t launch_lts(int prec, int method, int K, double tol, const dem_partic
   const int tb = 256;
   const unsigned grid = (unsigned)(n > 0 ? (n + tb - 1) / tb : 1);
   const unsigned pgrid = (unsigned)(out.max_pairs > 0 ? (out.max_pairs + tb - 1) / tb : 1);
+  int rec = trace_begin(S, TR_LTS, s);
   k_lts_step<<<grid, tb, 0, s>>>(n, cur, old, P.is_static, prm.dt_max, prm.alpha);
   S.launches += 1;
+  trace_end(S, rec, s);
   if ((e = launch_broad(P, out.pairs, out.max_pairs, out.n_pairs, S, s, prm.hose ? old : nullptr)) != cudaSuccess)
     return e;
   if ((e = launch_clusters(n, out.pairs, out.max_pairs, out.n_pairs, P.is_static, out.cluster_id, out.n_clusters, S,
                            s)) != cudaSuccess)
     return e;
+  rec = trace_begin(S, TR_LTS, s);
   k_lts_reduce<<<grid, tb, 0, s>>>(n, cur, P.is_static, out.cluster_id, S.lts_tmin, S.lts_step, S.err);
   k_lts_consolidate<<<grid, tb, 0, s>>>(n, cur, old, P.is_static, out.cluster_id, S.lts_tmin, S.lts_step, S.lts_tnew,
                                         S.stats);
   S.launches += 2;
-  if (out.max_pairs > 0) {
+  trace_end(S, rec, s);
+  if (out.max_pairs > 0 && out.narrow && method == DEM_CTIME_SAMPLES) {
+    // narrow phase at the pair start and collision times in one launch
+    if ((e = launch_detect(prec, P, out.pairs, out.max_pairs, out.n_pairs, *out.narrow, K, tol, out.t_coll,
+                           out.status, out.tri_ab, S, num_sms, s)) != cudaSuccess)
+      return e;
+  } else if (out.max_pairs > 0) {
+    if (out.narrow &&
+        (e = launch_narrow(prec, P, out.pairs, out.max_pairs, out.n_pairs, nullptr, *out.narrow, S, num_sms, s)) !=
+            cudaSuccess)
+      return e;
     if ((e = launch_ctime(prec, method, P, out.pairs, out.max_pairs, out.n_pairs, K, tol, out.t_coll, out.status, out.tri_ab,
                           S, num_sms, s)) != cudaSuccess)
       return e;
+  }
+  rec = trace_begin(S, TR_LTS, s);
+  if (out.max_pairs > 0) {
     k_lts_tnew<<<pgrid, tb, 0, s>>>(n, out.pairs, out.n_pairs, out.max_pairs, out.status, out.t_coll,
                                     out.cluster_id, S.lts_tnew);
     S.launches += 1;
@@ -206,6 +222,7 @@ cudaError_t launch_lts(int prec, int method, int K, double tol, const dem_partic
                                     S.lts_touch, prm.gravity[0], prm.gravity[1], prm.gravity[2],
                                     prm.zero_on_contact, out.active, out.t_global, S.stats);
   S.launches += 1;
+  trace_end(S, rec, s);
   return cudaGetLastError();
 }
 

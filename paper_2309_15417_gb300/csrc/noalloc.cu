@@ -18,6 +18,9 @@
 // array and it keeps the previous call's contents, so every call clears what
 // must start at zero; two calls whose work overlaps on the GPU (other streams,
 // other host threads) race on the array and must be serialised by the caller.
+// The array's error word is the exception: it collects what the kernels met
+// (bad index, non-finite state, capacity) until dem_noalloc_check reads and
+// clears it, the context-free counterpart of dem_check.
 #include <mutex>
 
 #include "internal.cuh"
@@ -83,6 +86,9 @@ cudaError_t scratch_base(unsigned char **out) {
 extern "C" dem_status dem_build_candidates_noalloc(const dem_particles *P, int32_t *pairs, int64_t cap,
                                                    int64_t *n_pairs, void *stream) {
   using namespace dem;
+  // a launch error left on this thread by an earlier, unrelated call would
+  // otherwise be reported as this call's: drain it first
+  (void)cudaGetLastError();
   if (!P || P->n < 0 || !n_pairs || cap < 0 || (cap > 0 && !pairs)) return DEM_ERR_ARG;
   if (P->n > 0 && (!P->state || !P->tri_off)) return DEM_ERR_ARG;
   if (P->n > NA_MAX) return DEM_ERR_CAPACITY;
@@ -114,8 +120,27 @@ extern "C" dem_status dem_build_candidates_noalloc(const dem_particles *P, int32
   S.sbox = reinterpret_cast<unsigned long long *>(b + OFF_SBOX);
   S.sbox32 = reinterpret_cast<float *>(b + OFF_SBOX32);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // the error word keeps the previous call's value: clear it
-  if (cudaMemsetAsync(S.err, 0, sizeof(uint32_t), s) != cudaSuccess) return DEM_ERR_CUDA;
+  // the error word collects the conditions met since the last
+  // dem_noalloc_check, which reads and clears it
   if (launch_broad(*P, pairs, cap, n_pairs, S, s) != cudaSuccess) return DEM_ERR_CUDA;
   return DEM_OK;
+}
+
+extern "C" dem_status dem_noalloc_check(void *stream) {
+  using namespace dem;
+  (void)cudaGetLastError();
+  unsigned char *b = nullptr;
+  if (scratch_base(&b) != cudaSuccess) return DEM_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return DEM_ERR_CUDA;
+  uint32_t bits = 0;
+  // a pageable host target: the copy completes before cudaMemcpy returns,
+  // and nothing is allocated
+  if (cudaMemcpy(&bits, b + OFF_ERR, sizeof(bits), cudaMemcpyDeviceToHost) != cudaSuccess) return DEM_ERR_CUDA;
+  if (!bits) return DEM_OK;
+  if (cudaMemset(b + OFF_ERR, 0, sizeof(uint32_t)) != cudaSuccess) return DEM_ERR_CUDA;
+  if (bits & ERR_INDEX) return DEM_ERR_INDEX;
+  if (bits & ERR_NONFINITE) return DEM_ERR_NONFINITE;
+  if (bits & ERR_CAPACITY) return DEM_ERR_CAPACITY;
+  return DEM_ERR_TIMEOUT;
 }

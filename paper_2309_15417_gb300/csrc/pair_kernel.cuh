@@ -118,6 +118,7 @@ struct PairArgs {
   unsigned int *work;
   uint32_t *err;
   unsigned long long *stats;
+  uint32_t wait_polls;  // polls of the first wait on a tile copy
 };
 
 template <int PREC>
@@ -208,9 +209,10 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t 
       : "memory");
   return ok != 0;
 }
-// bounded wait on the barrier phase; false if it ran out
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t phase) {
-  for (uint32_t it = 0; it < (1u << 22); ++it)
+// bounded wait on the barrier phase (at most `polls` polls); false if it ran out
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t phase,
+                                          uint32_t polls = WAIT_POLLS_DEFAULT) {
+  for (uint32_t it = 0; it < polls; ++it)
     if (mbar_try_wait(bar, phase)) return true;
   return false;
 }
@@ -464,7 +466,7 @@ struct Cta {
       for (int sl = 0; sl < 3; ++sl)
         bulk_g2s(&s.Ab[sl][0], A.tris + sl * A.n_tris + s.offA + (int64_t)ta * TT, 16u * na, &s.mbar);
     }
-    bool ok = mbar_wait(&s.mbar, phase);
+    bool ok = mbar_wait(&s.mbar, phase, A.wait_polls);
     ok = __syncthreads_and(ok) != 0;
     phase ^= 1u;
     if (!ok) {
@@ -472,7 +474,9 @@ struct Cta {
         set_err(A.err, ERR_TIMEOUT);
         s.abort = 1;
       }
-      mbar_wait(&s.mbar, phase ^ 1u);  // let the copy in flight land
+      // let the copy in flight land (full-length wait); if this runs out too,
+      // the copy may still write this CTA's shared memory after it exits
+      if (!mbar_wait(&s.mbar, phase ^ 1u) && tid == 0) set_err(A.err, ERR_DRAIN);
     }
     __syncthreads();
     return ok;
@@ -494,6 +498,10 @@ struct Cta {
         T d = dx * dx + dy * dy + dz * dz;
         r2 = d > r2 ? d : r2;
       }
+      // a non-finite vertex makes the centre or the radius non-finite; its
+      // sphere then fails every culling test, so the pair's result would be
+      // silently incomplete: report it
+      if (!(r2 <= T(3.0e38)) || !(fabs(double(cx) + double(cy) + double(cz)) <= 1.0e300)) set_err(A.err, ERR_NONFINITE);
       S[0][k] = cx;
       S[1][k] = cy;
       S[2][k] = cz;
@@ -1875,6 +1883,15 @@ struct Cta {
       }
       const double *st = A.st;
       const int64_t n = A.n;
+      if (!s.bad) {
+        bool fin = true;
+        for (int f = 0; f < DEM_NFIELDS; ++f) fin = fin && isfinite(st[f * n + s.i]) && isfinite(st[f * n + s.j]);
+        if (!fin) {  // skip the pair: its outputs are those of a pair without triangles
+          set_err(A.err, ERR_NONFINITE);
+          s.bad = 1;
+          s.nA = s.nB = 0;
+        }
+      }
       s.eps = OpsD::add(st[15 * n + s.i], st[15 * n + s.j]);
       const double ti = st[13 * n + s.i], tj = st[13 * n + s.j];
       const double di = st[14 * n + s.i], dj = st[14 * n + s.j];
@@ -1912,6 +1929,8 @@ __global__ void __launch_bounds__(Cfg<PREC>::NT, Cfg<PREC>::MINB) pair_kernel(Pa
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Smem<PREC> &s = *reinterpret_cast<Smem<PREC> *>(smem_raw);
   Cta<PREC> c(s, A);
+  unsigned long long t_begin = 0;
+  if (c.tid == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_begin));
   if (c.tid < ST_N) s.cnt[c.tid] = 0;
   if (c.tid == 0) {
     mbar_init(&s.mbar);
@@ -2121,7 +2140,15 @@ __global__ void __launch_bounds__(Cfg<PREC>::NT, Cfg<PREC>::MINB) pair_kernel(Pa
     __syncthreads();
   }
   __syncthreads();
-  if (c.tid < ST_N && s.cnt[c.tid]) atomicAdd(&A.stats[c.tid], s.cnt[c.tid]);
+  if (c.tid == 0) {  // this CTA's busy time: from its start to the end of its last pair
+    unsigned long long t_end;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+    s.cnt[ST_BUSY] = t_end - t_begin;
+    s.cnt[ST_CTAS] = 1;
+    atomicMax(&A.stats[ST_BUSYMAX], t_end - t_begin);
+  }
+  __syncthreads();
+  if (c.tid < ST_N && c.tid != ST_BUSYMAX && s.cnt[c.tid]) atomicAdd(&A.stats[c.tid], s.cnt[c.tid]);
 }
 
 // ------------------------------------------------------------- contact sort

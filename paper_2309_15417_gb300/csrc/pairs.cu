@@ -193,6 +193,7 @@ __global__ void k_tile_spheres(const int64_t *tri_off, const float4 *tris, int64
 // returns the error of the first call that failed
 cudaError_t prepare_tiles(const dem_particles &P, Scratch &S, cudaStream_t s) {
   if (P.n <= 0) return cudaSuccess;
+  const int rec = trace_begin(S, TR_TILES, s);
   unsigned long long *count = reinterpret_cast<unsigned long long *>(S.tmp + 4);
   cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
@@ -201,6 +202,7 @@ cudaError_t prepare_tiles(const dem_particles &P, Scratch &S, cudaStream_t s) {
   k_tile_spheres<<<1216, 256, 0, s>>>(P.tri_off, reinterpret_cast<const float4 *>(P.tris), P.n_tris, S.tile_list,
                                       count, S.tile_sph, S.tile_box, S.cap_tiles);
   S.launches += 2;
+  trace_end(S, rec, s);
   return cudaGetLastError();
 }
 
@@ -223,6 +225,7 @@ PairArgs make_args(const dem_particles &P, const int32_t *pairs, int64_t max_pai
   a.work = S.work;
   a.err = S.err;
   a.stats = S.stats;
+  a.wait_polls = S.wait_polls;
   return a;
 }
 
@@ -242,14 +245,17 @@ cudaError_t finish_narrow(int prec, PairArgs &a, const dem_particles &P, const i
     if ((e = cudaMemsetAsync(S.pc, 0, sizeof(int64_t) * max_pairs, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(S.pcur, 0, sizeof(int32_t) * max_pairs, s)) != cudaSuccess) return e;
     if ((e = prepare_tiles(P, S, s)) != cudaSuccess) return e;
+    const int rec = trace_begin(S, TR_PAIRS, s);
     if (fused)
       e = prec == 0 ? launch_pairs<0, MODE_BOTH>(a, num_sms, s) : launch_pairs<1, MODE_BOTH>(a, num_sms, s);
     else
       e = prec == 0 ? launch_pairs<0, MODE_NARROW>(a, num_sms, s) : launch_pairs<1, MODE_NARROW>(a, num_sms, s);
     if (e != cudaSuccess) return e;
+    trace_end(S, rec, s);
     S.launches += 1;
   }
   // per-pair offsets, scatter, sort
+  const int rec_c = trace_begin(S, TR_CONTACTS, s);
   int64_t *total = S.tmp;
   if (max_pairs > 0) {
     S.launches += scan_exclusive_i64(S.pc, S.po, max_pairs, total, S.scan_part, s);
@@ -266,6 +272,7 @@ cudaError_t finish_narrow(int prec, PairArgs &a, const dem_particles &P, const i
   }
   contact_total<<<1, 1, 0, s>>>(total, S.st_count, S.cap_contacts, out.n_contacts, S.err);
   S.launches += 1;
+  trace_end(S, rec_c, s);
   return cudaGetLastError();
 }
 
@@ -325,9 +332,13 @@ cudaError_t launch_ctime(int prec, int method, const dem_particles &P, const int
   if (max_pairs <= 0) return cudaSuccess;
   if ((e = prepare_tiles(P, S, s)) != cudaSuccess) return e;
   S.launches += 1;
+  const int rec = trace_begin(S, TR_PAIRS, s);
   if (method == DEM_CTIME_NARROWING)
-    return prec == 0 ? launch_pairs<0, MODE_NTIME>(a, num_sms, s) : launch_pairs<1, MODE_NTIME>(a, num_sms, s);
-  return prec == 0 ? launch_pairs<0, MODE_CTIME>(a, num_sms, s) : launch_pairs<1, MODE_CTIME>(a, num_sms, s);
+    e = prec == 0 ? launch_pairs<0, MODE_NTIME>(a, num_sms, s) : launch_pairs<1, MODE_NTIME>(a, num_sms, s);
+  else
+    e = prec == 0 ? launch_pairs<0, MODE_CTIME>(a, num_sms, s) : launch_pairs<1, MODE_CTIME>(a, num_sms, s);
+  trace_end(S, rec, s);
+  return e;
 }
 
 }  // namespace dem

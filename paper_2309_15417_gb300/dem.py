@@ -25,14 +25,23 @@ DEM_NFIELDS = 17
 DEM_PREC_FP32_FIXUP = 0
 DEM_PREC_FP64 = 1
 
-STATUS = {0: "DEM_OK", -1: "DEM_ERR_ARG", -2: "DEM_ERR_CAPACITY", -3: "DEM_ERR_CUDA", -4: "DEM_ERR_INDEX",
-          -5: "DEM_ERR_TIMEOUT"}
+DEM_OK, DEM_ERR_ARG, DEM_ERR_CAPACITY, DEM_ERR_CUDA, DEM_ERR_NONFINITE, DEM_ERR_TIMEOUT, DEM_ERR_INDEX = \
+    0, -1, -2, -3, -4, -5, -6
+STATUS = {0: "DEM_OK", -1: "DEM_ERR_ARG", -2: "DEM_ERR_CAPACITY", -3: "DEM_ERR_CUDA", -4: "DEM_ERR_NONFINITE",
+          -5: "DEM_ERR_TIMEOUT", -6: "DEM_ERR_INDEX"}
 
 # every symbol include/dem.h declares
 EXPORTS = ["dem_create", "dem_destroy", "dem_last_error", "dem_build_candidates", "dem_narrow_phase",
            "dem_collision_times", "dem_detect", "dem_clusters", "dem_lts_sweep", "dem_check", "dem_get_stats",
-           "dem_build_candidates_noalloc"]
+           "dem_build_candidates_noalloc", "dem_noalloc_check", "dem_set_wait_polls", "dem_trace",
+           "dem_trace_read",
+           # include/dem_probe.h (measurement support)
+           "dem_probe_fma_peak", "dem_count_dist_flops"]
 DEM_NOALLOC_MAX_PARTICLES = 16384
+DEM_WAIT_POLLS_DEFAULT = 4194304
+# launch groups of the trace (dem_trace)
+TRACE_SITES = {0: "broad phase", 1: "tile spheres", 2: "pair kernel", 3: "contact sort", 4: "clusters",
+               5: "LTS bookkeeping"}
 DEM_CTIME_SAMPLES, DEM_CTIME_NARROWING = 0, 1
 
 
@@ -67,7 +76,8 @@ class dem_lts_params(C.Structure):
 class dem_lts_out(C.Structure):
     _fields_ = [("pairs", C.c_void_p), ("max_pairs", C.c_int64), ("n_pairs", C.c_void_p), ("t_coll", C.c_void_p),
                 ("status", C.c_void_p), ("tri_ab", C.c_void_p), ("cluster_id", C.c_void_p),
-                ("n_clusters", C.c_void_p), ("active", C.c_void_p), ("t_global", C.c_void_p)]
+                ("n_clusters", C.c_void_p), ("active", C.c_void_p), ("t_global", C.c_void_p),
+                ("narrow", C.c_void_p)]
 
 
 class dem_stats(C.Structure):
@@ -75,7 +85,8 @@ class dem_stats(C.Structure):
                 ("dist_fp64", C.c_int64), ("pair_evals", C.c_int64), ("method_checks", C.c_int64),
                 ("bisect_steps", C.c_int64), ("contacts", C.c_int64), ("pairs_done", C.c_int64),
                 ("kernel_launches", C.c_int64), ("tile_pairs", C.c_int64), ("rollbacks", C.c_int64),
-                ("rollbacks_before_old", C.c_int64), ("advances", C.c_int64), ("reserved", C.c_int64 * 2)]
+                ("rollbacks_before_old", C.c_int64), ("advances", C.c_int64), ("cta_busy_ns", C.c_int64),
+                ("cta_busy_ns_max", C.c_int64), ("ctas", C.c_int64), ("reserved", C.c_int64 * 1)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
@@ -126,6 +137,19 @@ def load(build_if_needed: bool = True):
         L.dem_lts_sweep.argtypes = [vp, C.POINTER(dem_particles), vp, vp, C.POINTER(dem_lts_params),
                                     C.POINTER(dem_lts_out), vp]
         L.dem_lts_sweep.restype = C.c_int
+        L.dem_noalloc_check.argtypes = [vp]
+        L.dem_noalloc_check.restype = C.c_int
+        L.dem_set_wait_polls.argtypes = [vp, i64]
+        L.dem_set_wait_polls.restype = C.c_int
+        L.dem_trace.argtypes = [vp, C.c_int32]
+        L.dem_trace.restype = C.c_int
+        L.dem_trace_read.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_float), C.c_int32,
+                                     C.POINTER(C.c_int32)]
+        L.dem_trace_read.restype = C.c_int
+        L.dem_probe_fma_peak.argtypes = [C.c_int32, C.c_int32, vp, C.POINTER(C.c_double)]
+        L.dem_probe_fma_peak.restype = C.c_int
+        L.dem_count_dist_flops.argtypes = [vp, i64, vp, vp]
+        L.dem_count_dist_flops.restype = C.c_int
         _lib = L
         return L
 
@@ -214,8 +238,48 @@ def dem_build_candidates_noalloc(P: dem_particles, pairs, cap: int, n_pairs, str
                                                    _stream(stream)))
 
 
+def dem_noalloc_check(stream=None) -> int:
+    """Error word of the allocation-free candidate search (synchronises the
+    stream, clears the word).  Returns the C status code."""
+    return int(load().dem_noalloc_check(_stream(stream)))
+
+
+def dem_probe_fma_peak(precision: int, iters: int = 1 << 16, stream=None) -> float:
+    """Measured FP32 (0) or FP64 (1) FMA-chain peak of the current GPU, FLOP/s."""
+    r = C.c_double()
+    _check(None, load().dem_probe_fma_peak(int(precision), int(iters), _stream(stream), C.byref(r)))
+    return float(r.value)
+
+
+def dem_count_dist_flops(tri, stream=None):
+    """FP32 operations of the pair kernel's triangle-pair distance for each
+    row of tri (CUDA float32 [n, 18]); returns an int64 CUDA tensor [n]."""
+    import torch
+    tri = _cuda(tri, torch.float32, "tri")
+    ops = torch.zeros(tri.shape[0], dtype=torch.int64, device=tri.device)
+    _check(None, load().dem_count_dist_flops(_ptr(tri), int(tri.shape[0]), _ptr(ops), _stream(stream)))
+    return ops
+
+
 def dem_check(ctx, stream=None):
     _check(ctx, load().dem_check(ctx, _stream(stream)))
+
+
+def dem_set_wait_polls(ctx, polls: int):
+    _check(ctx, load().dem_set_wait_polls(ctx, int(polls)))
+
+
+def dem_trace(ctx, cap: int):
+    _check(ctx, load().dem_trace(ctx, int(cap)))
+
+
+def dem_trace_read(ctx, cap: int = 4096):
+    """[(site, ms)] of the records taken since dem_trace started."""
+    site = (C.c_int32 * max(cap, 1))()
+    ms = (C.c_float * max(cap, 1))()
+    n = C.c_int32()
+    _check(ctx, load().dem_trace_read(ctx, site, ms, int(cap), C.byref(n)))
+    return [(int(site[k]), float(ms[k])) for k in range(min(n.value, cap))]
 
 
 def dem_get_stats(ctx, reset=False) -> dict:
@@ -344,11 +408,13 @@ class Context:
         self.clusters(scene, stream=stream)
 
     def lts_sweep(self, scene: Scene, old, dt_max, alpha=2.0, gravity=(0.0, 0.0, 0.0), zero_on_contact=True,
-                  hose=False, stream=None):
+                  hose=False, narrow=False, stream=None):
         """One local-time-stepping sweep: scene.state is the current snapshot
         and ``old`` (same shape) the old one; both are updated in place.
         Outputs in this context's buffers (pairs, n_pairs, t_coll, status,
-        ct_ab, cluster_id, n_clusters, active, t_global)."""
+        ct_ab, cluster_id, n_clusters, active, t_global); with narrow=True
+        also the narrow phase of the sweep's pairs at their start time (dmin,
+        pa, pb, tri_ab, flag, dmin32, contacts, contact_geom, n_contacts)."""
         import torch
         if self.cluster_id is None or self.cluster_id.numel() < scene.n:
             self.cluster_id = torch.zeros(max(scene.n, 1), dtype=torch.int32, device=self.device)
@@ -362,11 +428,21 @@ class Context:
         out = dem_lts_out(pairs=self.pairs.data_ptr(), max_pairs=self.max_pairs, n_pairs=self.n_pairs.data_ptr(),
                           t_coll=self.t_coll.data_ptr(), status=self.status.data_ptr(), tri_ab=self.ct_ab.data_ptr(),
                           cluster_id=self.cluster_id.data_ptr(), n_clusters=self.n_clusters.data_ptr(),
-                          active=self.active.data_ptr(), t_global=self.t_global.data_ptr())
+                          active=self.active.data_ptr(), t_global=self.t_global.data_ptr(),
+                          narrow=C.addressof(self.out) if narrow else None)
         dem_lts_sweep(self.h, scene.P, scene.state, old, prm, out, stream)
 
     def check(self, stream=None):
         dem_check(self.h, stream)
+
+    def set_wait_polls(self, polls: int):
+        dem_set_wait_polls(self.h, polls)
+
+    def trace(self, cap: int):
+        dem_trace(self.h, cap)
+
+    def trace_read(self, cap: int = 4096):
+        return dem_trace_read(self.h, cap)
 
     def stats(self, reset=False):
         return dem_get_stats(self.h, reset)

@@ -518,14 +518,17 @@ def floor_scene(seed: int = 0, n_side: int = 6, nq: int = 40, size: float = 24.0
 
 
 def settling_column(seed: int = 0, nside: int = 100, spacing: float = 2.2, jitter: float = 0.1,
-                    nq: int = 316, eps: float = 0.01, dt: float = 1e-3, vsig: float = 0.1,
+                    nq: int = None, eps: float = 0.01, dt: float = 1e-3, vsig: float = 0.1,
                     wsig: float = 0.1, lift: float = 0.005) -> Workload:
     """Throughput scale: a settling column of nside^3 icospheres of radius 1,
     half with 80 and half with 320 triangles (types shuffled), on a simple-cubic
     lattice of spacing ``spacing``, jitter uniform in +-``jitter`` per axis
     (horizontal only in the bottom layer, whose lowest points stay ``lift``
     above the floor), over a static floor of ``nq`` x ``nq`` quads (Morton
-    order) spanning the column's footprint.  The floor is the last particle.
+    order) spanning the column's footprint; by default nq keeps the quads of
+    the full column's 316 x 316 floor (nq = 316 for nside = 100, smaller
+    columns get a proportionally smaller floor).  The floor is the last
+    particle.
     v ~ N(0, vsig), w ~ N(0, wsig), dt = 1e-3, eps = 0.01.  ``meta['gravity']``
     is the acceleration a stepping loop applies between steps (free flight
     within a step is at constant velocity)."""
@@ -543,6 +546,8 @@ def settling_column(seed: int = 0, nside: int = 100, spacing: float = 2.2, jitte
     P[:, 2] += R + lift
     foot = (nside - 1) * spacing
     size = foot + 2 * (R + 2 * jitter + 1.0)
+    if nq is None:
+        nq = max(8, int(round(316 * size / (99 * spacing + 2 * (R + 2 * jitter + 1.0)))))
     floor = floor_grid(nq, size)
     types = rng.permutation(np.arange(n) % 2) + 1
     mesh_of = np.concatenate([types, [0]])

@@ -25,7 +25,21 @@ def _mixed_time_stamps(w, dt_max, seed):
     return old
 
 
-def _compare_sweeps(dem, w, old, prec, sweeps, dt_max, gravity, max_pairs=1 << 16, hose=False):
+def _compare_narrow(c, w, r, m):
+    """The sweep's narrow phase (pairs at their start time after the
+    consolidation) against the oracle's narrow phase on the oracle's
+    consolidated snapshot."""
+    wc = W.Workload(w.name, r["consolidated"], w.is_static, w.tri_off, w.tris, w.K, w.tol)
+    on = oracle.narrow_phase(wc, r["pairs"])
+    assert np.array_equal(c.flag[:m].cpu().numpy(), on["flag"])
+    assert np.array_equal(c.tri_ab[:m].cpu().numpy(), on["tri_ab"])
+    assert np.array_equal(c.dmin[:m].cpu().numpy(), on["dmin"])
+    nc = int(c.n_contacts.item())
+    assert np.array_equal(c.contacts[:nc].cpu().numpy(), on["contacts"])
+    return nc
+
+
+def _compare_sweeps(dem, w, old, prec, sweeps, dt_max, gravity, max_pairs=1 << 16, hose=False, narrow=False):
     import torch
     c = dem.Context(K=w.K, tol=w.tol, precision=prec, max_particles=max(w.n, 16), max_pairs=max_pairs,
                     max_contacts=1 << 16, max_triangles=w.n_tris)
@@ -34,11 +48,14 @@ def _compare_sweeps(dem, w, old, prec, sweeps, dt_max, gravity, max_pairs=1 << 1
     o_w = W.Workload(w.name, w.state.copy(), w.is_static, w.tri_off, w.tris, w.K, w.tol)
     o_old = old.copy()
     seen = set()
+    contacts = 0
     for s in range(sweeps):
-        c.lts_sweep(sc, g_old, dt_max, gravity=gravity, hose=hose)
+        c.lts_sweep(sc, g_old, dt_max, gravity=gravity, hose=hose, narrow=narrow)
         c.check()
         r = oracle.lts_sweep(o_w, o_old, dt_max, gravity=gravity, hose=hose)
         m = int(c.n_pairs.item())
+        if narrow:
+            contacts += _compare_narrow(c, w, r, m)
         assert np.array_equal(c.pairs[:m].cpu().numpy(), r["pairs"]), s
         assert np.array_equal(c.status[:m].cpu().numpy(), r["status"]), s
         assert np.array_equal(c.t_coll[:m].cpu().numpy(), r["t_coll"]), s
@@ -52,6 +69,8 @@ def _compare_sweeps(dem, w, old, prec, sweeps, dt_max, gravity, max_pairs=1 << 1
         assert st["advances"] == int(r["active"].sum())
         seen |= set(r["status"].tolist())
     c.close()
+    if narrow:
+        assert contacts > 0
     return seen
 
 
@@ -94,6 +113,20 @@ def test_lts_sweeps_with_hoses(dem, prec):
 def test_lts_sweeps_settling_column(dem):
     w = W.settling_column(0, nside=6, nq=32)
     _compare_sweeps(dem, w, w.state.copy(), 0, 8, 1e-3, (0.0, 0.0, -9.81))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_lts_sweeps_with_narrow_phase(dem, prec):
+    """Sweeps that also emit the narrow phase of their pairs (one launch with
+    the collision times): snapshots as without it, contacts as the oracle's
+    narrow phase on the consolidated snapshot."""
+    w = W.settling_column(0, nside=6, nq=32)
+    _compare_sweeps(dem, w, w.state.copy(), prec, 6, 1e-3, (0.0, 0.0, -9.81), narrow=True)
+    w = W.floor_scene(1)
+    _compare_sweeps(dem, w, w.state.copy(), prec, 4, 1e-3, (0.0, 0.0, -9.81), narrow=True)
+    w = W.lts_mixed_steps(0, n=1500)
+    old = _mixed_time_stamps(w, 4e-3, 1)
+    _compare_sweeps(dem, w, old, prec, 3, 4e-3, (0.0, 0.0, 0.0), narrow=True)
 
 
 def test_lts_sweeps_in_a_cuda_graph(dem):

@@ -10,6 +10,7 @@ already run every other test; it passes alone and after the other tests.
 import numpy as np
 import pytest
 
+import oracle
 from paper_2309_15417_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -70,3 +71,42 @@ def test_noalloc_rejects_oversize_and_reports_truncation(dem):
     full = got[:, 0] < last
     assert np.array_equal(got[full], ref[:int(full.sum())])
     assert {tuple(r) for r in got[~full]} <= {tuple(r) for r in ref[ref[:, 0] == last]}
+
+
+def test_noalloc_matches_the_oracle_with_static_particles(dem):
+    """A static floor and a static post among moving particles (static box
+    tests, the static member written second): the oracle's candidate set, on
+    two calls in a row, and no error in the library's error word."""
+    dem.dem_noalloc_check()  # clear what earlier calls left
+    w = W.floor_scene(0)
+    ref = oracle.broad_phase(w)
+    assert (w.is_static[ref[:, 1]] == 1).any()
+    for _ in range(2):
+        got, m = _noalloc(dem, w)
+        assert m == len(ref)
+        assert np.array_equal(got, ref)
+    assert dem.dem_noalloc_check() == dem.DEM_OK
+
+
+def test_noalloc_check_reports_device_conditions(dem):
+    """The context-free error readback: a static particle whose triangle
+    range runs past the end of the triangles is an index error (its box is
+    skipped, nothing is read out of range); a capacity smaller than the
+    candidate count is a capacity error; the readback clears the word."""
+    import torch
+    dem.dem_noalloc_check()
+    w = W.floor_scene(0)
+    assert w.is_static[0] == 1
+    off = w.tri_off.copy()
+    off[1] = w.n_tris + 4096
+    sc = dem.Scene.from_workload(w)
+    sc.tri_off.copy_(torch.from_numpy(off).cuda())
+    pairs = torch.zeros((1 << 12, 2), dtype=torch.int32, device="cuda")
+    n = torch.zeros(1, dtype=torch.int64, device="cuda")
+    assert dem.dem_build_candidates_noalloc(sc.P, pairs, 1 << 12, n) == dem.DEM_OK
+    assert dem.dem_noalloc_check() == dem.DEM_ERR_INDEX
+    assert dem.dem_noalloc_check() == dem.DEM_OK
+    _noalloc(dem, W.dense_packing(0), cap=100)
+    assert dem.dem_noalloc_check() == dem.DEM_ERR_CAPACITY
+    _noalloc(dem, W.small_icospheres(1))
+    assert dem.dem_noalloc_check() == dem.DEM_OK
