@@ -1,25 +1,34 @@
 #!/usr/bin/env python
-"""Benchmark of the space-time contact-detection step on GB300.
+"""Benchmark of the space-time contact-detection path on GB300.
 
-One step = one pass of the whole path over the dense packing of 1,000
-icospheres (320 triangles, radius 1; jittered simple-cubic lattice at volume
-fraction 0.5, jitter +-0.1; dt = 1e-4, eps = 0.02; K = 8 samples, bisection to
-1e-3 of the step): candidate pairs -> narrow phase at the pair start ->
-collision times -> clusters of the candidate graph, all four through the C-ABI
-library, FP32 distances with binary64 recomputation.
-
-Metric: triangle-pair distance checks per second as the method defines them
-(per candidate pair T_i * T_j for the narrow phase plus T_i * T_j for every
-pair-distance evaluation of the collision-time search), plus particle-steps
-per second, and the same step with every distance in FP64 for comparison.
+Headline workload: the settling column -- 100^3 icospheres (half 80, half 320
+triangles, radius 1) on a jittered lattice of spacing 2.2 over a static floor
+of 316 x 316 quads (199,712 triangles); eps = 0.01, dt_max = 1e-3, gravity
+(0, 0, -9.81).  One step = one local-time-stepping sweep through the C-ABI
+(dem_lts_sweep): particle steps, candidate pairs (broad phase), clusters,
+consolidation, the narrow phase of every pair at its start time and the
+collision-time search (K = 8 samples, bisection to 1e-3 of the step) in one
+pair-kernel launch, masking, advance and roll-over, with a stand-in for the
+collision update (particles in contact stop).  The step is captured once in a
+CUDA graph and replayed; the state evolves from step to step.  The same steps
+run again from the same snapshots with every distance in FP64 and the
+outputs are compared bit for bit.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+value = particle-steps per second (particle advances: every particle that
+moves to a new time stamp in a sweep is one particle-step).  The JSON line
+also carries the triangle-pair checks per second as the method defines them
+and as performed after culling, the FP32 error of every FP32-kept output,
+the roofline of the pair kernel against measured FP32 / FP64 FMA peaks, and
+further legs (dense packing, uneven meshes, a search-heavy packing, the
+100,000-particle mixed-step cycle, narrowing against sampling).
+
 N > 1 (launched with torch.distributed.run): every rank runs an independent
-replica (its own seeded packing) -- weak scaling, no collective on the data
-path; value = checks of all ranks / max time over ranks.
---impl reference: the FP64 CPU oracle on this machine's cores, same workload,
-each step on a bounded sample of the candidate pairs.
+replica (its own seeded column) -- weak scaling, no collective on the data
+path; value = particle-steps of all ranks / max time over ranks.
+--impl reference: the FP64 CPU oracle on this machine's cores, each step one
+sweep of a sub-column (6^3 particles over its floor patch).
 """
 from __future__ import annotations
 
@@ -39,26 +48,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "triangle-pair distance checks/sec and particle-steps/sec at 1 GB300, FP32+fixup vs all-FP64"
-UNIT = "triangle-pair checks/s"
-WORKLOAD = ("dense packing: 1000 icospheres (subdivision 2, 320 triangles, r=1), jittered simple-cubic "
-            "lattice at volume fraction 0.5 (jitter +-0.1), v~N(0,0.2), w~N(0,0.2), dt=1e-4, eps=0.02; "
-            "K=8 samples then bisection to 1e-3 of the step; FP32 distances with FP64 recomputation")
+UNIT = "particle-steps/s"
+CHECKS = "triangle-pair checks/s"
+WORKLOAD = ("settling column: 100^3 icospheres (half 80, half 320 triangles, r=1), lattice spacing 2.2, "
+            "jitter +-0.1, over a static 316x316-quad floor (199,712 triangles); eps=0.01, dt_max=1e-3, "
+            "gravity (0,0,-9.81), v~N(0,0.1), w~N(0,0.1); one step = one local-time-stepping sweep "
+            "(candidates, clusters, consolidation, narrow phase + collision times with K=8 samples and "
+            "bisection to 1e-3 of the step, masking, advance); FP32 distances with FP64 recomputation")
 L2_BYTES = 129 * 1024 * 1024
 FLUSH_BYTES = 512 * 1024 * 1024
-
-# FP32 operations per unit of work of the collision-time kernel (FMA = 2), counted
-# from the formulas in csrc/geom.cuh and csrc/pairs.cu on their common path:
-#   triangle-sphere test: 3 sub, |d|^2 (mul + 2 fma), 2 add, 1 mul, 1 compare  -> 12
-#   group-sphere test: as above plus sqrt                                     -> 13
-#   triangle-pair distance: 6 segment-triangle crossing tests (31 each, no crossing),
-#   6 vertex-triangle closest points (~90 each, face region), 9 segment-segment
-#   closest points (~65 each)                                                -> 1311
-F_SPHERE = 12
-F_GROUP = 13
-F_DIST32 = 1311
-# FP32 peak: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz maximum SM clock
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "detect_kernel_dense1000.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pair_kernel_settling_column.md")
+REF_SIDE = 6  # sub-column of the oracle samples
 
 
 def parse():
@@ -68,12 +68,12 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--seed", type=int, default=0)
-    p.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison")
+    p.add_argument("--nside", type=int, default=100, help="particles per side of the settling column")
+    p.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 run of the same steps")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
-    p.add_argument("--cpu-sample", type=int, default=96, help="candidate pairs per oracle sample")
-    p.add_argument("--no-lts", action="store_true", help="skip the local-time-stepping measurements")
-    p.add_argument("--no-narrowing", action="store_true", help="skip the narrowing-vs-sampling comparison")
-    p.add_argument("--column-sweeps", type=int, default=50, help="sweeps of the settling column per replay")
+    p.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    p.add_argument("--no-legs", action="store_true", help="skip the further legs")
+    p.add_argument("--legs", default="dense,uneven,search,lts,narrowing", help="further legs to run")
     return p.parse_args()
 
 
@@ -137,11 +137,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# ------------------------------------------------------------------ GPU arm
+# ------------------------------------------------------------------ roofline inputs
 
 def _profile_traffic():
-    """DRAM bytes per launch of the fused pair kernel from the committed
-    ncu summary, if it was taken on the current kernel source."""
+    """DRAM bytes per launch of the sweep's pair kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
     try:
         txt = open(PROFILE_SUMMARY).read()
     except OSError:
@@ -150,269 +150,580 @@ def _profile_traffic():
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]+)", txt)
     if not m or not h:
         return None
-    src = open(os.path.join(ROOT, "paper_2309_15417_gb300", "csrc", "pair_kernel.cuh"), "rb").read()
-    geo = open(os.path.join(ROOT, "paper_2309_15417_gb300", "csrc", "geom.cuh"), "rb").read()
-    if hashlib.sha256(src + geo).hexdigest() != h.group(1):
+    if kernel_source_hash() != h.group(1):
         return None
     return float(m.group(1))
 
 
-def run_step(ctx, sc, ev=None, fused=True):
-    """One detection step: candidates, narrow phase at the pair start and
-    collision times (fused: one dem_detect launch; else the two calls),
-    clusters.  Optional events: before the narrow phase, between the two calls
-    (not fused), after the collision times."""
-    ctx.build_candidates(sc)
-    if ev:
-        ev[0].record()
-    if fused:
-        ctx.detect(sc)
-        if ev:
-            ev[1].record()
-    else:
-        ctx.narrow_phase(sc)
-        if ev:
-            ev[1].record()
-        ctx.collision_times(sc)
-    if ev:
-        ev[2].record()
-    ctx.clusters(sc)
+def kernel_source_hash():
+    csrc = os.path.join(ROOT, "paper_2309_15417_gb300", "csrc")
+    src = open(os.path.join(csrc, "pair_kernel.cuh"), "rb").read()
+    geo = open(os.path.join(csrc, "geom.cuh"), "rb").read()
+    return hashlib.sha256(src + geo).hexdigest()
 
 
-def gpu_arm(args, rank, world, local):
-    import torch
-    from paper_2309_15417_gb300 import dem
+def _rot(q):
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def performed_population(w, state, pairs, n_sample, seed, cap=200_000):
+    """Triangle pairs that the pair kernel evaluates in FP32 for a random
+    sample of candidate pairs: those whose triangle bounding spheres
+    (centroid, largest vertex distance) come within eps_pair + delta at the
+    particles' current poses (delta = the motion bound over the pair's step:
+    the kernel's collection threshold at the pair start).  Rows of 18 floats
+    (triangle a, triangle b), coordinates relative to particle i's centre."""
     from paper_2309_15417_gb300 import workloads as W
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(len(pairs), min(n_sample, len(pairs)), replace=False)
+    rows = []
+    total = 0
+    for k in idx:
+        i, j = int(pairs[k, 0]), int(pairs[k, 1])
+        X = {p: state[W.F_X:W.F_Z + 1, p] for p in (i, j)}
+        V = {}
+        for p in (i, j):
+            R = _rot(state[W.F_QW:W.F_QZ + 1, p])
+            t = w.tris[:, w.tri_off[p]:w.tri_off[p + 1], :3].astype(np.float64)  # (3, T, 3)
+            V[p] = np.einsum("ab,stb->sta", R, t) + X[p] - X[i]
+        eps = state[W.F_EPS, i] + state[W.F_EPS, j]
+        vi, vj = (np.linalg.norm(state[W.F_VX:W.F_VZ + 1, p]) for p in (i, j))
+        wi, wj = (np.linalg.norm(state[W.F_WX:W.F_WZ + 1, p]) for p in (i, j))
+        T = min(state[W.F_DT, i], state[W.F_DT, j])
+        delta = (vi + vj + wi * state[W.F_RADIUS, i] + wj * state[W.F_RADIUS, j]) * T
+        ca, cb = V[i].mean(axis=0), V[j].mean(axis=0)  # (T, 3) centroids
+        ra = np.linalg.norm(V[i] - ca[None], axis=2).max(axis=0)
+        rb = np.linalg.norm(V[j] - cb[None], axis=2).max(axis=0)
+        # a large mesh (the floor): only triangles near particle i can pass
+        near = np.linalg.norm(cb, axis=1) - rb <= state[W.F_RADIUS, i] + eps + delta
+        jb = np.nonzero(near)[0]
+        g = np.linalg.norm(ca[:, None, :] - cb[None, jb, :], axis=2) - ra[:, None] - rb[None, jb]
+        a_idx, b_idx = np.nonzero(g <= eps + delta)
+        b_idx = jb[b_idx]
+        if not len(a_idx):
+            continue
+        A = V[i][:, a_idx].transpose(1, 0, 2).reshape(-1, 9)
+        B = V[j][:, b_idx].transpose(1, 0, 2).reshape(-1, 9)
+        rows.append(np.concatenate([A, B], axis=1).astype(np.float32))
+        total += len(a_idx)
+        if total >= cap:
+            break
+    return np.concatenate(rows)[:cap] if rows else np.zeros((0, 18), np.float32)
 
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    w = W.dense_packing(args.seed + rank)
-    sc = dem.Scene.from_workload(w, device=dev)
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    mk = lambda prec: dem.Context(K=w.K, tol=w.tol, precision=prec, max_particles=w.n, max_pairs=1 << 16,
-                                  max_contacts=1 << 20, device=dev)
 
-    def measure(prec, steps, warmup, detail, fused=True):
-        """Stage split from direct calls (CUDA events between the calls), then
-        the timed steps as replays of the step captured in a CUDA graph."""
-        ctx = mk(prec)
-        for _ in range(warmup):
-            run_step(ctx, sc, fused=fused)
-        ctx.check()
-        ctx.stats(reset=True)
-        # stage split: direct calls
-        nsplit = max(3, min(steps, 10))
-        E = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(nsplit)]
-        for k in range(nsplit):
-            flush.fill_(float(k))
-            e = E[k]
-            e[0].record()
-            run_step(ctx, sc, ev=(e[1], e[2], e[3]), fused=fused)
-            e[4].record()
+def flops_per_distance(dem, w, state, pairs, seed, n_sample=64):
+    """Average FP32 operations of one triangle-pair distance (FMA = 2) over the
+    sampled population, counted by the library on the formulas the pair
+    kernel runs."""
+    import torch
+    pop = performed_population(w, state, pairs, n_sample, seed)
+    if not len(pop):
+        return None, 0
+    ops = dem.dem_count_dist_flops(torch.from_numpy(pop).cuda())
+    return float(ops.double().mean().item()), int(len(pop))
+
+
+def measured_peaks(dem, dev):
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    fp32 = dem.dem_probe_fma_peak(0, 1 << 16)
+    fp64 = dem.dem_probe_fma_peak(1, 1 << 12)
+    return {"fp32_tflops": fp32 / 1e12, "fp64_tflops": fp64 / 1e12, "sms": int(props.multi_processor_count),
+            "source": "dem_probe_fma_peak (include/dem_probe.h): 8 FMA chains per thread, 64 warps per SM, "
+                      "best of 3 CUDA-event-timed runs"}
+
+
+# ------------------------------------------------------------------ the sweep steps
+
+class SweepRun:
+    """K sweeps of the settling column replayed from one captured sweep."""
+
+    def __init__(self, dem, w, dev, prec):
+        import torch
+        self.dem, self.w, self.dev, self.prec = dem, w, dev, prec
+        self.sc = dem.Scene.from_workload(w, device=dev)
+        self.old = self.sc.state.clone()
+        self.ctx = dem.Context(K=w.K, tol=w.tol, precision=prec, max_particles=w.n, max_pairs=1 << 21,
+                               max_contacts=1 << 22, max_triangles=w.n_tris, device=dev)
+        self.g = None
+        self.torch = torch
+
+    def sweep(self):
+        self.ctx.lts_sweep(self.sc, self.old, 1e-3, gravity=(0.0, 0.0, -9.81), narrow=True)
+
+    def capture(self):
+        torch = self.torch
         torch.cuda.synchronize()
-        ct_ms = [e[2].elapsed_time(e[3]) for e in E]
-        nw_ms = [e[1].elapsed_time(e[2]) for e in E]
-        det_ms = [e[1].elapsed_time(e[3]) for e in E]
-        direct_ms = [e[0].elapsed_time(e[4]) for e in E]
-        # the whole step as one CUDA graph
-        g = torch.cuda.CUDAGraph()
-        side = torch.cuda.Stream()
-        side.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(side):
-            run_step(ctx, sc, fused=fused)
-        torch.cuda.current_stream().wait_stream(side)
-        torch.cuda.synchronize()
-        l0 = ctx.stats()["kernel_launches"]
-        with torch.cuda.graph(g):
-            run_step(ctx, sc, fused=fused)
-        launches_step = ctx.stats()["kernel_launches"] - l0
-        g.replay()
-        torch.cuda.synchronize()
-        ctx.check()
-        ctx.stats(reset=True)
-        G = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-        clk = ClockSampler(local) if detail else None
-        if clk:
-            clk.start()
-        t0 = time.perf_counter()
+        l0 = self.ctx.stats()["kernel_launches"]
+        self.ctx.trace(256)
+        self.g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.g):
+            self.sweep()
+        self.launches = self.ctx.stats()["kernel_launches"] - l0
+
+    def outputs(self):
+        """Host copies of one step's outputs."""
+        c = self.ctx
+        m = int(c.n_pairs.item())
+        nc = int(c.n_contacts.item())
+        g = lambda t: t.cpu().numpy().copy()
+        return dict(m=m, nc=nc, pairs=g(c.pairs[:m]), status=g(c.status[:m]), t_coll=g(c.t_coll[:m]),
+                    ct_ab=g(c.ct_ab[:m]), flag=g(c.flag[:m]), dmin=g(c.dmin[:m]), tri_ab=g(c.tri_ab[:m]),
+                    dmin32=g(c.dmin32[:m]), contacts=g(c.contacts[:min(nc, c.max_contacts)]),
+                    geom=g(c.contact_geom[:min(nc, c.max_contacts)]), ids=g(c.cluster_id[:self.w.n]))
+
+    def run(self, steps, flush, clocks=None, keep=True):
+        torch = self.torch
+        E = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+        step_ms, trace, stats, outs = [], [], [], []
+        self.ctx.stats(reset=True)
+        if clocks:
+            clocks.start()
         for k in range(steps):
-            flush.fill_(float(k))  # L2 flush between steps, outside the timed events
-            G[k][0].record()
-            g.replay()
-            G[k][1].record()
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        if world > 1:
-            torch.distributed.barrier()
-        clocks = clk.stop() if clk else None
-        ctx.check()
-        st = ctx.stats(reset=True)
-        st["kernel_launches"] = launches_step * steps
-        step_ms = [e[0].elapsed_time(e[1]) for e in G]
-        return ctx, dict(step_ms=step_ms, ct_ms=ct_ms, nw_ms=nw_ms, det_ms=det_ms, stats=st, wall=wall,
-                         clocks=clocks, direct_ms=direct_ms, graph=g)
+            flush.fill_(float(k))  # L2 flush between steps, outside the step's events
+            E[k][0].record()
+            self.g.replay()
+            E[k][1].record()
+            torch.cuda.synchronize()
+            step_ms.append(E[k][0].elapsed_time(E[k][1]))
+            trace.append(self.ctx.trace_read())
+            stats.append(self.ctx.stats(reset=True))
+            if keep:
+                outs.append(self.outputs())
+        clk = clocks.stop() if clocks else None
+        self.ctx.check()
+        return dict(step_ms=step_ms, trace=trace, stats=stats, outs=outs, clocks=clk)
 
-    ctx32, r32 = measure(dem.DEM_PREC_FP32_FIXUP, args.steps, args.warmup, True)
+    def close(self):
+        self.g = None
+        self.ctx.close()
+
+
+def trace_split(trace):
+    """Mean milliseconds per step of each launch group."""
+    from paper_2309_15417_gb300 import dem
+    acc = {}
+    for rec in trace:
+        per = {}
+        for site, ms in rec:
+            per[site] = per.get(site, 0.0) + ms
+        for site, ms in per.items():
+            acc.setdefault(dem.TRACE_SITES[site], []).append(ms)
+    return {k: float(np.mean(v)) for k, v in acc.items()}
+
+
+def compare_runs(o32, o64):
+    """Bit-identity of every integer and binary64 output, step by step, and
+    the FP32 error of the FP32-kept values (R = 1)."""
+    same = len(o32) == len(o64)
+    ed, ep, emin = [], [], []
+    for a, b in zip(o32, o64):
+        for key in ("pairs", "status", "t_coll", "ct_ab", "flag", "dmin", "tri_ab", "contacts", "ids"):
+            if not (a[key].shape == b[key].shape and np.array_equal(a[key], b[key])):
+                same = False
+        if a["nc"] != b["nc"] or a["m"] != b["m"]:
+            same = False
+        if a["nc"] == b["nc"] and np.array_equal(a["contacts"], b["contacts"]) and len(a["geom"]):
+            ed.append(np.abs(a["geom"][:, 0] - b["geom"][:, 0]))
+            ep.append(np.maximum(np.linalg.norm(a["geom"][:, 1:4] - b["geom"][:, 1:4], axis=1),
+                                 np.linalg.norm(a["geom"][:, 4:7] - b["geom"][:, 4:7], axis=1)))
+        fin = np.isfinite(b["dmin"])
+        if a["m"] == b["m"]:
+            emin.append(np.abs(a["dmin32"][fin].astype(np.float64) - b["dmin"][fin]))
+    st = lambda x: ({"max_abs_over_R": float(np.concatenate(x).max()),
+                     "p99_abs_over_R": float(np.percentile(np.concatenate(x), 99))}
+                    if x and sum(len(v) for v in x) else None)
+    return same, {"pair_minimum_fp32_before_fixup": st(emin), "contact_distance": st(ed),
+                  "contact_points": st(ep),
+                  "note": "against the all-FP64 run's identical keys; contact points of (near-)parallel "
+                          "triangles are not unique, so a point difference can be another valid point"}
+
+
+def column_leg(args, dem, W, dev, rank, world, peaks):
+    import torch
+    t0 = time.time()
+    w = W.settling_column(args.seed + rank, nside=args.nside)
+    gen_s = time.time() - t0
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     K = args.steps
-    checks_step = r32["stats"]["method_checks"] / K
-    t_total = sum(r32["step_ms"]) / 1e3
-    n_pairs = int(ctx32.n_pairs.item())
-
-    # dominant kernel (the fused pair kernel of dem_detect): counters of one
-    # call alone, duration from the events around dem_detect
-    ctx32.stats(reset=True)
-    run_step(ctx32, sc)
+    r32 = SweepRun(dem, w, dev, dem.DEM_PREC_FP32_FIXUP)
+    for _ in range(args.warmup):
+        r32.sweep()
+    r32.ctx.check()
     torch.cuda.synchronize()
-    ctx32.stats(reset=True)
-    ctx32.detect(sc)
-    st_ct = ctx32.stats(reset=True)
-    ct_flops = F_SPHERE * st_ct["sphere_tests"] + F_GROUP * st_ct["group_tests"] + F_DIST32 * st_ct["dist_fp32"]
-    ct_ms = float(np.mean(r32["det_ms"]))
-    achieved = ct_flops / (ct_ms / 1e3) / 1e12
-    # the same step through the four separate calls (narrow phase and
-    # collision times as two launches)
-    ctx4, r4 = measure(dem.DEM_PREC_FP32_FIXUP, max(3, min(K, 10)), 2, False, fused=False)
-    four_call = {"ms_per_step": float(np.mean(r4["step_ms"])), "narrow_ms": float(np.mean(r4["nw_ms"])),
-                 "collision_times_ms": float(np.mean(r4["ct_ms"]))}
-    ctx4.close()
-
-    # FP32 error against FP64 (pair minima), R = 1
-    fin = torch.isfinite(ctx32.dmin[:n_pairs])
-    d64 = ctx32.dmin[:n_pairs][fin]
-    d32 = ctx32.dmin32[:n_pairs][fin].double()
-    err = (d32 - d64).abs().cpu().numpy()
-    fp32_err = {"max_abs_over_R": float(err.max()) if err.size else 0.0,
-                "p99_abs_over_R": float(np.percentile(err, 99)) if err.size else 0.0,
-                "output": "pair minimum distance"}
-
+    cur0, old0 = r32.sc.state.clone(), r32.old.clone()
+    state_np = cur0.cpu().numpy()
+    r32.capture()
+    if world > 1:
+        torch.distributed.barrier()
+    res32 = r32.run(K, flush, clocks=ClockSampler(dev.index) if rank == 0 else None, keep=not args.no_fp64)
+    if world > 1:
+        torch.distributed.barrier()
+    t32 = sum(res32["step_ms"]) / 1e3
+    st = {k: sum(s[k] for s in res32["stats"]) for k in res32["stats"][0]}
+    split = trace_split(res32["trace"])
+    pairs_last = res32["outs"][-1]["pairs"] if res32["outs"] else r32.ctx.pairs[:int(r32.ctx.n_pairs.item())].cpu().numpy()
+    final32 = (r32.sc.state.cpu().numpy(), r32.old.cpu().numpy())
+    launches = r32.launches
+    # the roofline of the pair kernel (narrow phase + collision times of the sweep)
+    F, npop = flops_per_distance(dem, w, state_np, pairs_last, args.seed) if rank == 0 else (None, 0)
+    pk_ms = split.get("pair kernel")
+    roof = None
+    if F and pk_ms:
+        flops = st["dist_fp32"] / K * F
+        ach = flops / (pk_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "pair_kernel<FP32, narrow phase + collision times> of the sweep",
+                "achieved": ach, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+                "frac": ach / peaks["fp32_tflops"], "traffic": _profile_traffic(),
+                "peak_source": "measured: " + peaks["source"],
+                "flops_per_launch": flops, "ms_per_launch": pk_ms,
+                "F_flops_per_distance": F, "F_population": f"{npop} triangle pairs passing the triangle-sphere "
+                                                           "test at the pair start, 64 sampled candidate pairs",
+                "performed_fp32_distances_per_launch": st["dist_fp32"] / K,
+                "recipe_peak_tflops": peaks["sms"] * 128 * 2 * 2.07e9 / 1e12}
+    e2e = None
+    if not args.no_e2e:
+        # restore the snapshots after the timed steps and run end to end from host buffers
+        e2e = e2e_leg(dem, r32, min(K, 5))
+    r32.close()
+    del r32
+    torch.cuda.empty_cache()
     fp64 = None
     if not args.no_fp64:
-        k64 = max(3, min(K, 5))
-        ctx64, r64 = measure(dem.DEM_PREC_FP64, k64, 2, False)
-        t64 = sum(r64["step_ms"]) / 1e3
-        c64 = r64["stats"]["method_checks"] / k64
-        # same contact set and collision times in both precisions
-        m = int(ctx64.n_pairs.item())
-        same = (m == n_pairs and torch.equal(ctx64.flag[:m], ctx32.flag[:m])
-                and torch.equal(ctx64.status[:m], ctx32.status[:m])
-                and torch.equal(ctx64.t_coll[:m], ctx32.t_coll[:m])
-                and int(ctx64.n_contacts.item()) == int(ctx32.n_contacts.item())
-                and torch.equal(ctx64.contacts[:int(ctx64.n_contacts.item())],
-                                ctx32.contacts[:int(ctx32.n_contacts.item())]))
-        fp64 = {"value": c64 * k64 / t64, "unit": UNIT, "ms_per_step": t64 * 1e3 / k64,
-                "speedup_fp32_fixup_over_fp64": (checks_step * K / t_total) / (c64 * k64 / t64),
-                "results_identical": bool(same), "steps": k64}
-        if same:
-            # FP32 error of the contact list: the FP32+fixup run keeps the FP32
-            # distance and points of contacts outside the band; the FP64 run
-            # has the same contact keys with binary64 geometry (R = 1).  The
-            # points of (near-)parallel triangles are not unique, so a point
-            # difference can also be a different valid point.
-            nc = int(ctx32.n_contacts.item())
-            g32, g64 = ctx32.contact_geom[:nc], ctx64.contact_geom[:nc]
-            ed = (g32[:, 0] - g64[:, 0]).abs().cpu().numpy()
-            ep = torch.maximum((g32[:, 1:4] - g64[:, 1:4]).norm(dim=1),
-                               (g32[:, 4:7] - g64[:, 4:7]).norm(dim=1)).cpu().numpy()
-            if nc:
-                fp32_err["contact_distance"] = {"max_abs_over_R": float(ed.max()),
-                                                "p99_abs_over_R": float(np.percentile(ed, 99))}
-                fp32_err["contact_points"] = {"max_abs_over_R": float(ep.max()),
-                                              "p99_abs_over_R": float(np.percentile(ep, 99)),
-                                              "note": "largest of |pa32 - pa64|, |pb32 - pb64| per contact"}
-        ctx64.close()
-
-    # end to end through the public API from pinned host buffers
-    e2e = e2e_arm(dem, w, ctx32, sc, max(3, min(K, 10)), r32["graph"])
-
-    res = dict(value_local=checks_step * K, time_local=t_total, particles=w.n, K=K, n_pairs=n_pairs,
-               ms=float(np.mean(r32["step_ms"])), ct_ms=ct_ms, four_call=four_call,
-               direct_ms=float(np.mean(r32["direct_ms"])),
-               achieved=achieved, ct_flops=ct_flops, st_ct=st_ct, clocks=r32["clocks"], wall=r32["wall"],
-               launches=r32["stats"]["kernel_launches"], fp32_err=fp32_err, fp64=fp64, e2e=e2e,
-               checks_step=checks_step, stats_step={k: v / K for k, v in r32["stats"].items()})
-    ctx32.close()
-    del sc, flush
+        r64 = SweepRun(dem, w, dev, dem.DEM_PREC_FP64)
+        r64.sc.state.copy_(cur0)
+        r64.old.copy_(old0)
+        r64.sweep()  # warm-up outside the capture (restored below)
+        r64.ctx.check()
+        r64.sc.state.copy_(cur0)
+        r64.old.copy_(old0)
+        r64.capture()
+        res64 = r64.run(K, flush, keep=True)
+        final64 = (r64.sc.state.cpu().numpy(), r64.old.cpu().numpy())
+        same, err = compare_runs(res32["outs"], res64["outs"])
+        same = same and np.array_equal(final32[0], final64[0]) and np.array_equal(final32[1], final64[1])
+        t64 = sum(res64["step_ms"]) / 1e3
+        st64 = {k: sum(s[k] for s in res64["stats"]) for k in res64["stats"][0]}
+        fp64 = {"ms_per_step": t64 * 1e3 / K, "value": st64["advances"] / t64, "unit": UNIT,
+                "pair_kernel_ms": trace_split(res64["trace"]).get("pair kernel"),
+                "speedup_fp32_fixup_over_fp64": t64 / t32, "results_identical": bool(same),
+                "compared": "every step's pairs, statuses, collision times and pairs, clusters, narrow-phase "
+                            "flags, minima and closest pairs, contact keys; final current and old snapshots"}
+        r64.close()
+        del r64
+        torch.cuda.empty_cache()
+    else:
+        err = None
+    del flush
     torch.cuda.empty_cache()
-    # the further legs (not part of the timed step) run on a single GPU only,
-    # so that a multi-GPU run does not hold its GPUs for them
-    if world == 1 and not args.no_lts:
-        res["lts"] = lts_legs(args, dem, W, dev)
-    if world == 1 and not args.no_narrowing:
-        res["narrowing"] = narrowing_leg(args, dem, W, dev)
-    return res
+    return dict(w=w, K=K, t=t32, st=st, split=split, roof=roof, fp64=fp64, fp32_err=err, e2e=e2e,
+                clocks=res32["clocks"], launches=launches, step_ms=res32["step_ms"], gen_s=gen_s,
+                pairs_per_step=float(np.mean([o["m"] for o in res32["outs"]])) if res32["outs"] else None,
+                contacts_per_step=float(np.mean([o["nc"] for o in res32["outs"]])) if res32["outs"] else None)
 
 
-def lts_measure(dem, w, old_np, prec, sweeps, reps, dt_max, gravity, dev, max_pairs, hose=False):
-    """Sweeps of the local-time-stepping cycle captured in one CUDA graph and
-    replayed `reps` times from the same starting snapshots (restored between
-    replays, outside the timed events).  Returns times, counters and the final
-    snapshots."""
+def e2e_leg(dem, run, steps):
+    """Through the public API (dem_lts_sweep, direct calls) from pinned host
+    buffers: every step copies the two snapshots (the step's inputs) host to
+    device, sweeps, and copies the new snapshots and every output back.  The
+    meshes stay resident (model data that does not change between steps)."""
     import torch
-    sc = dem.Scene.from_workload(w, device=dev)
-    old = torch.from_numpy(old_np).to(dev)
-    cur0, old0 = sc.state.clone(), old.clone()
-    ctx = dem.Context(K=w.K, tol=w.tol, precision=prec, max_particles=w.n, max_pairs=max_pairs,
-                      max_contacts=1 << 16, max_triangles=w.n_tris, device=dev)
-    ctx.lts_sweep(sc, old, dt_max, gravity=gravity, hose=hose)  # first call outside the capture
+    c = run.ctx
+    pin = lambda t: torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+    h_cur, h_old = pin(run.sc.state), pin(run.old)
+    h_cur.copy_(run.sc.state)
+    h_old.copy_(run.old)
+    m_cap = c.max_pairs
+    outs = [c.pairs, c.n_pairs, c.status, c.t_coll, c.ct_ab, c.flag, c.dmin, c.tri_ab, c.cluster_id, c.n_clusters,
+            c.active, c.n_contacts]
+    h_outs = [pin(t) for t in outs]
+    h_cg, h_ck = pin(c.contact_geom), pin(c.contacts)
+    times, bo, adv = [], 0, 0
+    bi = 2 * h_cur.numel() * 8
+    c.stats(reset=True)
+    for k in range(steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run.sc.state.copy_(h_cur, non_blocking=True)
+        run.old.copy_(h_old, non_blocking=True)
+        run.sweep()
+        h_cur.copy_(run.sc.state, non_blocking=True)
+        h_old.copy_(run.old, non_blocking=True)
+        torch.cuda.synchronize()
+        m = int(h_outs[1][0])
+        nc = min(int(h_outs[11][0]), c.max_contacts)
+        b = 2 * h_cur.numel() * 8
+        for t, h in zip(outs, h_outs):  # outputs, only their filled parts
+            n = m if t.shape[0] == m_cap else t.shape[0]
+            h[:n].copy_(t[:n], non_blocking=True)
+            b += n * t[:1].numel() * t.element_size()
+        h_ck[:nc].copy_(c.contacts[:nc], non_blocking=True)
+        h_cg[:nc].copy_(c.contact_geom[:nc], non_blocking=True)
+        b += nc * (12 + 56)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st = c.stats(reset=True)
+        if k >= 1:
+            times.append(dt)
+            adv += st["advances"]
+            bo += b
+    c.check()
+    T = float(np.sum(times))
+    return {"value": adv / T, "unit": UNIT, "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo / steps),
+            "ms_per_step": 1e3 * T / steps, "steps": steps,
+            "path": "per step: pinned host -> device copy of the current and old snapshots, dem_lts_sweep "
+                    "(direct call), device -> pinned host copy of the new snapshots, pairs, statuses, "
+                    "collision times, narrow-phase outputs, contacts, clusters and the active set; meshes "
+                    "resident"}
+
+
+# ------------------------------------------------------------------ further legs
+
+def step_graph(dem, ctx, sc):
+    """candidates -> detect -> clusters captured in one CUDA graph."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        ctx.step_fused(sc)
+    torch.cuda.current_stream().wait_stream(side)
     torch.cuda.synchronize()
-    ctx.check()
-    l0 = ctx.stats()["kernel_launches"]
+    ctx.trace(64)
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
-        for _ in range(sweeps):
-            ctx.lts_sweep(sc, old, dt_max, gravity=gravity, hose=hose)
-    launches = ctx.stats()["kernel_launches"] - l0
-    ms, st = [], {}
-    for r in range(reps + 1):  # the first replay warms up
-        sc.state.copy_(cur0)
-        old.copy_(old0)
-        torch.cuda.synchronize()
-        ctx.stats(reset=True)
+        ctx.step_fused(sc)
+    return g
+
+
+def time_graph(ctx, g, steps, flush):
+    """Mean step and pair-kernel milliseconds, counters per step, and the
+    pair kernel's load balance (mean / max CTA busy time, averaged)."""
+    import torch
+    ms, pk, bal = [], [], []
+    acc = {}
+    ctx.stats(reset=True)
+    for k in range(steps + 1):
+        flush.fill_(float(k))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         g.replay()
         e1.record()
         torch.cuda.synchronize()
-        if r:
-            ms.append(e0.elapsed_time(e1))
-            for k, v in ctx.stats(reset=True).items():  # counters of every timed replay
-                st[k] = st.get(k, 0) + v
+        st = ctx.stats(reset=True)
+        if k == 0:
+            continue
+        ms.append(e0.elapsed_time(e1))
+        pk.append(sum(m for s, m in ctx.trace_read() if s == 2))
+        if st["ctas"] and st["cta_busy_ns_max"]:
+            bal.append(st["cta_busy_ns"] / st["ctas"] / st["cta_busy_ns_max"])
+        for key, v in st.items():
+            acc[key] = acc.get(key, 0) + v
     ctx.check()
-    st = {k: v / reps for k, v in st.items()}  # per replay
-    out = dict(ms=float(np.mean(ms)), stats=st, launches=launches, pairs=int(ctx.n_pairs.item()),
-               clusters=int(ctx.n_clusters.item()), cur=sc.state.cpu().numpy(), old=old.cpu().numpy(),
-               t_min=float(sc.state[13][torch.from_numpy(w.is_static == 0).to(dev)].min().item()))
-    ctx.close()
-    del sc, old, cur0, old0, g
+    st = {key: v / steps for key, v in acc.items()}
+    st["balance"] = float(np.mean(bal)) if bal else None
+    return float(np.mean(ms)), float(np.mean(pk)), st
+
+
+def dense_leg(args, dem, W, dev, peaks):
+    """Dense packing, 1,000 icospheres of 320 triangles (candidates ->
+    narrow phase + collision times -> clusters), FP32+fixup and all-FP64."""
+    import torch
+    w = W.dense_packing(args.seed)
+    sc = dem.Scene.from_workload(w, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = {"workload": "dense packing: 10^3 icospheres (320 triangles, r=1), simple-cubic lattice at volume "
+                       "fraction 0.5, jitter +-0.1, v~N(0,0.2), w~N(0,0.2), dt=1e-4, eps=0.02"}
+    res = {}
+    for prec, name in ((0, "fp32_fixup"), (1, "fp64")):
+        ctx = dem.Context(K=w.K, tol=w.tol, precision=prec, max_particles=w.n, max_pairs=1 << 16,
+                          max_contacts=1 << 20, device=dev)
+        g = step_graph(dem, ctx, sc)
+        ms, pk, st = time_graph(ctx, g, 10, flush)
+        m = int(ctx.n_pairs.item())
+        nc = int(ctx.n_contacts.item())
+        res[name] = dict(ms=ms, pk=pk, st=st, keys=(ctx.flag[:m].cpu().numpy(), ctx.status[:m].cpu().numpy(),
+                                                      ctx.t_coll[:m].cpu().numpy(), ctx.contacts[:nc].cpu().numpy()),
+                         pairs=ctx.pairs[:m].cpu().numpy())
+        del g
+        ctx.close()
+    a, b = res["fp32_fixup"], res["fp64"]
+    F, npop = flops_per_distance(dem, w, w.state, a["pairs"], args.seed)
+    for name, r in res.items():
+        st = r["st"]
+        out[name] = {"ms_per_step": r["ms"], "pair_kernel_ms": r["pk"],
+                     "method_checks_per_s": st["method_checks"] / (r["ms"] / 1e3),
+                     "performed_distances_per_s": (st["dist_fp32"] + st["dist_fp64"]) / (r["ms"] / 1e3),
+                     "particle_steps_per_s": w.n / (r["ms"] / 1e3),
+                     "status_counts": np.bincount(r["keys"][1], minlength=3).tolist(),
+                     "bisect_steps": st["bisect_steps"]}
+    out["results_identical"] = all(np.array_equal(x, y) for x, y in zip(a["keys"], b["keys"]))
+    out["speedup_fp32_fixup_over_fp64"] = b["ms"] / a["ms"]
+    if F:
+        ach = a["st"]["dist_fp32"] * F / (a["pk"] / 1e3) / 1e12
+        out["roofline"] = {"kernel": "pair_kernel<FP32, narrow phase + collision times>", "achieved_tflops": ach,
+                           "frac_of_measured_fp32": ach / peaks["fp32_tflops"], "F": F, "F_population": npop}
+    del sc, flush
     torch.cuda.empty_cache()
+    return out
+
+
+def uneven_leg(args, dem, W, dev):
+    """Batched uneven meshes (10,000 particles: icospheres of 80/320/1280
+    triangles and convex hulls, radii 0.5-4, 60% clustered): candidates ->
+    narrow phase + collision times -> clusters; load balance of the
+    persistent pair kernel (mean over max CTA busy time)."""
+    import torch
+    w = W.uneven_meshes(args.seed)
+    sc = dem.Scene.from_workload(w, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ctx = dem.Context(K=w.K, tol=w.tol, max_particles=w.n, max_pairs=1 << 18, max_contacts=1 << 20,
+                      max_triangles=w.n_tris, device=dev)
+    g = step_graph(dem, ctx, sc)
+    ms, pk, st = time_graph(ctx, g, 10, flush)
+    m = int(ctx.n_pairs.item())
+    cnt = np.diff(w.tri_off)
+    pr = ctx.pairs[:m].cpu().numpy()
+    cost = cnt[pr[:, 0]].astype(np.float64) * cnt[pr[:, 1]]
+    out = {"workload": "uneven meshes: 10,000 particles (icospheres of 80/320/1280 triangles and convex hulls of "
+                       "20-200 Gaussian points), radii log-uniform in [0.5,4], 10 Gaussian clusters holding 60%, "
+                       "v~N(0,1), w~N(0,0.5), eps=0.02 r, dt=1e-3",
+           "ms_per_step": ms, "pair_kernel_ms": pk, "candidate_pairs": m,
+           "pair_cost_spread": float(cost.max() / max(cost.min(), 1.0)) if m else None,
+           "method_checks_per_s": st["method_checks"] / (ms / 1e3),
+           "performed_distances_per_s": (st["dist_fp32"] + st["dist_fp64"]) / (ms / 1e3),
+           "pair_kernel_cta_balance": st["balance"],
+           "note_balance": "mean over max of the persistent CTAs' busy times in the pair-kernel launch"}
+    del g
+    ctx.close()
+    del sc, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def search_leg(args, dem, W, dev, peaks):
+    """A search-heavy packing: 14^3 icospheres (320 triangles) at volume
+    fraction 0.35, v~N(0,10), w~N(0,2), dt=1e-2, eps=0.02 -- about a third of
+    the candidate pairs first meet during the step (status 2), so the K
+    samples and the bisection run.  The collision-time call alone is timed
+    (its pair kernel dominates it), FP32+fixup and all-FP64."""
+    import torch
+    w = W.dense_packing(args.seed, nside=14, phi=0.35, vsig=10.0, wsig=2.0, dt=1e-2)
+    sc = dem.Scene.from_workload(w, device=dev)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = {"workload": "search-heavy packing: 14^3 icospheres (320 triangles, r=1), simple-cubic lattice at volume "
+                       "fraction 0.35, jitter +-0.1, v~N(0,10), w~N(0,2), dt=1e-2, eps=0.02"}
+    keys = {}
+    for prec, name in ((0, "fp32_fixup"), (1, "fp64")):
+        ctx = dem.Context(K=w.K, tol=w.tol, precision=prec, max_particles=w.n, max_pairs=1 << 16,
+                          max_contacts=1 << 16, device=dev)
+        ctx.build_candidates(sc)
+        ctx.collision_times(sc)
+        torch.cuda.synchronize()
+        ctx.trace(64)
+        ctx.stats(reset=True)
+        ms, pk = [], []
+        for k in range(10):
+            flush.fill_(float(k))
+            ctx.trace(64)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.collision_times(sc)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            pk.append(sum(m for s, m in ctx.trace_read() if s == 2))
+        ctx.check()
+        st = {k: v / 10 for k, v in ctx.stats(reset=True).items()}
+        m = int(ctx.n_pairs.item())
+        status = ctx.status[:m].cpu().numpy()
+        keys[name] = (status, ctx.t_coll[:m].cpu().numpy(), ctx.ct_ab[:m].cpu().numpy())
+        r = {"ms_per_call": float(np.mean(ms)), "pair_kernel_ms": float(np.mean(pk)), "candidate_pairs": m,
+             "status_counts": np.bincount(status, minlength=3).tolist(), "bisect_steps": st["bisect_steps"],
+             "pair_evaluations": st["pair_evals"], "method_checks_per_s": st["method_checks"] / (np.mean(ms) / 1e3),
+             "performed_distances_per_s": (st["dist_fp32"] + st["dist_fp64"]) / (np.mean(ms) / 1e3)}
+        if prec == 0:
+            F, npop = flops_per_distance(dem, w, w.state, ctx.pairs[:m].cpu().numpy(), args.seed)
+            if F:
+                ach = st["dist_fp32"] * F / (np.mean(pk) / 1e3) / 1e12
+                r["roofline"] = {"kernel": "pair_kernel<FP32, collision times>", "achieved_tflops": ach,
+                                 "frac_of_measured_fp32": ach / peaks["fp32_tflops"], "F": F, "F_population": npop}
+        out[name] = r
+        ctx.close()
+    out["results_identical"] = all(np.array_equal(x, y) for x, y in zip(keys["fp32_fixup"], keys["fp64"]))
+    out["speedup_fp32_fixup_over_fp64"] = out["fp64"]["ms_per_call"] / out["fp32_fixup"]["ms_per_call"]
+    del sc, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def lts_leg(args, dem, W, dev):
+    """One cycle of the 100,000-particle mixed-step layout as one graph."""
+    import torch
+    w = W.lts_mixed_steps(args.seed)
+    old = w.state.copy()
+    old[W.F_TCUR] = w.state[W.F_TCUR] - w.state[W.F_DT] / 2.0
+    out = {"workload": "lts-100k: 100,000 icospheres (320 triangles), 20% FCC blobs at volume fraction 0.55, 80% "
+                       "free at 0.02; particle steps log-uniform in [1e-5, 1e-2] as step histories "
+                       "(t_old = t_cur - dt/2, alpha = 2, dt_max = 1e-2)"}
+    for hose in (False, True):
+        sc = dem.Scene.from_workload(w, device=dev)
+        g_old = torch.from_numpy(old).to(dev)
+        cur0, old0 = sc.state.clone(), g_old.clone()
+        ctx = dem.Context(K=w.K, tol=w.tol, max_particles=w.n, max_pairs=1 << 20, max_contacts=1 << 16,
+                          max_triangles=w.n_tris, device=dev)
+        ctx.lts_sweep(sc, g_old, 1e-2, hose=hose)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            ctx.lts_sweep(sc, g_old, 1e-2, hose=hose)
+        ms, adv = [], []
+        for r in range(6):
+            sc.state.copy_(cur0)
+            g_old.copy_(old0)
+            torch.cuda.synchronize()
+            ctx.stats(reset=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            st = ctx.stats(reset=True)
+            if r:
+                ms.append(e0.elapsed_time(e1))
+                adv.append(st["advances"])
+        ctx.check()
+        key = "with_hose_check" if hose else "cycle"
+        out[key] = {"ms_per_cycle": float(np.mean(ms)), "particle_steps_per_s": float(np.mean(adv)) / (np.mean(ms) / 1e3),
+                    "candidate_pairs": int(ctx.n_pairs.item()), "clusters": int(ctx.n_clusters.item())}
+        del g
+        ctx.close()
+        del sc, g_old
+        torch.cuda.empty_cache()
     return out
 
 
 def narrowing_leg(args, dem, W, dev, reps=10):
     """Collision times by the paper's narrowing against K samples + bisection
-    on the same candidate pairs: time per call (CUDA events, L2 flushed
-    between calls), method checks/s, and how the two procedures' answers
-    compare (statuses; for pairs with status 2 in both, the narrowing time
-    minus the sampling time, in units of the pair's step)."""
+    on the same candidate pairs (time per call, status agreement, time
+    differences in units of the step)."""
     import torch
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     out = {}
-    cases = (("dense-packing-1000 (the benchmark workload)", W.dense_packing(args.seed)),
+    cases = (("dense-packing-1000", W.dense_packing(args.seed)),
              ("fast dense packing: 5^3 icospheres (320 triangles), v ~ N(0,150), w ~ N(0,150), dt = 1e-4",
               W.dense_packing(args.seed + 3, nside=5, vsig=150.0, wsig=150.0)))
     for name, w in cases:
         sc = dem.Scene.from_workload(w, device=dev)
         res = {}
         for method, key in ((dem.DEM_CTIME_SAMPLES, "samples_bisection"), (dem.DEM_CTIME_NARROWING, "narrowing")):
-            ctx = dem.Context(K=w.K, tol=w.tol, precision=dem.DEM_PREC_FP32_FIXUP, max_particles=w.n,
-                              max_pairs=1 << 16, max_contacts=1 << 20, ctime_method=method, device=dev)
+            ctx = dem.Context(K=w.K, tol=w.tol, max_particles=w.n, max_pairs=1 << 16, max_contacts=1 << 20,
+                              ctime_method=method, device=dev)
             ctx.build_candidates(sc)
             ctx.collision_times(sc)
             torch.cuda.synchronize()
-            ctx.stats(reset=True)
             ms = []
             for k in range(reps):
                 flush.fill_(float(k))
@@ -423,183 +734,72 @@ def narrowing_leg(args, dem, W, dev, reps=10):
                 torch.cuda.synchronize()
                 ms.append(e0.elapsed_time(e1))
             ctx.check()
-            st = ctx.stats(reset=True)
             m = int(ctx.n_pairs.item())
-            res[key] = dict(ms=float(np.mean(ms)), checks_per_s=st["method_checks"] / (sum(ms) / 1e3),
-                            status=ctx.status[:m].cpu().numpy(), t=ctx.t_coll[:m].cpu().numpy(), pairs=m)
+            res[key] = dict(ms=float(np.mean(ms)), status=ctx.status[:m].cpu().numpy(), t=ctx.t_coll[:m].cpu().numpy())
             ctx.close()
         a, b = res["samples_bisection"], res["narrowing"]
         both2 = (a["status"] == 2) & (b["status"] == 2)
         T = float(w.state[W.F_DT, 0])
         d = (b["t"][both2] - a["t"][both2]) / T
-        out[name] = {
-            "candidate_pairs": a["pairs"],
-            "samples_bisection": {"ms": a["ms"], "checks_per_s": a["checks_per_s"],
-                                  "status_counts": np.bincount(a["status"], minlength=3).tolist()},
-            "narrowing": {"ms": b["ms"], "checks_per_s": b["checks_per_s"],
-                          "status_counts": np.bincount(b["status"], minlength=3).tolist()},
-            "same_status": int((a["status"] == b["status"]).sum()),
-            "status2_in_both": int(both2.sum()),
-            "t_narrowing_minus_t_sampling_over_T": {"mean": float(d.mean()) if d.size else None,
-                                                    "min": float(d.min()) if d.size else None,
-                                                    "max": float(d.max()) if d.size else None}}
+        out[name] = {"samples_bisection_ms": a["ms"], "narrowing_ms": b["ms"],
+                     "status_counts": np.bincount(a["status"], minlength=3).tolist(),
+                     "same_status": int((a["status"] == b["status"]).sum()), "pairs": int(len(a["status"])),
+                     "t_narrowing_minus_t_sampling_over_T_mean": float(d.mean()) if d.size else None}
         del sc
     del flush
     torch.cuda.empty_cache()
     return out
 
 
-def lts_legs(args, dem, W, dev):
-    """The local-time-stepping measurements: one cycle on the 100,000-particle
-    mixed-step layout, and 50 sweeps of the 1,000,000-particle settling column
-    in FP32 + fixup and in all-FP64 (final snapshots compared bit for bit)."""
-    res = {}
-    # one cycle, 100k particles; the log-uniform steps are the particles'
-    # histories: t_old = t_cur - dt_p / alpha, so the damped step is dt_p
-    w = W.lts_mixed_steps(args.seed)
-    old = w.state.copy()
-    old[W.F_TCUR] = w.state[W.F_TCUR] - w.state[W.F_DT] / 2.0
-    r = lts_measure(dem, w, old, dem.DEM_PREC_FP32_FIXUP, 1, 5, 1e-2, (0.0, 0.0, 0.0), dev, 1 << 20)
-    st = r["stats"]
-    res["lts_cycle_100k"] = {
-        "workload": "lts-100k: 100,000 icospheres (320 triangles), 20% FCC blobs at volume fraction 0.55, 80% "
-                    "free at 0.02; particle steps log-uniform in [1e-5, 1e-2] as step histories "
-                    "(t_old = t_cur - dt/2, alpha = 2, dt_max = 1e-2)",
-        "ms_per_cycle": r["ms"], "cuda_graph": "one sweep (step sizes, candidates, clusters, consolidation, "
-                                               "collision times, masking, advance) captured as one graph",
-        "particle_steps_per_s": st["advances"] / (r["ms"] / 1e3),
-        "checks_per_s": st["method_checks"] / (r["ms"] / 1e3),
-        "advances_per_cycle": st["advances"], "candidate_pairs": r["pairs"], "clusters": r["clusters"],
-        "kernels_per_cycle": r["launches"]}
-    # the same cycle with the space-time hose check (Check 2) in the broad phase
-    rh = lts_measure(dem, w, old, dem.DEM_PREC_FP32_FIXUP, 1, 5, 1e-2, (0.0, 0.0, 0.0), dev, 1 << 20, hose=True)
-    res["lts_cycle_100k"]["with_hose_check"] = {
-        "ms_per_cycle": rh["ms"], "candidate_pairs": rh["pairs"], "clusters": rh["clusters"],
-        "advances_per_cycle": rh["stats"]["advances"],
-        "final_snapshots_identical_to_without": bool(np.array_equal(rh["cur"], r["cur"]) and
-                                                     np.array_equal(rh["old"], r["old"]))}
-    del w, old, r, rh
-    # the settling column: sweeps in a graph, both precisions
-    S = args.column_sweeps
-    w = W.settling_column(args.seed)
-    col = {}
-    for prec, name in ((dem.DEM_PREC_FP32_FIXUP, "fp32_fixup"), (dem.DEM_PREC_FP64, "fp64")):
-        r = lts_measure(dem, w, w.state.copy(), prec, S, 1, 1e-3, (0.0, 0.0, -9.81), dev, 1 << 21)
-        st = r["stats"]
-        col[name] = dict(ms_per_sweep=r["ms"] / S, particle_steps_per_s=st["advances"] / (r["ms"] / 1e3),
-                         checks_per_s=st["method_checks"] / (r["ms"] / 1e3), advances=st["advances"],
-                         last_sweep_pairs=r["pairs"], earliest_t_after=r["t_min"], kernels=r["launches"],
-                         final=(r["cur"], r["old"]))
-    same = bool(np.array_equal(col["fp32_fixup"]["final"][0], col["fp64"]["final"][0]) and
-                np.array_equal(col["fp32_fixup"]["final"][1], col["fp64"]["final"][1]))
-    for v in col.values():
-        del v["final"]
-    res["settling_column_1m"] = {
-        "workload": "settling column: 100^3 icospheres (half 80, half 320 triangles), lattice spacing 2.2, "
-                    "jitter +-0.1, over a static 316x316-quad floor (199,712 triangles); eps = 0.01, "
-                    "dt_max = 1e-3, gravity (0,0,-9.81), particles in contact stop (stand-in update)",
-        "sweeps": S, "cuda_graph": f"{S} sweeps captured in one graph", **col,
-        "speedup_fp32_fixup_over_fp64": col["fp64"]["ms_per_sweep"] / col["fp32_fixup"]["ms_per_sweep"],
-        "final_snapshots_identical": same}
-    return res
-
-
-def e2e_arm(dem, w, ctx, sc, steps, graph):
-    """Through the public API from pinned host buffers: host-to-device copies
-    of the particle data into the scene the step graph was captured on, the
-    step, device-to-host copies of every output."""
-    import torch
-    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-    h_state, h_static, h_off, h_tris = pin(w.state), pin(w.is_static), pin(w.tri_off), pin(w.tris)
-    h_out = {}
-    bi = sum(t.numel() * t.element_size() for t in (h_state, h_static, h_off, h_tris))
-    times, bo = [], 0
-    for k in range(steps + 2):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sc.state.copy_(h_state, non_blocking=True)
-        sc.is_static.copy_(h_static, non_blocking=True)
-        sc.tri_off.copy_(h_off, non_blocking=True)
-        sc.tris.copy_(h_tris, non_blocking=True)
-        graph.replay()
-        m = int(ctx.n_pairs.item())
-        nc = min(int(ctx.n_contacts.item()), ctx.max_contacts)
-        outs = [ctx.pairs[:m], ctx.flag[:m], ctx.dmin[:m], ctx.tri_ab[:m], ctx.t_coll[:m], ctx.status[:m],
-                ctx.ct_ab[:m], ctx.cluster_id[:w.n], ctx.n_clusters, ctx.contacts[:nc], ctx.contact_geom[:nc]]
-        host = [t.to("cpu", non_blocking=True) for t in outs]
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if k >= 2:
-            times.append(dt)
-            bo = 2 * 8 + sum(t.numel() * t.element_size() for t in host)
-        h_out = host
-    ctx.check()
-    st = ctx.stats(reset=True)
-    checks = st["method_checks"] / (steps + 2)
-    h_out.clear()
-    return {"value": checks / float(np.mean(times)), "unit": UNIT, "h2d_bytes_per_step": int(bi),
-            "d2h_bytes_per_step": int(bo), "ms_per_step": 1e3 * float(np.mean(times))}
-
-
 # ------------------------------------------------------------------ CPU oracle
 
-def cpu_sample(w, pairs, n_sample, seed):
-    import oracle
-    rng = np.random.default_rng(seed)
-    idx = np.sort(rng.choice(len(pairs), min(n_sample, len(pairs)), replace=False))
-    sp = pairs[idx]
-    cnt = np.diff(w.tri_off)
-    nt = oracle.default_threads()
-    t0 = time.perf_counter()
-    bp = oracle.broad_phase(w)
-    r = oracle.narrow_phase(w, sp, n_threads=nt)
-    c = oracle.collision_times(w, sp, n_threads=nt)
-    ids, ncl = oracle.clusters(w.n, bp, w.is_static)
-    dt = time.perf_counter() - t0
-    tt = (cnt[sp[:, 0]] * cnt[sp[:, 1]]).astype(np.float64)
-    checks = float(np.sum(tt * (1 + c["n_evals"])))
-    return checks, dt, nt, len(sp), len(pairs)
-
-
-def cpu_baseline(args, w=None):
+def oracle_sweeps(seed, sweeps, n_threads=None):
+    """The FP64 oracle's sweeps of a 6^3 sub-column over its floor patch (the
+    same particles, spacing, floor quads and parameters as the full column).
+    Returns (advances, seconds, threads, description)."""
     import oracle
     from paper_2309_15417_gb300 import workloads as W
-    w = w or W.dense_packing(args.seed)
-    pairs = oracle.broad_phase(w)
-    checks, dt, nt, ns, npairs = cpu_sample(w, pairs, args.cpu_sample, args.seed)
-    return {"value": checks / dt, "unit": UNIT, "cores": nt, "kind": "oracle",
-            "sample": f"{ns} of {npairs} candidate pairs (narrow phase + collision times, every triangle pair "
-                      f"in FP64); broad phase and clusters over all {w.n} particles",
-            "seconds": dt}
+    oracle.build()
+    w = W.settling_column(seed, nside=REF_SIDE)
+    old = w.state.copy()
+    nt = n_threads or oracle.default_threads()
+    adv, secs = [], []
+    for _ in range(sweeps):
+        t0 = time.perf_counter()
+        r = oracle.lts_sweep(w, old, 1e-3, gravity=(0.0, 0.0, -9.81), n_threads=nt)
+        secs.append(time.perf_counter() - t0)
+        adv.append(int(r["active"].sum()))
+    desc = (f"one sweep per step of a {REF_SIDE}^3 sub-column ({w.n - 1} icospheres over a "
+            f"{w.n_tris - int(w.tri_off[-2])}-triangle floor patch, same spacing, quads and parameters), the "
+            f"oracle's broad phase, clusters, consolidation, collision times and advance, every triangle pair "
+            f"in FP64")
+    return adv, secs, nt, desc
+
+
+def cpu_baseline(args):
+    adv, secs, nt, desc = oracle_sweeps(args.seed, 3)
+    v = sum(adv) / sum(secs)
+    return {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": desc + "; 3 sweeps",
+            "seconds": sum(secs)}
 
 
 def reference_arm(args, rank, world):
     """The FP64 CPU oracle as the reference arm (rank 0 only)."""
     if rank != 0:
         return
-    import oracle
-    from paper_2309_15417_gb300 import workloads as W
-    oracle.build()
-    w = W.dense_packing(args.seed)
-    pairs = oracle.broad_phase(w)
-    for k in range(args.warmup):
-        cpu_sample(w, pairs, max(4, args.cpu_sample // 8), args.seed + 100 + k)
-    tot_c, tot_t, nt, ns = 0.0, 0.0, 1, 0
-    for k in range(args.steps):
-        c, t, nt, ns, _ = cpu_sample(w, pairs, max(4, args.cpu_sample // 4), args.seed + k)
-        tot_c += c
-        tot_t += t
-    v = tot_c / tot_t
+    adv, secs, nt, desc = oracle_sweeps(args.seed, args.warmup + args.steps)
+    adv, secs = adv[args.warmup:], secs[args.warmup:]
+    v = sum(adv) / sum(secs)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle",
-                             "sample": f"per step {ns} of {len(pairs)} candidate pairs (narrow phase + collision "
-                                       f"times); broad phase and clusters over all {w.n} particles"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
+
+# ------------------------------------------------------------------ main
 
 def main():
     args = parse()
@@ -613,50 +813,69 @@ def main():
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU (the contact-detection path has no CPU fallback)")
     from paper_2309_15417_gb300 import dem
+    from paper_2309_15417_gb300 import workloads as W
     dem.load()
-    r = gpu_arm(args, rank, world, local)
-    vals = aggregate(r["value_local"], r["time_local"], world)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks = measured_peaks(dem, dev)
+    r = column_leg(args, dem, W, dev, rank, world, peaks)
+    adv_total, tmax = aggregate(r["st"]["advances"], r["t"], world)
+    legs = {}
+    if world == 1 and not args.no_legs:
+        want = set(args.legs.split(","))
+        for name, fn in (("dense", lambda: dense_leg(args, dem, W, dev, peaks)),
+                         ("uneven", lambda: uneven_leg(args, dem, W, dev)),
+                         ("search", lambda: search_leg(args, dem, W, dev, peaks)),
+                         ("lts", lambda: lts_leg(args, dem, W, dev)),
+                         ("narrowing", lambda: narrowing_leg(args, dem, W, dev))):
+            if name in want:
+                legs[name] = fn()
     if rank == 0:
-        cpu = None
-        if not args.no_cpu:
-            cpu = cpu_baseline(args)
-        total_checks, tmax = vals
-        value = total_checks / tmax
+        cpu = None if args.no_cpu else cpu_baseline(args)
         K = args.steps
-        ms = 1e3 * tmax / K
-        roof = {"bound": "alu", "kernel": "pair_kernel<FP32, narrow phase + collision times>", "achieved": r["achieved"],
-                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": r["achieved"] / FP32_PEAK_TFLOPS,
-                "traffic": _profile_traffic(), "peak_source": "recipe unit counts: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                "flops_per_launch": r["ct_flops"], "ms_per_launch": r["ct_ms"]}
+        st, w = r["st"], r["w"]
+        value = adv_total / tmax
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": 1e3 * tmax / K, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "particles": r["particles"], "candidate_pairs": r["n_pairs"],
-                           "precision": "FP32 + FP64 recomputation in the FP32 error band",
-                           "l2": "flushed (512 MB write) between timed steps", "parallelism": f"replicas x{world}"},
-                "particle_steps_per_s": world * r["particles"] * K / tmax,
-                "checks_per_step": r["checks_step"],
-                "stage_ms": {"detect (narrow phase + collision times)": r["ct_ms"],
-                             "step_without_graph": r["direct_ms"]},
-                "four_call_step": r["four_call"],
-                "cuda_graph": "timed steps are replays of the step (candidates, detect, clusters) captured in "
-                              "one CUDA graph",
-                "roofline": roof, "cpu_baseline": cpu, "e2e": r["e2e"], "clocks": r["clocks"],
-                "gpu_launches": int(r["launches"]), "fp64_form": r["fp64"], "fp32_error": r["fp32_err"],
-                "counters_per_step": r["stats_step"], "local_time_stepping": r.get("lts"),
-                "narrowing_vs_sampling": r.get("narrowing")}
+                "config": {"workload": WORKLOAD, "particles": w.n - 1, "triangles": w.n_tris,
+                           "precision": "FP32 + FP64 recomputation of undecided distances",
+                           "l2": "flushed (512 MB write) between timed steps; inputs (9.6 GB) exceed L2",
+                           "parallelism": f"replicas x{world}",
+                           "cuda_graph": "one sweep captured once, replayed once per step (the state evolves)"},
+                "particle_steps": {"per_s": value, "advances_per_step": st["advances"] / K,
+                                   "particle_sweeps_per_s": world * (w.n - 1) * K / tmax,
+                                   "note": "a particle-step is a particle moving to its new time stamp; under the "
+                                           "masking of local time stepping not every particle advances in every "
+                                           "sweep"},
+                "triangle_pair_checks": {
+                    "method_per_s": st["method_checks"] / r["t"], "performed_per_s":
+                        (st["dist_fp32"] + st["dist_fp64"]) / r["t"], "unit": CHECKS,
+                    "method_per_step": st["method_checks"] / K,
+                    "performed_fp32_per_step": st["dist_fp32"] / K, "performed_fp64_per_step": st["dist_fp64"] / K,
+                    "note": "method = sum over candidate pairs of T_i T_j per evaluation the method defines (a "
+                            "floor pair counts all 199,712 floor triangles); performed = triangle-pair distances "
+                            "actually evaluated after culling"},
+                "per_step": {"candidate_pairs": r["pairs_per_step"], "contacts": r["contacts_per_step"],
+                             "pair_evaluations": st["pair_evals"] / K, "bisect_steps": st["bisect_steps"] / K,
+                             "step_ms_min_median_max": [float(np.min(r["step_ms"])), float(np.median(r["step_ms"])),
+                                                        float(np.max(r["step_ms"]))]},
+                "stage_ms": r["split"], "fp64_form": r["fp64"], "fp32_error": r["fp32_err"],
+                "roofline": r["roof"], "peaks": peaks, "cpu_baseline": cpu, "e2e": r["e2e"],
+                "clocks": r["clocks"], "gpu_launches": int(r["launches"] * K), "kernels_per_step": int(r["launches"]),
+                "legs": legs}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-def aggregate(checks_local, time_local, world):
-    """Sum of checks over ranks and max of time over ranks."""
+def aggregate(units_local, time_local, world):
+    """Sum of units over ranks and max of time over ranks."""
     if world == 1:
-        return checks_local, time_local
+        return units_local, time_local
     import torch
     dev = torch.device("cuda", torch.cuda.current_device()) if torch.distributed.get_backend() == "nccl" else "cpu"
-    t = torch.tensor([checks_local, time_local], dtype=torch.float64, device=dev)
+    t = torch.tensor([units_local, time_local], dtype=torch.float64, device=dev)
     c = t[:1].clone()
     torch.distributed.all_reduce(c, op=torch.distributed.ReduceOp.SUM)
     m = t[1:].clone()

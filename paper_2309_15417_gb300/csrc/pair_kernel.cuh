@@ -1052,10 +1052,12 @@ struct Cta {
 
   // --- one pass over tile pair (ta, tb) -------------------------------------
   // pass 0: triangle pairs with sphere bound LB <= th0;
-  // pass 1: th0 < LB <= bound (shared, shrinking), group pairs in order of
-  // their lower bounds.
+  // pass 1: LB <= bound (shared, shrinking), group pairs in order of their
+  // lower bounds; the pairs with LB <= th0 are left out only when pass 0
+  // scanned this tile pair (seen0) -- a tile pair that pass 0's tile test
+  // culled has never had any of its pairs evaluated.
   template <bool DECIDE, bool ARGMIN, bool CONTACTS>
-  __device__ void scan_tiles(int ta, int tb, bool pass1, T th0, int64_t pk) {
+  __device__ void scan_tiles(int ta, int tb, bool pass1, T th0, int64_t pk, bool seen0 = true) {
     const int na = min(TT, s.nA - ta * TT), nb = min(TT, s.nB - tb * TT);
     const int nga = (na + G - 1) / G, ngb = (nb + G - 1) / G;
     const T Elb = T(s.Elb);
@@ -1148,7 +1150,7 @@ struct Cta {
             __syncwarp();
             const T bn = T(bitsd(*(volatile unsigned long long *)&s.bound)) + Elb;
             const T t1 = bn + ar + br;
-            cand = valid && d2c <= t1 * t1 && !(d2c <= t0 * t0);
+            cand = valid && d2c <= t1 * t1 && !(seen0 && d2c <= t0 * t0);
           }
           ntests += __popc(__ballot_sync(0xffffffffu, valid));
           const uint32_t m = __ballot_sync(0xffffffffu, cand);
@@ -1350,10 +1352,12 @@ struct Cta {
         const int q0 = multi ? bound_by_tiles(nta, ntb) : 0;
         {
           const int ta = q0 / ntb, tb = q0 - (q0 / ntb) * ntb;
+          // whether pass 0 scanned this tile pair (the same test, same pose)
+          const bool seen0 = !multi || __syncthreads_or(tid == 0 && tile_near(ta, tb, double(th0)));
           if (!load_tiles(ta, tb)) return false;
           frames(ta, tb);
           if (tid == 0) stat(ST_TILES, 1);
-          scan_tiles<false, true, false>(ta, tb, true, th0, pk);
+          scan_tiles<false, true, false>(ta, tb, true, th0, pk, seen0);
         }
         for (int c0 = 0; multi && c0 < nq; c0 += NT) {
           const int q = c0 + tid;
@@ -1370,10 +1374,11 @@ struct Cta {
               const int ta = qq / ntb, tb = qq - ta * ntb;
               if (!__syncthreads_or(tid == 0 && tile_near(ta, tb, bitsd(*(volatile unsigned long long *)&s.bound))))
                 continue;
+              const bool seen0 = __syncthreads_or(tid == 0 && tile_near(ta, tb, double(th0)));
               if (!load_tiles(ta, tb)) return false;
               frames(ta, tb);
               if (tid == 0) stat(ST_TILES, 1);
-              scan_tiles<false, true, false>(ta, tb, true, th0, pk);
+              scan_tiles<false, true, false>(ta, tb, true, th0, pk, seen0);
             }
           }
           __syncthreads();

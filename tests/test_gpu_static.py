@@ -140,3 +140,52 @@ def test_floor_tiles_are_culled(dem):
         print(f"prec {prec}: {len(sel)} floor pairs, tile pairs scanned {st['tile_pairs']} of {full} per pass "
               f"({st['tile_pairs'] / full:.3f}), fp32 {st['dist_fp32']}, fp64 {st['dist_fp64']}")
         assert 0 < st["tile_pairs"] < 0.2 * full
+
+
+def hovering_over_floor(seed, n=40, nq=48, size=34.0, eps=0.01):
+    """Icospheres (320 triangles) hovering 1-4 halo widths above a static floor
+    of nq x nq quads (Morton order, 15 tiles of 320 triangles), at rest: the
+    closest floor triangle of every particle lies farther than the pass-0
+    threshold, in a tile whose box bound also exceeds it."""
+    rng = np.random.default_rng(seed)
+    ico = W.icosphere(2)
+    R = W.mesh_radius(ico)
+    floor = W.floor_grid(nq, size)
+    xy = rng.uniform(-size / 2 + 2.0, size / 2 - 2.0, size=(n, 2))
+    gap = rng.uniform(1.05, 4.0, size=n) * 2 * eps
+    pos = np.concatenate([np.column_stack([xy, R + gap]), [[0.0, 0.0, 0.0]]])
+    quat = np.concatenate([W.random_quaternions(rng, n), [[1.0, 0.0, 0.0, 0.0]]])
+    st = np.zeros(n + 1, np.uint8)
+    st[n] = 1
+    z = np.zeros((n + 1, 3))
+    return W._assemble(f"hovering-{n}", [floor, ico], [1] * n + [0], pos, z, quat, z, 0.0, 1e-3, eps,
+                       is_static=st)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("seed", [0, 1])
+def test_closest_pair_in_a_tile_culled_by_the_first_pass(dem, prec, seed):
+    """The closest pair's search beyond the first pass must scan the pairs of
+    tiles that the first pass culled (regression: it skipped every triangle
+    pair whose sphere bound was within the first threshold, as if the first
+    pass had evaluated it)."""
+    import torch
+    w = hovering_over_floor(seed)
+    pairs = np.array([[p, w.n - 1] for p in range(w.n - 1)], np.int32)
+    on = oracle.narrow_phase(w, pairs)
+    oc = oracle.collision_times(w, pairs)
+    assert (on["dmin"] > 0.02).all()
+    c = dem.Context(K=w.K, tol=w.tol, precision=prec, max_particles=w.n, max_pairs=1024, max_contacts=1 << 14,
+                    max_triangles=w.n_tris)
+    sc = dem.Scene.from_workload(w)
+    gp = torch.from_numpy(pairs).cuda()
+    c.narrow_phase(sc, pairs=gp)
+    c.collision_times(sc, pairs=gp)
+    c.check()
+    m = len(pairs)
+    assert np.array_equal(c.dmin[:m].cpu().numpy(), on["dmin"])
+    assert np.array_equal(c.tri_ab[:m].cpu().numpy(), on["tri_ab"])
+    assert np.array_equal(c.flag[:m].cpu().numpy(), on["flag"])
+    assert np.array_equal(c.status[:m].cpu().numpy(), oc["status"])
+    assert np.array_equal(c.ct_ab[:m].cpu().numpy(), oc["tri_ab"])
+    c.close()
