@@ -355,6 +355,11 @@ def column_leg(args, dem, W, dev, rank, world, peaks):
     r32.ctx.check()
     torch.cuda.synchronize()
     cur0, old0 = r32.sc.state.clone(), r32.old.clone()
+    # the pair kernel's launch configuration, tuned on the last warm-up sweep's
+    # pairs (outside the timed region; the snapshots are restored afterwards)
+    tune32 = r32.ctx.autotune(r32.sc, dem.DEM_TUNE_DETECT)
+    r32.sc.state.copy_(cur0)
+    r32.old.copy_(old0)
     state_np = cur0.cpu().numpy()
     r32.capture()
     if world > 1:
@@ -386,8 +391,11 @@ def column_leg(args, dem, W, dev, rank, world, peaks):
                 "recipe_peak_tflops": peaks["sms"] * 128 * 2 * 2.07e9 / 1e12}
     e2e = None
     if not args.no_e2e:
-        # restore the snapshots after the timed steps and run end to end from host buffers
-        e2e = e2e_leg(dem, r32, min(K, 5))
+        # the same K steps from the same snapshots, end to end from host buffers
+        # (the particle-steps are then those of the device-timed steps)
+        r32.sc.state.copy_(cur0)
+        r32.old.copy_(old0)
+        e2e = e2e_leg(dem, r32, K)
     r32.close()
     del r32
     torch.cuda.empty_cache()
@@ -397,6 +405,7 @@ def column_leg(args, dem, W, dev, rank, world, peaks):
         r64.sc.state.copy_(cur0)
         r64.old.copy_(old0)
         r64.sweep()  # warm-up outside the capture (restored below)
+        tune64 = r64.ctx.autotune(r64.sc, dem.DEM_TUNE_DETECT)
         r64.ctx.check()
         r64.sc.state.copy_(cur0)
         r64.old.copy_(old0)
@@ -409,7 +418,7 @@ def column_leg(args, dem, W, dev, rank, world, peaks):
         st64 = {k: sum(s[k] for s in res64["stats"]) for k in res64["stats"][0]}
         fp64 = {"ms_per_step": t64 * 1e3 / K, "value": st64["advances"] / t64, "unit": UNIT,
                 "pair_kernel_ms": trace_split(res64["trace"]).get("pair kernel"),
-                "speedup_fp32_fixup_over_fp64": t64 / t32, "results_identical": bool(same),
+                "speedup_fp32_fixup_over_fp64": t64 / t32, "results_identical": bool(same), "launch_tuning": tune64,
                 "compared": "every step's pairs, statuses, collision times and pairs, clusters, narrow-phase "
                             "flags, minima and closest pairs, contact keys; final current and old snapshots"}
         r64.close()
@@ -419,7 +428,7 @@ def column_leg(args, dem, W, dev, rank, world, peaks):
         err = None
     del flush
     torch.cuda.empty_cache()
-    return dict(w=w, K=K, t=t32, st=st, split=split, roof=roof, fp64=fp64, fp32_err=err, e2e=e2e,
+    return dict(w=w, K=K, t=t32, st=st, split=split, roof=roof, fp64=fp64, fp32_err=err, e2e=e2e, tune=tune32,
                 clocks=res32["clocks"], launches=launches, step_ms=res32["step_ms"], gen_s=gen_s,
                 pairs_per_step=float(np.mean([o["m"] for o in res32["outs"]])) if res32["outs"] else None,
                 contacts_per_step=float(np.mean([o["nc"] for o in res32["outs"]])) if res32["outs"] else None)
@@ -444,7 +453,7 @@ def e2e_leg(dem, run, steps):
     times, bo, adv = [], 0, 0
     bi = 2 * h_cur.numel() * 8
     c.stats(reset=True)
-    for k in range(steps + 1):
+    for k in range(steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         run.sc.state.copy_(h_cur, non_blocking=True)
@@ -466,10 +475,9 @@ def e2e_leg(dem, run, steps):
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         st = c.stats(reset=True)
-        if k >= 1:
-            times.append(dt)
-            adv += st["advances"]
-            bo += b
+        times.append(dt)
+        adv += st["advances"]
+        bo += b
     c.check()
     T = float(np.sum(times))
     return {"value": adv / T, "unit": UNIT, "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo / steps),
@@ -581,8 +589,20 @@ def uneven_leg(args, dem, W, dev):
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     ctx = dem.Context(K=w.K, tol=w.tol, max_particles=w.n, max_pairs=1 << 18, max_contacts=1 << 20,
                       max_triangles=w.n_tris, device=dev)
+    configs = {}
+    for name, kw in (("index_order", dict(ctas_per_sm=0, wflush=64, cost_order=0)),
+                     ("costliest_first", dict(ctas_per_sm=0, wflush=64, cost_order=1))):
+        ctx.set_tuning(dem.DEM_TUNE_DETECT, **kw)
+        g = step_graph(dem, ctx, sc)
+        ms_, pk_, st_ = time_graph(ctx, g, 10, flush)
+        configs[name] = {"ms_per_step": ms_, "pair_kernel_ms": pk_, "pair_kernel_cta_balance": st_["balance"], **kw}
+        del g
+    ctx.build_candidates(sc)
+    tuned = ctx.autotune(sc, dem.DEM_TUNE_DETECT)
     g = step_graph(dem, ctx, sc)
     ms, pk, st = time_graph(ctx, g, 10, flush)
+    configs["autotuned"] = {"ms_per_step": ms, "pair_kernel_ms": pk, "pair_kernel_cta_balance": st["balance"],
+                            **{k: tuned[k] for k in ("ctas_per_sm", "wflush", "cost_order")}}
     m = int(ctx.n_pairs.item())
     cnt = np.diff(w.tri_off)
     pr = ctx.pairs[:m].cpu().numpy()
@@ -594,7 +614,7 @@ def uneven_leg(args, dem, W, dev):
            "pair_cost_spread": float(cost.max() / max(cost.min(), 1.0)) if m else None,
            "method_checks_per_s": st["method_checks"] / (ms / 1e3),
            "performed_distances_per_s": (st["dist_fp32"] + st["dist_fp64"]) / (ms / 1e3),
-           "pair_kernel_cta_balance": st["balance"],
+           "pair_kernel_cta_balance": st["balance"], "launch_configurations": configs,
            "note_balance": "mean over max of the persistent CTAs' busy times in the pair-kernel launch"}
     del g
     ctx.close()
@@ -842,7 +862,8 @@ def main():
                            "precision": "FP32 + FP64 recomputation of undecided distances",
                            "l2": "flushed (512 MB write) between timed steps; inputs (9.6 GB) exceed L2",
                            "parallelism": f"replicas x{world}",
-                           "cuda_graph": "one sweep captured once, replayed once per step (the state evolves)"},
+                           "cuda_graph": "one sweep captured once, replayed once per step (the state evolves)",
+                           "launch_tuning": r["tune"]},
                 "particle_steps": {"per_s": value, "advances_per_step": st["advances"] / K,
                                    "particle_sweeps_per_s": world * (w.n - 1) * K / tmax,
                                    "note": "a particle-step is a particle moving to its new time stamp; under the "

@@ -380,6 +380,38 @@ dem_status dem_trace(dem_ctx *ctx, int32_t cap);
 dem_status dem_trace_read(dem_ctx *ctx, int32_t *site /* host */, float *ms /* host */, int32_t cap,
                           int32_t *n /* host */);
 
+/* Launch configuration of the pair kernel (one per precision and call kind,
+ * held by the context).  Not part of the paper's method: it decides only the
+ * schedule, never a result. */
+typedef struct {
+  int32_t ctas_per_sm; /* persistent CTAs per SM (0 = as many as fit, at most 4 in FP32, 2 in FP64) */
+  int32_t wflush;      /* triangle pairs a warp collects before it evaluates them (32 or 64) */
+  int32_t cost_order;  /* 1: pairs handed out costliest first (classes of T_i * T_j, a factor of two
+                          each); 0: in index order */
+  float ms;            /* dem_autotune: the chosen configuration's time (milliseconds) */
+} dem_tuning;
+
+enum { DEM_TUNE_NARROW = 0, DEM_TUNE_CTIME = 1, DEM_TUNE_DETECT = 2, DEM_TUNE_NARROWING = 3 };
+
+/* Autotuner: times the call selected by `kind` (DEM_TUNE_NARROW:
+ * dem_narrow_phase at the pair start; DEM_TUNE_CTIME / DEM_TUNE_NARROWING:
+ * dem_collision_times by samples / by the narrowing; DEM_TUNE_DETECT:
+ * dem_detect) in the context's precision on the given pairs for every
+ * configuration of CTAs per SM {1, 2, 3, 4} x wflush {32, 64} x cost_order
+ * {0, 1} (reps timed runs each after one warm-up run, CUDA events on
+ * `stream`), keeps the fastest in the context for that kind and writes it to
+ * *best (host, optional).  The outputs (out, t_coll, status, tri_ab, as the
+ * tuned call takes them) hold the last run's results, which every
+ * configuration computes identically.  Synchronises `stream`; do not call it
+ * during a stream capture.  DEM_ERR_ARG for bad arguments. */
+dem_status dem_autotune(dem_ctx *ctx, int32_t kind, const dem_particles *P, const int32_t *pairs, int64_t max_pairs,
+                        const int64_t *n_pairs, const dem_narrow_out *out, double *t_coll, uint8_t *status,
+                        int32_t *tri_ab, int32_t reps, dem_tuning *best, void *stream);
+
+/* Read or set the configuration used for call kind `kind` (host struct). */
+dem_status dem_get_tuning(dem_ctx *ctx, int32_t kind, dem_tuning *out);
+dem_status dem_set_tuning(dem_ctx *ctx, int32_t kind, const dem_tuning *in);
+
 /* Synchronise the device, copy the counters to host *out; reset them if
  * `reset` is nonzero. */
 dem_status dem_get_stats(dem_ctx *ctx, dem_stats *out, int reset);

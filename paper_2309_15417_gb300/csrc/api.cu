@@ -167,7 +167,8 @@ dem_status dem_create(const dem_config *cfg, dem_ctx **out) {
             alloc(c, &S.st_count, 1) && alloc(c, &S.pc, nq) && alloc(c, &S.po, nq) && alloc(c, &S.pcur, nq) &&
             alloc(c, &S.sidx, nc) && alloc(c, &S.tile_sph, S.cap_tiles) && alloc(c, &S.tile_box, 2 * S.cap_tiles) && alloc(c, &S.tile_list, S.cap_tiles) && alloc(c, &S.lts_tmin, np) &&
             alloc(c, &S.lts_step, np) && alloc(c, &S.lts_tnew, np) && alloc(c, &S.lts_tglob, 1) &&
-            alloc(c, &S.lts_touch, np);
+            alloc(c, &S.lts_touch, np) && alloc(c, &S.order, nq) && alloc(c, &S.cost_bucket, nq) &&
+            alloc(c, &S.cost_hist, 128);
   if (!ok) {
     dem_destroy(c);
     return DEM_ERR_CUDA;
@@ -325,6 +326,96 @@ dem_status dem_check(dem_ctx *c, void *stream) {
   if (bits & dem::ERR_DRAIN)
     return fail(c, DEM_ERR_TIMEOUT, "device: bounded wait ran out, and so did the wait for the copy in flight");
   return fail(c, DEM_ERR_TIMEOUT, "device: bounded wait ran out (the copy in flight landed)");
+}
+
+dem_status dem_get_tuning(dem_ctx *c, int32_t kind, dem_tuning *out) {
+  if (!c || !out || kind < 0 || kind >= dem::N_MODES) return DEM_ERR_ARG;
+  const dem::Tune &t = c->S.tune[c->cfg.precision][kind];
+  out->ctas_per_sm = t.ctas_per_sm;
+  out->wflush = t.wflush;
+  out->cost_order = t.order;
+  out->ms = 0.f;
+  return DEM_OK;
+}
+
+dem_status dem_set_tuning(dem_ctx *c, int32_t kind, const dem_tuning *in) {
+  if (!c || !in || kind < 0 || kind >= dem::N_MODES) return DEM_ERR_ARG;
+  if (in->ctas_per_sm < 0 || in->ctas_per_sm > 16 || (in->wflush != 32 && in->wflush != 64) ||
+      (in->cost_order != 0 && in->cost_order != 1))
+    return fail(c, DEM_ERR_ARG, "set_tuning: out of range");
+  dem::Tune &t = c->S.tune[c->cfg.precision][kind];
+  t.ctas_per_sm = in->ctas_per_sm;
+  t.wflush = in->wflush;
+  t.order = in->cost_order;
+  return DEM_OK;
+}
+
+dem_status dem_autotune(dem_ctx *c, int32_t kind, const dem_particles *P, const int32_t *pairs, int64_t max_pairs,
+                        const int64_t *n_pairs, const dem_narrow_out *out, double *t_coll, uint8_t *status,
+                        int32_t *tri_ab, int32_t reps, dem_tuning *best, void *stream) {
+  if (!c) return DEM_ERR_ARG;
+  Range range("dem_autotune");
+  if (kind < 0 || kind >= dem::N_MODES || reps < 1) return fail(c, DEM_ERR_ARG, "autotune: bad kind or reps");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return fail(c, DEM_ERR_ARG, "autotune: stream is being captured");
+  const int method = kind == DEM_TUNE_NARROWING ? DEM_CTIME_NARROWING : DEM_CTIME_SAMPLES;
+  auto run = [&]() -> dem_status {
+    if (kind == DEM_TUNE_NARROW) return dem_narrow_phase(c, P, pairs, max_pairs, n_pairs, nullptr, out, stream);
+    if (kind == DEM_TUNE_DETECT) return dem_detect(c, P, pairs, max_pairs, n_pairs, out, t_coll, status, tri_ab, stream);
+    const int keep = c->cfg.ctime_method;
+    c->cfg.ctime_method = method;
+    const dem_status st = dem_collision_times(c, P, pairs, max_pairs, n_pairs, t_coll, status, tri_ab, stream);
+    c->cfg.ctime_method = keep;
+    return st;
+  };
+  dem::Trace *tr = c->S.trace;
+  c->S.trace = nullptr;  // the tuning runs take no trace records
+  dem::Tune &t = c->S.tune[c->cfg.precision][kind];
+  const dem::Tune saved = t;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    c->S.trace = tr;
+    return fail(c, DEM_ERR_CUDA, "autotune: events");
+  }
+  dem::Tune best_t = saved;
+  float best_ms = 3.0e38f;
+  dem_status st = DEM_OK;
+  for (int order = 0; order < 2 && st == DEM_OK; ++order)
+    for (int wf = 32; wf <= 64 && st == DEM_OK; wf += 32)
+      for (int cps = 1; cps <= 4 && st == DEM_OK; ++cps) {
+        t.ctas_per_sm = cps;
+        t.wflush = wf;
+        t.order = order;
+        float tot = 0.f;
+        for (int r = 0; r <= reps && st == DEM_OK; ++r) {  // run 0 warms up
+          cudaEventRecord(e0, s);
+          st = run();
+          cudaEventRecord(e1, s);
+          if (st == DEM_OK && cudaEventSynchronize(e1) != cudaSuccess) st = DEM_ERR_CUDA;
+          float ms = 0.f;
+          if (st == DEM_OK) cudaEventElapsedTime(&ms, e0, e1);
+          if (r > 0) tot += ms;
+        }
+        if (st == DEM_OK && tot / reps < best_ms) {
+          best_ms = tot / reps;
+          best_t = t;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->S.trace = tr;
+  t = st == DEM_OK ? best_t : saved;
+  if (st != DEM_OK) return st;
+  if (best) {
+    best->ctas_per_sm = t.ctas_per_sm;
+    best->wflush = t.wflush;
+    best->cost_order = t.order;
+    best->ms = best_ms;
+  }
+  return DEM_OK;
 }
 
 dem_status dem_set_wait_polls(dem_ctx *c, int64_t polls) {

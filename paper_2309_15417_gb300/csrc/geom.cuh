@@ -73,6 +73,12 @@ struct Geo {
   static __device__ __forceinline__ T clamp01(T s) {
     return s < T(0) ? T(0) : (s > T(1) ? T(1) : s);
   }
+  // clamp to [0, 1] in the FP32 filter only (binary64: unchanged, the
+  // operation order of the definition)
+  static __device__ __forceinline__ T fp32_clamp01(T s) {
+    if constexpr (sizeof(T) == 4) return clamp01(s);
+    return s;
+  }
 
   // Closest point q of triangle (a,b,c) to p, by Voronoi regions of the
   // triangle (Ericson, Real-Time Collision Detection, Sec. 5.1.5).  e1 = b-a,
@@ -92,7 +98,7 @@ struct Geo {
       } else {
         T vc = O::sub(O::mul(s1, s4), O::mul(s3, s2));
         if (vc <= T(0) && s1 >= T(0) && s3 <= T(0)) {
-          q = axpy(a, e1, O::div(s1, O::sub(s1, s3)));
+          q = axpy(a, e1, fp32_clamp01(O::div(s1, O::sub(s1, s3))));
         } else {
           V pc = sub(p, c);
           T s5 = dot(e1, pc), s6 = dot(e2, pc);
@@ -101,15 +107,21 @@ struct Geo {
           } else {
             T vb = O::sub(O::mul(s5, s2), O::mul(s1, s6));
             if (vb <= T(0) && s2 >= T(0) && s6 <= T(0)) {
-              q = axpy(a, e2, O::div(s2, O::sub(s2, s6)));
+              q = axpy(a, e2, fp32_clamp01(O::div(s2, O::sub(s2, s6))));
             } else {
               T va = O::sub(O::mul(s3, s6), O::mul(s5, s4));
               T u43 = O::sub(s4, s3), u56 = O::sub(s5, s6);
               if (va <= T(0) && u43 >= T(0) && u56 >= T(0)) {
-                q = axpy(b, sub(c, b), O::div(u43, O::add(u43, u56)));
+                q = axpy(b, sub(c, b), fp32_clamp01(O::div(u43, O::add(u43, u56))));
               } else {
                 T sum = O::add(O::add(va, vb), vc);
                 T v = O::div(vb, sum), w = O::div(vc, sum);
+                if constexpr (sizeof(T) == 4) {
+                  // FP32 filter only: barycentric weights in the triangle, so
+                  // q is a point of the triangle up to the rounding of q itself
+                  v = fminf(fmaxf(v, 0.f), 1.f);
+                  w = fminf(fmaxf(w, 0.f), 1.f - v);
+                }
                 q = mk(O::add(O::add(a.x, O::mul(e1.x, v)), O::mul(e2.x, w)),
                        O::add(O::add(a.y, O::mul(e1.y, v)), O::mul(e2.y, w)),
                        O::add(O::add(a.z, O::mul(e1.z, v)), O::mul(e2.z, w)));
@@ -170,7 +182,7 @@ struct Geo {
     T sp = dot(nrm, sub(p, a)), sq = dot(nrm, sub(q, a));
     if ((sp > T(0) && sq > T(0)) || (sp < T(0) && sq < T(0)) || (sp == T(0) && sq == T(0)))
       return false;
-    T t = O::div(sp, O::sub(sp, sq));
+    T t = fp32_clamp01(O::div(sp, O::sub(sp, sq)));
     x = axpy(p, sub(q, p), t);
     T g0 = dot(cross(sub(b, a), sub(x, a)), nrm);
     T g1 = dot(cross(sub(c, b), sub(x, b)), nrm);
@@ -183,13 +195,21 @@ struct Geo {
   // then of B against A) as both points.  Otherwise the first minimum, under
   // strict "<", in the order: vertices of A against B, vertices of B against
   // A, edge i of A against edge j of B (i major).
+  // Feature ids (the order of the definition): 0..2 vertex i of A against
+  // B, 3..5 vertex j of B against A, 6 + 3 i + j edge i of A against edge j
+  // of B, 15 + i edge i of A crossing B, 18 + j edge j of B crossing A.
   static __device__ __forceinline__ T tri_dist2(const V A[3], const V B[3], V &pa, V &pb) {
+    int f;
+    return tri_dist2(A, B, pa, pb, f);
+  }
+  static __device__ __forceinline__ T tri_dist2(const V A[3], const V B[3], V &pa, V &pb, int &feat) {
     V x;
 #pragma unroll 1
     for (int i = 0; i < 3; ++i)
       if (seg_tri_cross(A[i], A[i == 2 ? 0 : i + 1], B[0], B[1], B[2], x)) {
         pa = x;
         pb = x;
+        feat = 15 + i;
         return T(0);
       }
 #pragma unroll 1
@@ -197,15 +217,21 @@ struct Geo {
       if (seg_tri_cross(B[j], B[j == 2 ? 0 : j + 1], A[0], A[1], A[2], x)) {
         pa = x;
         pb = x;
+        feat = 18 + j;
         return T(0);
       }
-    return tri_dist2_features(A, B, pa, pb);
+    return tri_dist2_features(A, B, pa, pb, feat);
   }
 
   // Minimum over the 15 vertex-triangle and edge-edge feature pairs only.
   static __device__ __forceinline__ T tri_dist2_features(const V A[3], const V B[3], V &pa, V &pb) {
+    int f;
+    return tri_dist2_features(A, B, pa, pb, f);
+  }
+  static __device__ __forceinline__ T tri_dist2_features(const V A[3], const V B[3], V &pa, V &pb, int &feat) {
     T best = O::inf();
     V q, c1, c2;
+    feat = 0;
 #pragma unroll 1
     for (int i = 0; i < 3; ++i) {
       T d2 = closest_pt_tri(A[i], B[0], B[1], B[2], q);
@@ -213,6 +239,7 @@ struct Geo {
         best = d2;
         pa = A[i];
         pb = q;
+        feat = i;
       }
     }
 #pragma unroll 1
@@ -222,6 +249,7 @@ struct Geo {
         best = d2;
         pa = q;
         pb = B[j];
+        feat = 3 + j;
       }
     }
 #pragma unroll 1
@@ -233,11 +261,68 @@ struct Geo {
           best = d2;
           pa = c1;
           pb = c2;
+          feat = 6 + 3 * i + j;
         }
       }
     return best;
   }
+
+  // One feature's squared distance and points, computed exactly as the full
+  // routine computes that feature (so in binary64 it is the definition's
+  // value for that feature); a crossing feature gives 0 and the crossing
+  // point if the edge crosses, else infinity.
+  static __device__ __forceinline__ T feature_dist2(int f, const V A[3], const V B[3], V &pa, V &pb) {
+    if (f < 3) {
+      pa = A[f];
+      return closest_pt_tri(A[f], B[0], B[1], B[2], pb);
+    }
+    if (f < 6) {
+      pb = B[f - 3];
+      return closest_pt_tri(B[f - 3], A[0], A[1], A[2], pa);
+    }
+    if (f < 15) {
+      const int i = (f - 6) / 3, j = (f - 6) % 3;
+      return seg_seg(A[i], A[i == 2 ? 0 : i + 1], B[j], B[j == 2 ? 0 : j + 1], pa, pb);
+    }
+    V x{T(0), T(0), T(0)};
+    bool hit;
+    if (f < 18) {
+      const int i = f - 15;
+      hit = seg_tri_cross(A[i], A[i == 2 ? 0 : i + 1], B[0], B[1], B[2], x);
+    } else {
+      const int j = f - 18;
+      hit = seg_tri_cross(B[j], B[j == 2 ? 0 : j + 1], A[0], A[1], A[2], x);
+    }
+    pa = x;
+    pb = x;
+    return hit ? T(0) : O::inf();
+  }
 };
+
+// ---------------------------------------------------------------------------
+// Separation certificates (FP32 filter).  For any direction n and convex
+// sets P, Q: d(P, Q) >= (min over Q of n.y - max over P of n.x) / |n|, and
+// for a triangle or a segment the extremes are at its vertices.  With n the
+// difference of two computed closest points the bound is close to the
+// distance; it is a lower bound whatever n is, so the FP32 decisions built on
+// it need no assumption on how accurately the closest points were found.
+// Returned raw: the caller subtracts the rounding margin of these dot
+// products, the norm and the FP32 relative pose (E of the pair kernel).
+__device__ __forceinline__ float cert_dot(V3<float> n, V3<float> v) {
+  return fmaf(n.z, v.z, fmaf(n.y, v.y, n.x * v.x));
+}
+__device__ __forceinline__ float cert_scale(float gap, V3<float> n) {
+  const float nn = cert_dot(n, n);
+  if (!(nn > 1e-30f)) return -OpsF::inf();
+  return gap * rsqrtf(nn);
+}
+// P = {p1..pk} (k = np points), Q = {q1..qm}: separation along n
+__device__ __forceinline__ float cert_sep(const V3<float> *P, int np, const V3<float> *Q, int nq, V3<float> n) {
+  float mx = -OpsF::inf(), mn = OpsF::inf();
+  for (int k = 0; k < np; ++k) mx = fmaxf(mx, cert_dot(n, P[k]));
+  for (int k = 0; k < nq; ++k) mn = fminf(mn, cert_dot(n, Q[k]));
+  return cert_scale(mn - mx, n);
+}
 
 // ---------------------------------------------------------------------------
 // Free-flight pose at time t in binary64, every operation rounded on its own

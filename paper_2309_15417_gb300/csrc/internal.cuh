@@ -65,8 +65,23 @@ struct Trace {
   int32_t *site = nullptr;        // [cap] launch group of each record
 };
 
+// launch configuration of the pair kernel, per precision and mode
+// (autotuned by dem_autotune): CTAs per SM of the persistent grid (0 = as
+// many as fit), warp candidate-list flush size, pairs handed out costliest
+// first (by triangle counts) or in index order
+struct Tune {
+  int ctas_per_sm = 0;
+  int wflush = 64;
+  int order = 1;
+};
+constexpr int N_MODES = 4;  // narrow phase, collision times, both, narrowing
+
 struct Scratch {
   Trace *trace = nullptr;         // launch-group timing (null: off)
+  Tune tune[2][N_MODES];          // [precision][mode]
+  int32_t *order = nullptr;       // [cap_pairs] hand-out order of the pair kernel
+  uint8_t *cost_bucket = nullptr; // [cap_pairs] cost class of each pair
+  unsigned int *cost_hist = nullptr;  // [128] counts (64) and cursors (64) of the cost classes
   int64_t launches = 0;           // host-side count of kernel launches issued
   uint32_t wait_polls = WAIT_POLLS_DEFAULT;  // first bounded wait of the pair kernel's tile copies
   // common

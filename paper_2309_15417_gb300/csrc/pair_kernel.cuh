@@ -43,7 +43,7 @@ constexpr int H = 8;         // triangles per subgroup
 constexpr int WCAP = 96;     // per-warp candidate list capacity
 constexpr int XQCAP = 64;    // per-warp binary64 queue capacity
 constexpr int ACAP = 512;    // closest-pair candidates per evaluation
-constexpr int WFLUSH = 64;   // a warp evaluates its candidate list at this size
+constexpr int WFLUSH = 64;   // default: a warp evaluates its candidate list at this size (<= WCAP - 32)
 constexpr int QWARP = 12;    // binary64 queues up to this size run one triangle pair per warp
 constexpr int GRID_MAX = 16; // sample times whose poses are computed up front
 constexpr int ILCAP = 512;   // triangle pairs of the pair-interval candidate list
@@ -119,6 +119,11 @@ struct PairArgs {
   uint32_t *err;
   unsigned long long *stats;
   uint32_t wait_polls;  // polls of the first wait on a tile copy
+  // launch configuration (autotuned per context): hand-out order of the pairs
+  // (NULL: index order), warp candidate-list flush size, CTAs per SM
+  const int32_t *order;
+  int wflush;
+  int ctas_per_sm;
 };
 
 template <int PREC>
@@ -1157,7 +1162,7 @@ struct Cta {
           if (cand) s.wl[w][cnt + __popc(m & lanemask_lt())] = (uint32_t(a) << 16) | uint32_t(b);
           cnt += __popc(m);
           __syncwarp();
-          if (cnt >= WFLUSH) {
+          if (cnt >= A.wflush) {
             warp_eval<DECIDE, ARGMIN, CONTACTS>(s.wl[w], cnt, ta, tb, pk, pass1);
             cnt = 0;
             __syncwarp();
@@ -1945,7 +1950,19 @@ __global__ void __launch_bounds__(Cfg<PREC>::NT, Cfg<PREC>::MINB) pair_kernel(Pa
   __syncthreads();
   const int64_t m = pair_count(A);
   for (;;) {
-    if (c.tid == 0) s.work_item = atomicAdd(A.work, 1u);
+    if (c.tid == 0) {
+      const unsigned int q = atomicAdd(A.work, 1u);
+      // the q-th pair handed out: in the given order (costliest first), else q
+      int64_t k = q;
+      if (A.order && (int64_t)q < m) {
+        k = A.order[q];
+        if (k < 0 || k >= m) {  // not a permutation of the pairs: report and stop
+          set_err(A.err, ERR_INDEX);
+          k = m;
+        }
+      }
+      s.work_item = (unsigned int)((int64_t)q >= m ? m : k);
+    }
     __syncthreads();
     const int64_t k = s.work_item;
     const bool quit = s.abort != 0;
@@ -2173,7 +2190,8 @@ cudaError_t launch_pairs(const PairArgs &a, int num_sms, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     per_sm = q < 1 ? 1 : q;
   }
-  int64_t grid = (int64_t)num_sms * per_sm;
+  const int want = a.ctas_per_sm > 0 && a.ctas_per_sm < per_sm ? a.ctas_per_sm : per_sm;
+  int64_t grid = (int64_t)num_sms * want;
   if (a.max_pairs < grid) grid = a.max_pairs > 0 ? a.max_pairs : 1;
   pair_kernel<PREC, MODE><<<(unsigned)grid, Cfg<PREC>::NT, smem, s>>>(a);
   return cudaGetLastError();

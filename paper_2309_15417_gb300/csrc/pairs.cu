@@ -207,9 +207,68 @@ cudaError_t prepare_tiles(const dem_particles &P, Scratch &S, cudaStream_t s) {
 }
 
 
+// Hand-out order of the persistent pair kernel: pairs by decreasing cost
+// class (leading zeros of T_i * T_j, so each class spans a factor of two),
+// a counting sort over 64 classes; the order inside a class is that of the
+// atomic cursors (it does not affect any result, only the schedule).
+__global__ void k_cost_class(const int32_t *pairs, const int64_t *n_pairs, int64_t max_pairs,
+                             const int64_t *tri_off, int64_t n, uint8_t *bucket, unsigned int *hist) {
+  int64_t m = max_pairs;
+  if (n_pairs) m = min(m, *n_pairs);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = pairs[2 * k], j = pairs[2 * k + 1];
+    unsigned long long cost = 0;
+    if (i >= 0 && j >= 0 && i < n && j < n) {
+      const int64_t a = tri_off[i + 1] - tri_off[i], b = tri_off[j + 1] - tri_off[j];
+      if (a > 0 && b > 0) cost = (unsigned long long)a * (unsigned long long)b;
+    }
+    const int c = cost ? __clzll(cost) : 63;  // 0 .. 63, costliest first
+    bucket[k] = uint8_t(c);
+    atomicAdd(&hist[c], 1u);
+  }
+}
+
+__global__ void k_cost_offsets(unsigned int *hist) {
+  if (threadIdx.x == 0) {
+    unsigned int acc = 0;
+    for (int c = 0; c < 64; ++c) {
+      const unsigned int v = hist[c];
+      hist[c] = acc;       // start of class c
+      hist[64 + c] = 0u;   // its cursor
+      acc += v;
+    }
+  }
+}
+
+__global__ void k_cost_scatter(const int64_t *n_pairs, int64_t max_pairs, const uint8_t *bucket, unsigned int *hist,
+                               int32_t *order) {
+  int64_t m = max_pairs;
+  if (n_pairs) m = min(m, *n_pairs);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+    const int c = bucket[k];
+    order[hist[c] + atomicAdd(&hist[64 + c], 1u)] = int32_t(k);
+  }
+}
+
+cudaError_t prepare_order(const dem_particles &P, const int32_t *pairs, int64_t max_pairs, const int64_t *n_pairs,
+                          Scratch &S, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(S.cost_hist, 0, sizeof(unsigned int) * 128, s);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)((max_pairs + 255) / 256);
+  k_cost_class<<<grid, 256, 0, s>>>(pairs, n_pairs, max_pairs, P.tri_off, P.n, S.cost_bucket, S.cost_hist);
+  k_cost_offsets<<<1, 32, 0, s>>>(S.cost_hist);
+  k_cost_scatter<<<grid, 256, 0, s>>>(n_pairs, max_pairs, S.cost_bucket, S.cost_hist, S.order);
+  S.launches += 3;
+  return cudaGetLastError();
+}
+
 PairArgs make_args(const dem_particles &P, const int32_t *pairs, int64_t max_pairs, const int64_t *n_pairs,
-                   Scratch &S) {
+                   Scratch &S, int prec, int mode) {
   PairArgs a{};
+  const Tune &t = S.tune[prec][mode];
+  a.order = t.order ? S.order : nullptr;
+  a.wflush = t.wflush == 32 ? 32 : 64;
+  a.ctas_per_sm = t.ctas_per_sm;
   a.n = P.n;
   a.st = P.state;
   a.is_static = P.is_static;
@@ -245,6 +304,7 @@ cudaError_t finish_narrow(int prec, PairArgs &a, const dem_particles &P, const i
     if ((e = cudaMemsetAsync(S.pc, 0, sizeof(int64_t) * max_pairs, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(S.pcur, 0, sizeof(int32_t) * max_pairs, s)) != cudaSuccess) return e;
     if ((e = prepare_tiles(P, S, s)) != cudaSuccess) return e;
+    if (a.order && (e = prepare_order(P, pairs, max_pairs, n_pairs, S, s)) != cudaSuccess) return e;
     const int rec = trace_begin(S, TR_PAIRS, s);
     if (fused)
       e = prec == 0 ? launch_pairs<0, MODE_BOTH>(a, num_sms, s) : launch_pairs<1, MODE_BOTH>(a, num_sms, s);
@@ -279,7 +339,7 @@ cudaError_t finish_narrow(int prec, PairArgs &a, const dem_particles &P, const i
 cudaError_t launch_narrow(int prec, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
                           const int64_t *n_pairs, const double *t_eval, const dem_narrow_out &out,
                           Scratch &S, int num_sms, cudaStream_t s) {
-  PairArgs a = make_args(P, pairs, max_pairs, n_pairs, S);
+  PairArgs a = make_args(P, pairs, max_pairs, n_pairs, S, prec, MODE_NARROW);
   a.t_eval = t_eval;
   a.dmin = out.dmin;
   a.pa = out.pa;
@@ -298,7 +358,7 @@ cudaError_t launch_narrow(int prec, const dem_particles &P, const int32_t *pairs
 cudaError_t launch_detect(int prec, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
                           const int64_t *n_pairs, const dem_narrow_out &out, int K, double tol, double *t_coll,
                           uint8_t *status, int32_t *tri_ab, Scratch &S, int num_sms, cudaStream_t s) {
-  PairArgs a = make_args(P, pairs, max_pairs, n_pairs, S);
+  PairArgs a = make_args(P, pairs, max_pairs, n_pairs, S, prec, MODE_BOTH);
   a.dmin = out.dmin;
   a.pa = out.pa;
   a.pb = out.pb;
@@ -321,7 +381,8 @@ cudaError_t launch_detect(int prec, const dem_particles &P, const int32_t *pairs
 cudaError_t launch_ctime(int prec, int method, const dem_particles &P, const int32_t *pairs, int64_t max_pairs,
                          const int64_t *n_pairs, int K, double tol, double *t_coll, uint8_t *status,
                          int32_t *tri_ab, Scratch &S, int num_sms, cudaStream_t s) {
-  PairArgs a = make_args(P, pairs, max_pairs, n_pairs, S);
+  PairArgs a = make_args(P, pairs, max_pairs, n_pairs, S, prec,
+                         method == DEM_CTIME_NARROWING ? MODE_NTIME : MODE_CTIME);
   a.t_coll = t_coll;
   a.status = status;
   a.ct_ab = tri_ab;
@@ -331,6 +392,7 @@ cudaError_t launch_ctime(int prec, int method, const dem_particles &P, const int
   if ((e = cudaMemsetAsync(S.work, 0, sizeof(unsigned int), s)) != cudaSuccess) return e;
   if (max_pairs <= 0) return cudaSuccess;
   if ((e = prepare_tiles(P, S, s)) != cudaSuccess) return e;
+  if (a.order && (e = prepare_order(P, pairs, max_pairs, n_pairs, S, s)) != cudaSuccess) return e;
   S.launches += 1;
   const int rec = trace_begin(S, TR_PAIRS, s);
   if (method == DEM_CTIME_NARROWING)

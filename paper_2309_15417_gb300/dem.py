@@ -34,7 +34,7 @@ STATUS = {0: "DEM_OK", -1: "DEM_ERR_ARG", -2: "DEM_ERR_CAPACITY", -3: "DEM_ERR_C
 EXPORTS = ["dem_create", "dem_destroy", "dem_last_error", "dem_build_candidates", "dem_narrow_phase",
            "dem_collision_times", "dem_detect", "dem_clusters", "dem_lts_sweep", "dem_check", "dem_get_stats",
            "dem_build_candidates_noalloc", "dem_noalloc_check", "dem_set_wait_polls", "dem_trace",
-           "dem_trace_read",
+           "dem_trace_read", "dem_autotune", "dem_get_tuning", "dem_set_tuning",
            # include/dem_probe.h (measurement support)
            "dem_probe_fma_peak", "dem_count_dist_flops"]
 DEM_NOALLOC_MAX_PARTICLES = 16384
@@ -78,6 +78,16 @@ class dem_lts_out(C.Structure):
                 ("status", C.c_void_p), ("tri_ab", C.c_void_p), ("cluster_id", C.c_void_p),
                 ("n_clusters", C.c_void_p), ("active", C.c_void_p), ("t_global", C.c_void_p),
                 ("narrow", C.c_void_p)]
+
+
+class dem_tuning(C.Structure):
+    _fields_ = [("ctas_per_sm", C.c_int32), ("wflush", C.c_int32), ("cost_order", C.c_int32), ("ms", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+DEM_TUNE_NARROW, DEM_TUNE_CTIME, DEM_TUNE_DETECT, DEM_TUNE_NARROWING = 0, 1, 2, 3
 
 
 class dem_stats(C.Structure):
@@ -146,6 +156,13 @@ def load(build_if_needed: bool = True):
         L.dem_trace_read.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_float), C.c_int32,
                                      C.POINTER(C.c_int32)]
         L.dem_trace_read.restype = C.c_int
+        L.dem_autotune.argtypes = [vp, C.c_int32, C.POINTER(dem_particles), vp, i64, vp, C.POINTER(dem_narrow_out),
+                                   vp, vp, vp, C.c_int32, C.POINTER(dem_tuning), vp]
+        L.dem_autotune.restype = C.c_int
+        L.dem_get_tuning.argtypes = [vp, C.c_int32, C.POINTER(dem_tuning)]
+        L.dem_get_tuning.restype = C.c_int
+        L.dem_set_tuning.argtypes = [vp, C.c_int32, C.POINTER(dem_tuning)]
+        L.dem_set_tuning.restype = C.c_int
         L.dem_probe_fma_peak.argtypes = [C.c_int32, C.c_int32, vp, C.POINTER(C.c_double)]
         L.dem_probe_fma_peak.restype = C.c_int
         L.dem_count_dist_flops.argtypes = [vp, i64, vp, vp]
@@ -267,6 +284,26 @@ def dem_check(ctx, stream=None):
 
 def dem_set_wait_polls(ctx, polls: int):
     _check(ctx, load().dem_set_wait_polls(ctx, int(polls)))
+
+
+def dem_autotune(ctx, kind, P: dem_particles, pairs, max_pairs: int, n_pairs, out, t_coll, status, tri_ab,
+                 reps: int = 1, stream=None) -> dict:
+    best = dem_tuning()
+    _check(ctx, load().dem_autotune(ctx, int(kind), C.byref(P), _ptr(pairs), int(max_pairs), _ptr(n_pairs),
+                                    C.byref(out) if out is not None else None, _ptr(t_coll), _ptr(status),
+                                    _ptr(tri_ab), int(reps), C.byref(best), _stream(stream)))
+    return best.as_dict()
+
+
+def dem_get_tuning(ctx, kind) -> dict:
+    t = dem_tuning()
+    _check(ctx, load().dem_get_tuning(ctx, int(kind), C.byref(t)))
+    return t.as_dict()
+
+
+def dem_set_tuning(ctx, kind, ctas_per_sm=0, wflush=64, cost_order=1):
+    t = dem_tuning(ctas_per_sm=ctas_per_sm, wflush=wflush, cost_order=cost_order)
+    _check(ctx, load().dem_set_tuning(ctx, int(kind), C.byref(t)))
 
 
 def dem_trace(ctx, cap: int):
@@ -434,6 +471,22 @@ class Context:
 
     def check(self, stream=None):
         dem_check(self.h, stream)
+
+    def autotune(self, scene: Scene, kind=DEM_TUNE_DETECT, pairs=None, n_pairs=None, reps=1, stream=None):
+        """Tune the pair kernel's launch configuration for `kind` on these pairs
+        (default: the context's candidate pairs); returns the chosen one."""
+        if pairs is None:
+            pairs, m, cnt = self.pairs, self.max_pairs, self.n_pairs
+        else:
+            m, cnt = int(pairs.shape[0]), n_pairs
+        return dem_autotune(self.h, kind, scene.P, pairs, m, cnt, self.out, self.t_coll, self.status, self.ct_ab,
+                            reps, stream)
+
+    def get_tuning(self, kind=DEM_TUNE_DETECT):
+        return dem_get_tuning(self.h, kind)
+
+    def set_tuning(self, kind=DEM_TUNE_DETECT, **kw):
+        dem_set_tuning(self.h, kind, **kw)
 
     def set_wait_polls(self, polls: int):
         dem_set_wait_polls(self.h, polls)

@@ -37,7 +37,8 @@ def test_struct_layouts_match_header(tmp_path):
     """Every field of the Python mirrors sits at the offset the C compiler
     gives it for include/dem.h, and the structs have the same sizes."""
     import subprocess
-    structs = [D.dem_config, D.dem_particles, D.dem_narrow_out, D.dem_stats, D.dem_lts_params, D.dem_lts_out]
+    structs = [D.dem_config, D.dem_particles, D.dem_narrow_out, D.dem_stats, D.dem_lts_params, D.dem_lts_out,
+               D.dem_tuning]
     lines = ['#include <stdio.h>', '#include "dem.h"', 'int main(void) {']
     for S in structs:
         name = S.__name__

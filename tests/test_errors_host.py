@@ -34,6 +34,9 @@ def test_null_context_is_an_argument_error(L):
         L.dem_set_wait_polls(None, 10),
         L.dem_trace(None, 4),
         L.dem_trace_read(None, site, ms, 4, C.byref(n)),
+        L.dem_autotune(None, 2, C.byref(P), None, 0, None, C.byref(out), None, None, None, 1, None, None),
+        L.dem_get_tuning(None, 2, C.byref(D.dem_tuning())),
+        L.dem_set_tuning(None, 2, C.byref(D.dem_tuning(wflush=64, cost_order=1))),
     ]
     assert calls == [D.DEM_ERR_ARG] * len(calls)
     assert L.dem_last_error(None) == b"null context"

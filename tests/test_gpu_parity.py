@@ -163,32 +163,42 @@ def test_narrow_dense_subset(dem, prec):
     assert_narrow_equal(g, o, w, pairs, prec)
 
 
+_DENSE_ORACLE = {}
+
+
+def _dense_oracle():
+    """The oracle's narrow phase and collision times of every candidate pair of
+    the dense packing (computed once per session: ~5e8 triangle-pair distances)."""
+    if not _DENSE_ORACLE:
+        w = W.dense_packing(0)
+        pairs = oracle.broad_phase(w)
+        _DENSE_ORACLE.update(w=w, pairs=pairs, on=oracle.narrow_phase(w, pairs), oc=oracle.collision_times(w, pairs))
+    return _DENSE_ORACLE
+
+
 @pytest.mark.parametrize("prec", PRECS)
-def test_narrow_dense_full_size_sampled(dem, prec):
-    """1000 icospheres (320 triangles): the GPU runs every candidate pair; the
-    oracle checks a seeded sample of them one by one."""
-    w = W.dense_packing(0)
-    pairs = oracle.broad_phase(w)
-    g = gpu_narrow(dem, w, pairs, prec)
-    rng = np.random.default_rng(7)
-    idx = np.sort(rng.choice(len(pairs), 24, replace=False))
-    o = oracle.narrow_phase(w, pairs[idx])
-    for key in ("flag", "tri_ab", "dmin", "pa", "pb"):
-        assert np.array_equal(g[key][idx], o[key]), key
-    # contacts of the sampled pairs
-    gk = g["contacts"]
-    sel = np.isin(gk[:, 0], idx)
-    remap = {int(k): n for n, k in enumerate(idx)}
-    gsub = gk[sel].copy()
-    gsub[:, 0] = [remap[int(k)] for k in gsub[:, 0]]
-    assert np.array_equal(gsub, o["contacts"])
-    R = 1.0
-    if prec == 1:
-        assert np.array_equal(g["geom"][sel], o["geom"])
-    else:
-        assert_contact_geometry(gsub, g["geom"][sel], o["geom"], w, pairs[idx], None, 1e-5 * R)
-    # contact counts of all pairs are consistent with the sorted output
-    assert np.all(np.diff(gk[:, 0]) >= 0)
+def test_dense_full_size_exhaustive(dem, prec):
+    """1000 icospheres (320 triangles), the benchmark's dense packing: every
+    candidate pair, narrow phase at the pair start and collision times in one
+    launch (dem_detect), against the oracle pair by pair."""
+    d = _dense_oracle()
+    w, pairs, on, oc = d["w"], d["pairs"], d["on"], d["oc"]
+    c = _ctx(dem, w, prec, max_pairs=len(pairs))
+    sc = dem.Scene.from_workload(w)
+    c.build_candidates(sc)
+    c.detect(sc)
+    c.check()
+    m = int(c.n_pairs.item())
+    assert np.array_equal(c.pairs[:m].cpu().numpy(), pairs)
+    nc = int(c.n_contacts.item())
+    g = dict(dmin=c.dmin[:m].cpu().numpy(), pa=c.pa[:m].cpu().numpy(), pb=c.pb[:m].cpu().numpy(),
+             tri_ab=c.tri_ab[:m].cpu().numpy(), flag=c.flag[:m].cpu().numpy(), dmin32=c.dmin32[:m].cpu().numpy(),
+             contacts=c.contacts[:nc].cpu().numpy(), geom=c.contact_geom[:nc].cpu().numpy())
+    assert_narrow_equal(g, on, w, pairs, prec)
+    assert np.array_equal(c.status[:m].cpu().numpy(), oc["status"])
+    assert np.array_equal(c.t_coll[:m].cpu().numpy(), oc["t_coll"])
+    assert np.array_equal(c.ct_ab[:m].cpu().numpy(), oc["tri_ab"])
+    c.close()
 
 
 @pytest.mark.parametrize("prec", PRECS)

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
+from floor_oracle import floor_pair_oracle
 from paper_2309_15417_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -116,13 +117,69 @@ def test_settling_column_full_size(dem):
         assert np.array_equal(oracle.broad_partners(w, int(p)), gp), p
     ids, nc = oracle.clusters(w.n, pairs, w.is_static)
     assert np.array_equal(g["ids"], ids) and g["n_clusters"] == nc
-    # sampled pairs: floor pairs in contact at the start (status 1), two that
-    # are not, and pairs between lattice neighbours
+    # a few hundred pairs between particles, one by one against the oracle
+    others = np.where(pairs[:, 1] != floor)[0]
+    _check_sampled_pairs(w, g, np.sort(rng.choice(others, 240, replace=False)))
+    # floor pairs: every one whose search bisected (status 2), and sampled
+    # ones in contact at the start and apart, each on its reduced floor
     fl = np.where(pairs[:, 1] == floor)[0]
     touching = fl[g["flag"][fl] == 1]
     apart = fl[g["flag"][fl] == 0]
-    assert len(touching) > 100
-    others = np.where(pairs[:, 1] != floor)[0]
-    idx = np.unique(np.concatenate([rng.choice(touching, 6, replace=False), rng.choice(apart, 2, replace=False),
-                                    rng.choice(others, 12, replace=False)]))
-    _check_sampled_pairs(w, g, idx)
+    bis = fl[g["status"][fl] == 2]
+    assert len(touching) > 100 and len(apart) > 100
+    gk = g["contacts"]
+    for k in np.unique(np.concatenate([bis, rng.choice(touching, 40, replace=False),
+                                       rng.choice(apart, 40, replace=False)])):
+        on, oc, kept = floor_pair_oracle(w, int(pairs[k, 0]), floor)
+        for key in ("flag", "tri_ab", "dmin", "pa", "pb"):
+            assert np.array_equal(g[key][k:k + 1], on[key]), (k, key)
+        assert g["status"][k] == oc["status"][0] and g["t_coll"][k] == oc["t_coll"][0], k
+        assert np.array_equal(g["ct_ab"][k], oc["tri_ab"][0]), k
+        sub = gk[gk[:, 0] == k][:, 1:]
+        assert np.array_equal(sub, on["contacts"][:, 1:]), k
+        assert 0 < kept < 2000
+
+
+def test_every_launch_configuration_gives_identical_results(dem):
+    """The autotuner's space (CTAs per SM, warp flush size, costliest-first or
+    index hand-out) changes only the schedule: on the uneven-mesh batch every
+    configuration gives the same outputs bit for bit, equal to the oracle on
+    the costliest pairs; dem_autotune keeps one of them."""
+    w = W.uneven_meshes(2, n=2000, box=80.0)
+    sc = dem.Scene.from_workload(w)
+    c = dem.Context(K=w.K, tol=w.tol, max_particles=w.n, max_pairs=1 << 16, max_contacts=1 << 20,
+                    max_triangles=w.n_tris)
+    c.build_candidates(sc)
+    c.check()
+    m = int(c.n_pairs.item())
+    assert m > 20
+
+    def outputs():
+        nc = int(c.n_contacts.item())
+        return [t.cpu().numpy().copy() for t in (c.dmin[:m], c.tri_ab[:m], c.flag[:m], c.t_coll[:m], c.status[:m],
+                                                c.ct_ab[:m], c.contacts[:nc])]
+
+    ref = None
+    for order in (0, 1):
+        for wf in (32, 64):
+            for cps in (1, 4):
+                c.set_tuning(dem.DEM_TUNE_DETECT, ctas_per_sm=cps, wflush=wf, cost_order=order)
+                c.detect(sc)
+                c.check()
+                got = outputs()
+                if ref is None:
+                    ref = got
+                assert all(np.array_equal(a, b) for a, b in zip(ref, got)), (order, wf, cps)
+    best = c.autotune(sc, dem.DEM_TUNE_DETECT)
+    assert best["wflush"] in (32, 64) and best["cost_order"] in (0, 1) and 1 <= best["ctas_per_sm"] <= 4
+    assert c.get_tuning(dem.DEM_TUNE_DETECT)["ctas_per_sm"] == best["ctas_per_sm"]
+    got = outputs()
+    assert all(np.array_equal(a, b) for a, b in zip(ref, got))
+    c.check()
+    pairs = c.pairs[:m].cpu().numpy()
+    cnt = w.tri_counts()
+    idx = np.sort(np.argsort(-(cnt[pairs[:, 0]] * cnt[pairs[:, 1]]))[:6])
+    on, oc = oracle.narrow_phase(w, pairs[idx]), oracle.collision_times(w, pairs[idx])
+    assert np.array_equal(ref[0][idx], on["dmin"]) and np.array_equal(ref[4][idx], oc["status"])
+    assert np.array_equal(ref[3][idx], oc["t_coll"])
+    c.close()
