@@ -122,6 +122,10 @@ typedef struct {
   int64_t max_contacts;  /* capacity: contact staging per narrow-phase call (0 -> 1<<20) */
   int64_t max_triangles; /* capacity: n_tris per call (0 -> 1280 * max_particles); sizes the
                             bounding spheres of the 320-triangle tiles of large meshes */
+  int64_t list_spill;    /* collision times: triangle pairs per persistent CTA that the pair-interval
+                            list (the triangle pairs that can meet within a pair's interval) keeps in
+                            global memory beyond the 512 held in shared memory (0 -> 8192; a longer
+                            list makes that pair's evaluations visit every triangle pair, culled) */
 } dem_config;
 
 /* Outputs of dem_narrow_phase.  Per pair k (M = pair count):
@@ -137,7 +141,11 @@ typedef struct {
  * Contacts: every triangle pair with distance <= eps_i + eps_j, sorted by
  * (pair, a, b): contacts[3c..] = (pair index k, a, b) int32,
  * contact_geom[7c..] = (d, pa.xyz, pb.xyz) FP64 world.  *n_contacts (device)
- * receives the total; only min(total, contact_cap) are written. */
+ * receives the total; only min(total, contact_cap) are written.  When the
+ * context's contact staging (max_contacts) overflows, dem_check reports
+ * DEM_ERR_CAPACITY and *n_contacts is a capacity that suffices for a re-call
+ * (the FP32 mode stages candidates before deciding them in binary64, so this
+ * can exceed the final count). */
 typedef struct {
   double *dmin;
   double *pa;

@@ -132,9 +132,11 @@ dem_status dem_create(const dem_config *cfg, dem_ctx **out) {
   if (k.max_pairs == 0) k.max_pairs = 1 << 20;
   if (k.max_contacts == 0) k.max_contacts = 1 << 20;
   if (k.max_triangles == 0) k.max_triangles = 1280 * k.max_particles;
+  if (k.list_spill == 0) k.list_spill = 8192;
   if (k.K < 1 || !(k.bisect_tol > 0.0) || (k.precision != DEM_PREC_FP32_FIXUP && k.precision != DEM_PREC_FP64) ||
       (k.ctime_method != DEM_CTIME_SAMPLES && k.ctime_method != DEM_CTIME_NARROWING) ||
-      k.max_particles < 0 || k.max_pairs < 0 || k.max_contacts < 0 || k.max_triangles < 0 ||
+      k.max_particles < 0 || k.max_pairs < 0 || k.max_contacts < 0 || k.max_triangles < 0 || k.list_spill < 0 ||
+      k.list_spill > ((int64_t)1 << 24) ||
       k.max_triangles > ((int64_t)1 << 40) ||
       k.max_particles > (int64_t)(dem::SCAN_BLOCK * dem::SCAN_PART_CAP / 2) ||
       k.max_pairs > (int64_t)(dem::SCAN_BLOCK * dem::SCAN_PART_CAP) || k.max_contacts > ((int64_t)1 << 31) - 1) {
@@ -168,7 +170,9 @@ dem_status dem_create(const dem_config *cfg, dem_ctx **out) {
             alloc(c, &S.sidx, nc) && alloc(c, &S.tile_sph, S.cap_tiles) && alloc(c, &S.tile_box, 2 * S.cap_tiles) && alloc(c, &S.tile_list, S.cap_tiles) && alloc(c, &S.lts_tmin, np) &&
             alloc(c, &S.lts_step, np) && alloc(c, &S.lts_tnew, np) && alloc(c, &S.lts_tglob, 1) &&
             alloc(c, &S.lts_touch, np) && alloc(c, &S.order, nq) && alloc(c, &S.cost_bucket, nq) &&
-            alloc(c, &S.cost_hist, 128);
+            alloc(c, &S.cost_hist, 128) &&
+            alloc(c, &S.ilg, (size_t)c->num_sms * dem::MAX_PAIR_CTAS_PER_SM * (size_t)k.list_spill);
+  S.ilg_cap = k.list_spill;
   if (!ok) {
     dem_destroy(c);
     return DEM_ERR_CUDA;

@@ -80,6 +80,8 @@ struct Scratch {
   Trace *trace = nullptr;         // launch-group timing (null: off)
   Tune tune[2][N_MODES];          // [precision][mode]
   int32_t *order = nullptr;       // [cap_pairs] hand-out order of the pair kernel
+  unsigned long long *ilg = nullptr;  // [MAX_PAIR_CTAS][ilg_cap] spill of the pair-interval lists
+  int64_t ilg_cap = 0;
   uint8_t *cost_bucket = nullptr; // [cap_pairs] cost class of each pair
   unsigned int *cost_hist = nullptr;  // [128] counts (64) and cursors (64) of the cost classes
   int64_t launches = 0;           // host-side count of kernel launches issued
@@ -139,6 +141,7 @@ struct Scratch {
 };
 
 constexpr int TILE_TRIS = 320;                 // triangles per shared-memory tile of the pair kernel
+constexpr int MAX_PAIR_CTAS_PER_SM = 4;        // persistent CTAs of the pair kernel per SM, at most
 constexpr int64_t SCAN_BLOCK = 2048;           // elements per scan block
 constexpr int64_t SCAN_PART_CAP = 4096;        // partial sums (=> up to 8M elements)
 

@@ -21,14 +21,18 @@
 //    (margins below), so it never changes a result.
 //  * Each warp owns a candidate list and evaluates it itself (no block-wide
 //    barrier in the inner loop).
-//  * FP32 distances carry an error bound E = ERR_REL32 * S, S = R_A + R_B +
-//    |x_B - x_A| (the coordinate scale in A's frame).  A decision d <= eps is
-//    taken in FP32 only when |d32 - eps| > E; otherwise the triangle pair is
-//    recomputed in binary64 with the fixed operation order of geom.cuh, in the
-//    world frame, from the same float32 vertices.  The closest pair (argmin)
-//    is chosen among all triangle pairs with d32 <= min d32 + 2E, recomputed
-//    in binary64, smallest (d^2, a, b).  Decisions and argmin are therefore
-//    the binary64 ones.
+//  * FP32 mode decides nothing from an FP32 distance.  For each triangle pair
+//    the FP32 pass yields closest points pa, pb and a certificate: the
+//    separation of the two triangles along n = pb - pa, less E = ERR_REL32 * S
+//    (S = R_A + R_B + |t|, the coordinate scale of the frame; a tile-local
+//    frame uses its own, smaller S).  Whatever pa and pb are, the certificate
+//    is below the binary64 distance by more than m64 = ERR_REL64_LB *
+//    (S + |X_A| + |X_B|) (the derivation is beside the constants).  "Apart"
+//    is certified (L > eps + m64); "in contact" comes only from binary64
+//    feature values computed exactly as the binary64 distance computes them;
+//    the closest pair is the binary64 minimum over every triangle pair whose
+//    certificate does not exceed a binary64 reference distance.  Decisions,
+//    closest pairs and collision times are therefore the binary64 ones.
 //  * FP64 mode computes every distance in binary64 in the world frame.
 #include <cstdio>
 
@@ -46,12 +50,26 @@ constexpr int ACAP = 512;    // closest-pair candidates per evaluation
 constexpr int WFLUSH = 64;   // default: a warp evaluates its candidate list at this size (<= WCAP - 32)
 constexpr int QWARP = 12;    // binary64 queues up to this size run one triangle pair per warp
 constexpr int GRID_MAX = 16; // sample times whose poses are computed up front
-constexpr int ILCAP = 512;   // triangle pairs of the pair-interval candidate list
-// FP32 error band relative to the pair's coordinate scale S: 2^-17 = 128
-// units of float32 rounding.  The measured maximum of |d32 - d64| / S over
-// the workload and the adversarial cases of the tests is below 2^-22.
-constexpr double ERR_REL32 = 7.62939453125e-06;
-constexpr double ERR_REL64_LB = 9.094947017729282e-13;  // 2^-40: FP64 culling margin
+constexpr int ILCAP = 512;   // triangle pairs of the pair-interval candidate list in shared memory
+                             // (more spill to the CTA's region of the global list, PairArgs::ilg)
+// Margin E of an FP32 certificate, relative to the frame's coordinate scale M
+// (|every coordinate| <= M; M <= S).  Forward error, u = 2^-24, fmaf rounding
+// once, rsqrtf within 2 ulp:
+//  * B's vertex in A's frame, Rr b + t with Rr, t formed in FP32 from the
+//    rounded binary64 poses (entries within 5u, t within 5u |t|) and the fmaf
+//    chain (3 roundings): moved by at most 24u M from its exact image;
+//    A's vertices are its exact float32 body coordinates;
+//  * each dot product n.x (two fmaf, one product): within 3u |n| M, so the
+//    gap min n.y - max n.x within 6u |n| M, its rounding 2u |n| M;
+//  * the scale gap * rsqrtf(n.n): relative 1.5u (n.n) + 4u (rsqrtf) + u, on a
+//    value of at most 2M: 13u M.
+// Total 45u M < 128u M = 2^-17 M, a factor 2.8 to spare.
+constexpr double ERR_REL32 = 7.62939453125e-06;  // 2^-17
+// Binary64 margin relative to S + |X_A| + |X_B|: the oracle's world vertices
+// round relative to the particles' positions, its distance relative to S, and
+// the rotation matrices deviate from orthogonal by a few units of 2^-53;
+// 2^-40 leaves 2^13 such units.  Also the FP64 mode's culling margin.
+constexpr double ERR_REL64_LB = 9.094947017729282e-13;  // 2^-40
 
 constexpr int MODE_NARROW = 0;
 constexpr int MODE_CTIME = 1;
@@ -119,6 +137,10 @@ struct PairArgs {
   uint32_t *err;
   unsigned long long *stats;
   uint32_t wait_polls;  // polls of the first wait on a tile copy
+  // spill of the pair-interval list beyond ILCAP entries: ilg_cap entries per
+  // CTA at ilg + blockIdx.x * ilg_cap (NULL / 0: none)
+  unsigned long long *ilg;
+  int64_t ilg_cap;
   // launch configuration (autotuned per context): hand-out order of the pairs
   // (NULL: index order), warp candidate-list flush size, CTAs per SM
   const int32_t *order;
@@ -154,6 +176,13 @@ struct __align__(128) Smem {
   double RA[9], XA[3], RB[9], XB[3];
   float Rr[9], tr[3];
   double eps, ts, T_, Ed, Elb;
+  double m64;                         // binary64 underestimate margin (FP32 mode: 2^-40 S)
+  double Et;                          // FP32 margin E of the B tile in frames (its local scale)
+  float oo[3], to[3];                 // that tile's local origin (B body frame) and its position in A's frame
+  double Eam;                         // closest-pair collection slack (2 E; widened by a re-run)
+  double cull;                        // threshold the last closest-pair search culled with
+  unsigned long long ref_key;         // closest-pair reference candidate
+  int redo;                           // the closest-pair search must re-run with a wider slack
   int64_t i, j, offA, offB;
   int nA, nB, ngp, gpnext, found, resA, resB, frmA, frmB, bad, abort, nac, ngrid;
   int wcnt[NW];
@@ -303,6 +332,15 @@ struct Cta {
 
   __device__ int ntiles(int n) const { return (n + TT - 1) / TT; }
 
+  // entry k of the pair-interval list: shared memory, then the CTA's spill region
+  __device__ __forceinline__ unsigned long long il_entry(int k) const {
+    return k < ILCAP ? s.il[k] : A.ilg[(int64_t)blockIdx.x * A.ilg_cap + (k - ILCAP)];
+  }
+  __device__ __forceinline__ int il_count() const {
+    const int64_t cap = (int64_t)ILCAP + (A.ilg ? A.ilg_cap : 0);
+    return s.nil < cap ? s.nil : int(cap);
+  }
+
   // --- tile culling (particles with more than one tile) ---------------------
   // Bounding sphere of tile k of A or B in the evaluation frame: the stored
   // body-frame tile sphere of a multi-tile particle, else the body origin with
@@ -413,7 +451,7 @@ struct Cta {
       T ra, rb;
       const T g = tile_gap(q / ntb, q % ntb, ra, rb);
       const double lb = double(g - ra - rb);
-      ub = fmin(ub, double(g + ra + rb) + 2.0 * s.Elb + 4.0 * s.Ed);
+      ub = fmin(ub, double(g + ra + rb) + 2.0 * s.Elb + 2.0 * s.Ed + s.Eam);
       if (lb < best) {
         best = lb;
         bq = q;
@@ -589,16 +627,25 @@ struct Cta {
             s.Ae[3 * q + 2][k] = T(p.z);
           }
     }
+    if constexpr (PREC == 0) {
+      if (doB) {
+        if (tid == 0) tile_frame(tb);
+        __syncthreads();
+      }
+    }
     if (doB) {
       for (int k = tid; k < nb; k += NT)
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const float4 f = A.tris[q * A.n_tris + s.offB + tb * TT + k];
           if constexpr (PREC == 0) {
+            // relative to the tile's local origin: every term of the FP32
+            // transform is at the tile's scale, not the whole mesh's
             const float *R = s.Rr;
-            s.Be[3 * q][k] = T(fmaf(R[0], f.x, fmaf(R[1], f.y, fmaf(R[2], f.z, s.tr[0]))));
-            s.Be[3 * q + 1][k] = T(fmaf(R[3], f.x, fmaf(R[4], f.y, fmaf(R[5], f.z, s.tr[1]))));
-            s.Be[3 * q + 2][k] = T(fmaf(R[6], f.x, fmaf(R[7], f.y, fmaf(R[8], f.z, s.tr[2]))));
+            const float bx = f.x - s.oo[0], by = f.y - s.oo[1], bz = f.z - s.oo[2];
+            s.Be[3 * q][k] = T(fmaf(R[0], bx, fmaf(R[1], by, fmaf(R[2], bz, s.to[0]))));
+            s.Be[3 * q + 1][k] = T(fmaf(R[3], bx, fmaf(R[4], by, fmaf(R[5], bz, s.to[1]))));
+            s.Be[3 * q + 2][k] = T(fmaf(R[6], bx, fmaf(R[7], by, fmaf(R[8], bz, s.to[2]))));
           } else {
             V3<double> p = to_world_exact(s.RB, s.XB, f.x, f.y, f.z);
             s.Be[3 * q][k] = T(p.x);
@@ -632,6 +679,65 @@ struct Cta {
       Y[q] = to_world_exact(s.RB, s.XB, g.x, g.y, g.z);
     }
     return GD::tri_dist2(X, Y, pa, pb);
+  }
+
+  // FP32 frame of B's tile tb (thread 0): local origin o = the tile sphere's
+  // centre for a particle of several tiles, else B's body origin; its
+  // position t_o = R_A^T (R_B o + X_B - X_A) in A's frame (binary64, rounded
+  // once); margin E of the tile = 2^-17 (R_A + r + |t_o|), r bounding the
+  // tile's vertices about o -- the scale of every FP32 coordinate and term of
+  // the tile's transform Rr (b - o) + t_o.
+  __device__ void tile_frame(int tb) {
+    const int64_t slot = s.offB / TT + s.j + tb;
+    float o[3] = {0.f, 0.f, 0.f};
+    double r = A.st[16 * A.n + s.j];
+    if (s.nB > TT && slot < A.cap_tiles) {
+      const float4 f = A.tile_sph[slot];
+      o[0] = f.x;
+      o[1] = f.y;
+      o[2] = f.z;
+      r = f.w;
+    }
+    double t[3];
+    local_origin(o, t);
+    for (int c = 0; c < 3; ++c) {
+      s.oo[c] = o[c];
+      s.to[c] = float(t[c]);
+    }
+    s.Et = ERR_REL32 * (A.st[16 * A.n + s.i] + r + sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]));
+  }
+  // position in A's frame of B's body-frame point o: R_A^T (R_B o + X_B - X_A)
+  __device__ void local_origin(const float o[3], double t[3]) const {
+    double w[3];
+    for (int r = 0; r < 3; ++r)
+      w[r] = s.RB[3 * r] * double(o[0]) + s.RB[3 * r + 1] * double(o[1]) + s.RB[3 * r + 2] * double(o[2]) +
+             (s.XB[r] - s.XA[r]);
+    for (int c = 0; c < 3; ++c) t[c] = s.RA[c] * w[0] + s.RA[3 + c] * w[1] + s.RA[6 + c] * w[2];
+  }
+
+  // Certified lower bound (FP32 mode) of the binary64 distance of the A-frame
+  // FP32 triangles X, Y whose computed closest points are pa, pb: their
+  // separation along pb - pa less E (the rounding of the separation, of the
+  // FP32 relative pose and the binary64 underestimate; E = 2^-17 S of the
+  // frame the coordinates come from); -inf when the points coincide.
+  __device__ __forceinline__ double certificate(const V3<float> X[3], const V3<float> Y[3], V3<float> pa,
+                                                V3<float> pb, double E) const {
+    const V3<float> n{pb.x - pa.x, pb.y - pa.y, pb.z - pa.z};
+    return double(cert_sep(X, 3, Y, 3, n)) - E;
+  }
+
+  // One feature of triangles a (particle i) and b (particle j) in binary64,
+  // world frame, exactly as the binary64 triangle distance computes it.
+  __device__ __noinline__ double feature64(int f, int a, int b, V3<double> &pa, V3<double> &pb) const {
+    V3<double> X[3], Y[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float4 fa = A.tris[q * A.n_tris + s.offA + a];
+      X[q] = to_world_exact(s.RA, s.XA, fa.x, fa.y, fa.z);
+      const float4 fb = A.tris[q * A.n_tris + s.offB + b];
+      Y[q] = to_world_exact(s.RB, s.XB, fb.x, fb.y, fb.z);
+    }
+    return GD::feature_dist2(f, X, Y, pa, pb);
   }
 
   // The same binary64 triangle distance with one warp per triangle pair.
@@ -691,17 +797,26 @@ struct Cta {
       const int j = lane - 3;
       hit = GD::seg_tri_cross(Y[j], Y[j == 2 ? 0 : j + 1], X[0], X[1], X[2], p1);
     }
-    // FP32 feature distances
+    // FP32 feature distances and their certified lower bounds
     float df = OpsF::inf();
+    double Lf = -OpsD::inf();
     {
       V3<float> q1, q2;
       if (fvt) {
-        df = lane < 11 ? GF::closest_pt_tri(Xf[vi], Yf[0], Yf[1], Yf[2], q1)
-                       : GF::closest_pt_tri(Yf[vi], Xf[0], Xf[1], Xf[2], q1);
+        if (lane < 11) {
+          df = GF::closest_pt_tri(Xf[vi], Yf[0], Yf[1], Yf[2], q1);
+          Lf = double(cert_sep(&Xf[vi], 1, Yf, 3, V3<float>{q1.x - Xf[vi].x, q1.y - Xf[vi].y, q1.z - Xf[vi].z}));
+        } else {
+          df = GF::closest_pt_tri(Yf[vi], Xf[0], Xf[1], Xf[2], q1);
+          Lf = double(cert_sep(Xf, 3, &Yf[vi], 1, V3<float>{Yf[vi].x - q1.x, Yf[vi].y - q1.y, Yf[vi].z - q1.z}));
+        }
       } else if (fee) {
-        df = GF::seg_seg(Xf[ei], Xf[ei == 2 ? 0 : ei + 1], Yf[ej], Yf[ej == 2 ? 0 : ej + 1], q1, q2);
+        const V3<float> sa[2] = {Xf[ei], Xf[ei == 2 ? 0 : ei + 1]}, sb[2] = {Yf[ej], Yf[ej == 2 ? 0 : ej + 1]};
+        df = GF::seg_seg(sa[0], sa[1], sb[0], sb[1], q1, q2);
+        Lf = double(cert_sep(sa, 2, sb, 2, V3<float>{q2.x - q1.x, q2.y - q1.y, q2.z - q1.z}));
       }
       df = OpsF::sqrt(df);
+      Lf -= s.Ed;
     }
     const uint32_t hm = __ballot_sync(0xffffffffu, hit) & 0x3fu;
     if (hm) {
@@ -711,10 +826,21 @@ struct Cta {
       pb = pa;
       return 0.0;
     }
-    const float m32 = warp_min(df);
-    const bool need = (fvt || fee) && df <= m32 + 2.0f * float(s.Ed);
-    double d2 = OpsD::inf();
-    if (need) {
+    // the feature closest in FP32 (ties: the definition's order) gives the
+    // binary64 reference; every feature whose certificate does not exceed it
+    // can attain the binary64 minimum and is recomputed in binary64
+    float rm = (fvt || fee) ? df : OpsF::inf();
+    int ro = (fvt || fee) ? ord : 99;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const float om = __shfl_xor_sync(0xffffffffu, rm, o);
+      const int oo = __shfl_xor_sync(0xffffffffu, ro, o);
+      if (om < rm || (om == rm && oo < ro)) {
+        rm = om;
+        ro = oo;
+      }
+    }
+    auto feature_b64 = [&](double &d2) {
       if (fvt) {
         if (lane < 11) {
           d2 = GD::closest_pt_tri(X[vi], Y[0], Y[1], Y[2], p2);
@@ -726,9 +852,16 @@ struct Cta {
       } else {
         d2 = GD::seg_seg(X[ei], X[ei == 2 ? 0 : ei + 1], Y[ej], Y[ej == 2 ? 0 : ej + 1], p1, p2);
       }
-    }
+    };
+    const bool isref = (fvt || fee) && ord == ro;
+    double d2 = OpsD::inf();
+    if (isref) feature_b64(d2);
+    const int rsrc = ro < 3 ? 8 + ro : (ro < 6 ? 11 + (ro - 3) : 16 + (ro - 6));
+    const double dref = OpsD::sqrt(__shfl_sync(0xffffffffu, d2, rsrc));
+    const bool need = (fvt || fee) && !isref && Lf <= dref + s.m64;
+    if (need) feature_b64(d2);
     double bd = d2;
-    int bo = need ? ord : 99;
+    int bo = (need || isref) ? ord : 99;
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       const double od = __shfl_xor_sync(0xffffffffu, bd, o);
@@ -787,6 +920,28 @@ struct Cta {
     }
   }
 
+  // FP32 mode: stage a warp's contact candidates (pairs not certified apart)
+  // with the feature the FP32 pass found closest; contact_verify decides each
+  // in binary64 after the launch and counts the accepted ones per pair
+  __device__ void put_candidates(bool cand, int64_t pk, int ag, int bg, int feat) {
+    const uint32_t m = __ballot_sync(0xffffffffu, cand);
+    if (!m) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(A.st_count, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (cand) {
+      const unsigned long long slot = base + __popc(m & lanemask_lt());
+      if (slot < (unsigned long long)A.st_cap) {
+        A.st_keys[3 * slot] = int32_t(pk);
+        A.st_keys[3 * slot + 1] = ag;
+        A.st_keys[3 * slot + 2] = bg;
+        A.st_geom[7 * slot] = double(feat);
+      } else {
+        set_err(A.err, ERR_CAPACITY);
+      }
+    }
+  }
+
   __device__ void update_best(double d2, unsigned long long key, const V3<double> &pa, const V3<double> &pb) {
     if (d2 < bd2 || (d2 == bd2 && key < bkey)) {
       bd2 = d2;
@@ -831,8 +986,8 @@ struct Cta {
           if (__shfl_sync(0xffffffffu, f, 0)) break;
         }
         V3<double> qa, qb;
-        // decision and contact band entries have d32 >= eps - E
-        const double e2 = exact_warp(ta * TT + a, tb * TT + b, qa, qb, (why & WHY_ARG) || !(s.eps > 6.0 * s.Ed));
+        // a queued pair is not certified apart: it may cross
+        const double e2 = exact_warp(ta * TT + a, tb * TT + b, qa, qb, true);
         ++n64;
         const double de = OpsD::sqrt(e2);
         if (DECIDE && (why & WHY_DEC) && de <= s.eps && lane == 0) s.found = 1;
@@ -891,7 +1046,7 @@ struct Cta {
   __device__ void warp_eval(const uint32_t *list, int cnt, int ta, int tb, int64_t pk, bool pass1) {
     const T eps = T(s.eps);
     const T Ed = T(s.Ed);
-    unsigned long long n32 = 0;
+    unsigned long long n32 = 0, nv64 = 0;
     for (int e = 0; e < cnt; e += 32) {
       const int k = e + lane;
       const bool have = k < cnt;
@@ -899,11 +1054,21 @@ struct Cta {
       const int a = int(ent >> 16), b = int(ent & 0xffffu);
       T d2 = O::inf();
       V pa{}, pb{};
+      int feat = 0;
+      double L = -OpsD::inf();  // FP32: certified lower bound of the binary64 distance
       if (have) {
         V X[3], Y[3];
         load_vtx(true, a, X);
         load_vtx(false, b, Y);
-        if (DECIDE && !ARGMIN && !CONTACTS) {
+        if constexpr (PREC == 0) {
+          // a decision alone needs no FP32 crossing test: crossing triangles
+          // have no separating direction, so their certificate never clears them
+          if (DECIDE && !ARGMIN && !CONTACTS)
+            d2 = GT::tri_dist2_features(X, Y, pa, pb, feat);
+          else
+            d2 = GT::tri_dist2(X, Y, pa, pb, feat);
+          L = certificate(X, Y, pa, pb, s.Et);
+        } else if (DECIDE && !ARGMIN && !CONTACTS) {
           // features first; the crossing test only when they do not settle it
           d2 = GT::tri_dist2_features(X, Y, pa, pb);
           if (!(O::sqrt(d2) < eps - Ed)) {
@@ -923,9 +1088,10 @@ struct Cta {
       const T d = O::sqrt(d2);
       if (s.ilcol) {
         // remember the triangle pair for the rest of the pair interval when
-        // its distance at ts is within the list threshold (eps + delta plus
-        // the FP32 band): no other pair can come within eps in the interval
-        const bool col = have && double(d) <= s.ilthr;
+        // it can come within eps in the interval: its distance at ts is at
+        // most eps + delta (FP32: its certified lower bound; FP64: its value),
+        // no other pair can
+        const bool col = have && (PREC == 0 ? L : double(d)) <= s.ilthr;
         const uint32_t m = __ballot_sync(0xffffffffu, col);
         if (m) {
           int base = 0;
@@ -934,16 +1100,20 @@ struct Cta {
           if (col) {
             const int pos = base + __popc(m & lanemask_lt());
             const int ag = ta * TT + a, bg = tb * TT + b;
-            // lower bound of the binary64 distance (FP32: d32 - 2E, rounded
-            // down), truncated to 16 bits of its float pattern (rounds down)
+            // lower bound of the binary64 distance (FP32: the certificate,
+            // rounded down), truncated to 16 bits of its float pattern
             float dlb;
             if constexpr (PREC == 0)
-              dlb = __fsub_rd(float(d), 2.0f * float(s.Ed));
+              dlb = __double2float_rd(L);
             else
               dlb = __double2float_rd(double(d));
             const unsigned long long dq = __float_as_uint(dlb > 0.0f ? dlb : 0.0f) >> 16;
+            const unsigned long long ent =
+                (dq << 48) | (static_cast<unsigned long long>(ag) << 24) | static_cast<uint32_t>(bg);
             if (pos < ILCAP)
-              s.il[pos] = (dq << 48) | (static_cast<unsigned long long>(ag) << 24) | static_cast<uint32_t>(bg);
+              s.il[pos] = ent;
+            else if (A.ilg && pos - ILCAP < A.ilg_cap)
+              A.ilg[(int64_t)blockIdx.x * A.ilg_cap + (pos - ILCAP)] = ent;
             else
               s.ilover = 1;
           }
@@ -952,18 +1122,43 @@ struct Cta {
       const unsigned long long key = key_of(a, b, ta, tb);
       if constexpr (PREC == 0) {
         uint32_t why = 0;
-        bool yes = false, con = false;
-        if (DECIDE && have) {
-          yes = d < eps - Ed;
-          if (!yes && d <= eps + Ed) why |= WHY_DEC;
+        bool yes = false;
+        double gd = 0.0;
+        const bool apart = !have || L > s.eps + s.m64;
+        if (DECIDE && ARGMIN) {
+          // the decision is the binary64 closest pair's (eval); a pair not
+          // certified apart only calls for that search
+          if (__any_sync(0xffffffffu, !apart) && lane == 0) s.found = 1;
+        } else if (DECIDE) {
+          // apart: certified; in contact: the binary64 value of the feature
+          // the FP32 pass found closest is within eps (the pair's binary64
+          // distance can only be smaller) -- checked for the lane with the
+          // smallest FP32 distance; otherwise binary64 in full
+          const bool cand = have && !apart && d < eps;
+          const T dm = warp_min(cand ? d : O::inf());
+          const uint32_t pm = __ballot_sync(0xffffffffu, cand && d == dm);
+          const bool pick = pm && lane == __ffs(pm) - 1;
+          bool ok = false;
+          if (pm) {
+            V3<double> qa{0.0, 0.0, 0.0}, qb{0.0, 0.0, 0.0};
+            double e2 = OpsD::inf();
+            if (pick) {
+              e2 = feature64(feat, ta * TT + a, tb * TT + b, qa, qb);
+              ++nv64;
+            }
+            gd = OpsD::sqrt(e2);
+            ok = pick && gd <= s.eps;
+          }
+          yes = ok;
+          if (!apart && !__any_sync(0xffffffffu, ok)) why |= WHY_DEC;
         }
-        if (CONTACTS && have) {
-          con = d < eps - Ed;
-          if (!con && d <= eps + Ed) why |= WHY_CON;
-        }
+        if (CONTACTS) put_candidates(have && !apart, pk, ta * TT + a, tb * TT + b, feat);
         if (ARGMIN) {
           mw = fmin(mw, warp_min(have ? d : O::inf()));
-          const bool am = have && d <= mw + T(2) * Ed;
+          // candidates for the closest pair: certificate within the current
+          // FP32 minimum plus the slack (checked against the binary64
+          // reference distance in argmin_list)
+          const bool am = have && L <= double(mw) + s.Eam;
           const uint32_t mm = __ballot_sync(0xffffffffu, am);
           if (mm) {
             int base = 0;
@@ -973,7 +1168,7 @@ struct Cta {
             if (base + __popc(mm) <= ACAP) {
               if (am) {
                 s.ac_key[pos] = key;
-                s.ac_d[pos] = float(d);
+                s.ac_d[pos] = __double2float_rd(L);
               }
             } else {
               // list full: mark the reserved slots empty, recompute through the queue
@@ -983,14 +1178,6 @@ struct Cta {
           }
         }
         if (DECIDE && __any_sync(0xffffffffu, yes) && lane == 0) s.found = 1;
-        if (CONTACTS) {
-          double ga3[3], gb3[3];
-          if (con) {
-            world_of_A_frame(pa, ga3);
-            world_of_A_frame(pb, gb3);
-          }
-          put_contacts(con, pk, ta * TT + a, tb * TT + b, double(d), ga3, gb3);
-        }
         // queue the binary64 recomputations
         const uint32_t m = __ballot_sync(0xffffffffu, why != 0);
         if (m) {
@@ -1016,13 +1203,19 @@ struct Cta {
       }
       if (ARGMIN && pass1 && lane == 0) {
         // tighten the shared bound with this warp's minimum
-        const double nb = double(mw) + 3.0 * s.Ed + s.Elb;
+        const double nb = double(mw) + s.Eam + s.Ed + s.Elb;
         atomicMin(&s.bound, dbits(nb));
       }
     }
 #pragma unroll
-    for (int o = 16; o; o >>= 1) n32 += __shfl_xor_sync(0xffffffffu, n32, o);
-    if (lane == 0) stat(ST_FP32, n32);
+    for (int o = 16; o; o >>= 1) {
+      n32 += __shfl_xor_sync(0xffffffffu, n32, o);
+      nv64 += __shfl_xor_sync(0xffffffffu, nv64, o);
+    }
+    if (lane == 0) {
+      stat(ST_FP32, n32);
+      stat(ST_FP64, nv64);
+    }
   }
 
   // block-wide sort of the group-pair list by lower bound (bitonic)
@@ -1065,7 +1258,8 @@ struct Cta {
   __device__ void scan_tiles(int ta, int tb, bool pass1, T th0, int64_t pk, bool seen0 = true) {
     const int na = min(TT, s.nA - ta * TT), nb = min(TT, s.nB - tb * TT);
     const int nga = (na + G - 1) / G, ngb = (nb + G - 1) / G;
-    const T Elb = T(s.Elb);
+    // culling margin: FP32 spheres of the tiles' FP32 vertices, the tile's scale
+    const T Elb = T(PREC == 0 ? s.Et : s.Elb);
     if (tid == 0) {
       s.ngp = 0;
       s.gpnext = 0;
@@ -1149,7 +1343,7 @@ struct Cta {
             // every centroid pair bounds the minimum distance from above
             const T rowmin = warp_min(valid ? d2c : O::inf());
             if (lane == 0) {
-              const double ub = double(O::sqrt(rowmin)) + 2.0 * s.Elb + 4.0 * s.Ed;
+              const double ub = double(O::sqrt(rowmin)) + 2.0 * s.Elb + 2.0 * s.Ed + s.Eam;
               atomicMin(&s.bound, dbits(ub));
             }
             __syncwarp();
@@ -1238,8 +1432,8 @@ struct Cta {
     }
     __syncthreads();
     if (w == 0) {
-      // relative pose of B in A's frame in FP32 (its error is inside the
-      // band): lane 3r+c computes Rr[r][c], lane 9+r computes tr[r]
+      // relative pose of B in A's frame in FP32 (its error is part of the
+      // margin E): lane 3r+c computes Rr[r][c], lane 9+r computes tr[r]
       const int r = lane < 9 ? lane / 3 : (lane < 12 ? lane - 9 : 0), c = lane < 9 ? lane % 3 : 0;
       const float ra0 = float(s.RA[r]), ra1 = float(s.RA[3 + r]), ra2 = float(s.RA[6 + r]);
       float v;
@@ -1260,6 +1454,12 @@ struct Cta {
           const double S = ri + rj + sqrtf(tr[0] * tr[0] + tr[1] * tr[1] + tr[2] * tr[2]);
           s.Ed = S * ERR_REL32;
           s.Elb = s.Ed;
+          s.Et = s.Ed;
+          // the oracle's world vertices round relative to |X|, not S
+          s.m64 = (S + sqrt(s.XA[0] * s.XA[0] + s.XA[1] * s.XA[1] + s.XA[2] * s.XA[2]) +
+                   sqrt(s.XB[0] * s.XB[0] + s.XB[1] * s.XB[1] + s.XB[2] * s.XB[2])) *
+                  ERR_REL64_LB;
+          s.Eam = 2.0 * s.Ed;
           // FP32 A-frame data stay valid; B moves
           s.frmB = -1;
         } else {
@@ -1267,6 +1467,9 @@ struct Cta {
                            sqrt(s.XB[0] * s.XB[0] + s.XB[1] * s.XB[1] + s.XB[2] * s.XB[2]);
           s.Ed = 0.0;
           s.Elb = S * ERR_REL64_LB;
+          s.Et = s.Elb;
+          s.m64 = 0.0;
+          s.Eam = 0.0;
           s.frmA = -1;
           s.frmB = -1;
         }
@@ -1305,17 +1508,119 @@ struct Cta {
       if (extra > 0.0) {
         s.nil = 0;
         s.ilover = 0;
-        s.ilthr = double(th0) + s.Ed;
+        s.ilthr = PREC == 0 ? s.eps + extra + s.m64 : double(th0);
       }
       s.ilcol = extra > 0.0 ? 1 : 0;
     }
     __syncthreads();
+    const bool multi = nta > 1 || ntb > 1;
+    const int nq = nta * ntb;
+    if (!pass0<DECIDE, ARGMIN, CONTACTS>(th0, nta, ntb, pk)) return false;
+    if (tid == 0) s.ilcol = 0;
+    if (DECIDE && ARGMIN) {
+      const bool f = *(volatile int *)&s.found != 0;
+      __syncthreads();
+      if (!f) return false;
+    }
+    if (ARGMIN) {
+      for (int attempt = 0;; ++attempt) {
+        // FP32 (FP64) minimum over the evaluated pairs
+        const double mh = block_min(double(mw));
+        const double slack = s.Eam + s.Ed + s.Elb;
+        const bool complete = mh + slack <= double(th0);
+        if (!complete && nta > 0 && ntb > 0) {
+          if (tid == 0) s.bound = dbits(mh + slack);  // inf if nothing seen
+          __syncthreads();
+          // the nearest tile pair first (it tightens the bound), then the
+          // others in chunks tested in parallel against the bound at the
+          // chunk's start; a selected tile pair is tested again against the
+          // bound as it is when its turn comes
+          const int q0 = multi ? bound_by_tiles(nta, ntb) : 0;
+          {
+            const int ta = q0 / ntb, tb = q0 - (q0 / ntb) * ntb;
+            // whether pass 0 scanned this tile pair (the same test, same pose)
+            const bool seen0 = !multi || __syncthreads_or(tid == 0 && tile_near(ta, tb, double(th0)));
+            if (!load_tiles(ta, tb)) return false;
+            frames(ta, tb);
+            if (tid == 0) stat(ST_TILES, 1);
+            scan_tiles<false, true, false>(ta, tb, true, th0, pk, seen0);
+          }
+          for (int c0 = 0; multi && c0 < nq; c0 += NT) {
+            const int q = c0 + tid;
+            const bool near = q < nq && q != q0 &&
+                              tile_near(q / ntb, q - (q / ntb) * ntb, bitsd(*(volatile unsigned long long *)&s.bound));
+            const uint32_t m = __ballot_sync(0xffffffffu, near);
+            if (lane == 0) s.tmask[w] = m;
+            __syncthreads();
+            for (int wq = 0; wq < NW; ++wq) {
+              uint32_t mm = s.tmask[wq];
+              while (mm) {
+                const int qq = c0 + wq * 32 + __ffs(mm) - 1;
+                mm &= mm - 1;
+                const int ta = qq / ntb, tb = qq - ta * ntb;
+                if (!__syncthreads_or(tid == 0 && tile_near(ta, tb, bitsd(*(volatile unsigned long long *)&s.bound))))
+                  continue;
+                const bool seen0 = __syncthreads_or(tid == 0 && tile_near(ta, tb, double(th0)));
+                if (!load_tiles(ta, tb)) return false;
+                frames(ta, tb);
+                if (tid == 0) stat(ST_TILES, 1);
+                scan_tiles<false, true, false>(ta, tb, true, th0, pk, seen0);
+              }
+            }
+            __syncthreads();
+          }
+        }
+        const double mh2 = block_min(double(mw));
+        if (tid == 0) s.cull = complete ? double(th0) : bitsd(s.bound);
+        __syncthreads();
+        if constexpr (PREC == 0) {
+          argmin_list(mh2);
+          if (s.redo && attempt < 2) {
+            // the binary64 reference lies beyond the slack the candidates or
+            // the culling used: search again, argmin alone, with a wider one
+            __syncthreads();
+            if (tid == 0) {
+              s.Eam = attempt == 0 ? s.Eam * 1024.0 : OpsD::inf();
+              s.nac = 0;
+              s.redo = 0;
+            }
+            mw = O::inf();
+            bd2 = OpsD::inf();
+            bkey = ~0ull;
+            wbd2 = OpsD::inf();
+            wbkey = ~0ull;
+            qn = 0;
+            __syncthreads();
+            if (!pass0<false, true, false>(th0, nta, ntb, pk)) return false;
+            continue;
+          }
+        }
+        reduce_best();
+        if (tid == 0) {
+          s.mhat = mh2;
+          // FP32 mode: a decision with the closest pair is that pair's
+          // binary64 distance within eps (the definition of f(t) <= eps)
+          if (PREC == 0 && DECIDE) s.found = s.best_key != ~0ull && OpsD::sqrt(s.best_d2) <= s.eps;
+        }
+        __syncthreads();
+        break;
+      }
+    }
+    const bool f = DECIDE ? (*(volatile int *)&s.found != 0) : false;
+    __syncthreads();
+    return f;
+  }
+
+  // The first pass of an evaluation: every tile pair whose tile bound is
+  // within th0 (in chunks of NT tile pairs: every thread tests one, the warps
+  // publish ballots, the CTA scans the near ones in order); a decision alone
+  // stops at the first triangle pair within eps.  False if a tile copy timed
+  // out.
+  template <bool DECIDE, bool ARGMIN, bool CONTACTS>
+  __device__ bool pass0(T th0, int nta, int ntb, int64_t pk) {
     bool stop = false;
     const bool multi = nta > 1 || ntb > 1;
     const int nq = nta * ntb;
-    // tile pairs q = ta * ntb + tb in chunks of NT: every thread tests one
-    // pair's spheres, the warps publish ballots, then the CTA scans the near
-    // ones in order
     for (int c0 = 0; c0 < nq && !stop; c0 += NT) {
       const int q = c0 + tid;
       const bool near = q < nq && (!multi || tile_near(q / ntb, q - (q / ntb) * ntb, double(th0)));
@@ -1337,92 +1642,91 @@ struct Cta {
       }
       __syncthreads();  // the next chunk rewrites s.tmask
     }
-    if (tid == 0) s.ilcol = 0;
-    if (DECIDE && ARGMIN) {
-      const bool f = *(volatile int *)&s.found != 0;
-      __syncthreads();
-      if (!f) return false;
-    }
-    if (ARGMIN) {
-      // FP32 (FP64) minimum over the evaluated pairs
-      const double mh = block_min(double(mw));
-      const bool complete = mh + 3.0 * s.Ed + s.Elb <= double(th0);
-      if (!complete && nta > 0 && ntb > 0) {
-        if (tid == 0) s.bound = dbits(mh + 3.0 * s.Ed + s.Elb);  // inf if nothing seen
-        __syncthreads();
-        // the nearest tile pair first (it tightens the bound), then the
-        // others in chunks tested in parallel against the bound at the chunk's
-        // start; a selected tile pair is tested again against the bound as it
-        // is when its turn comes
-        const int q0 = multi ? bound_by_tiles(nta, ntb) : 0;
-        {
-          const int ta = q0 / ntb, tb = q0 - (q0 / ntb) * ntb;
-          // whether pass 0 scanned this tile pair (the same test, same pose)
-          const bool seen0 = !multi || __syncthreads_or(tid == 0 && tile_near(ta, tb, double(th0)));
-          if (!load_tiles(ta, tb)) return false;
-          frames(ta, tb);
-          if (tid == 0) stat(ST_TILES, 1);
-          scan_tiles<false, true, false>(ta, tb, true, th0, pk, seen0);
-        }
-        for (int c0 = 0; multi && c0 < nq; c0 += NT) {
-          const int q = c0 + tid;
-          const bool near = q < nq && q != q0 &&
-                            tile_near(q / ntb, q - (q / ntb) * ntb, bitsd(*(volatile unsigned long long *)&s.bound));
-          const uint32_t m = __ballot_sync(0xffffffffu, near);
-          if (lane == 0) s.tmask[w] = m;
-          __syncthreads();
-          for (int wq = 0; wq < NW; ++wq) {
-            uint32_t mm = s.tmask[wq];
-            while (mm) {
-              const int qq = c0 + wq * 32 + __ffs(mm) - 1;
-              mm &= mm - 1;
-              const int ta = qq / ntb, tb = qq - ta * ntb;
-              if (!__syncthreads_or(tid == 0 && tile_near(ta, tb, bitsd(*(volatile unsigned long long *)&s.bound))))
-                continue;
-              const bool seen0 = __syncthreads_or(tid == 0 && tile_near(ta, tb, double(th0)));
-              if (!load_tiles(ta, tb)) return false;
-              frames(ta, tb);
-              if (tid == 0) stat(ST_TILES, 1);
-              scan_tiles<false, true, false>(ta, tb, true, th0, pk, seen0);
-            }
-          }
-          __syncthreads();
-        }
-      }
-      const double mh2 = block_min(double(mw));
-      if (PREC == 0) argmin_list(mh2);
-      reduce_best();
-      if (tid == 0) s.mhat = mh2;
-      __syncthreads();
-    }
-    const bool f = DECIDE ? (*(volatile int *)&s.found != 0) : false;
-    __syncthreads();
-    return f;
+    return true;
   }
 
-  // Closest pair among the collected candidates: those with d32 <= min + 2E
-  // (compacted by warp 0), sorted by (a, b), recomputed in binary64 one
-  // candidate per warp per round; once a round finds a zero distance no later
-  // (larger) key can win.
+  // Closest pair (FP32 mode) among the collected candidates, each with its
+  // certified lower bound L of the binary64 distance.  The candidate with the
+  // smallest L is the reference: its binary64 distance dref bounds the
+  // binary64 minimum from above, so only candidates with L <= dref + m64 can
+  // attain it; they are sorted by (a, b) and recomputed in binary64, one per
+  // warp per round, stopping after a round that found a zero (no later key
+  // can win then).  A reference beyond the slack the candidates were
+  // collected with, or beyond the culling threshold, sets s.redo: a pair that
+  // was not collected or not evaluated could then attain the minimum.
   __device__ void argmin_list(double mh) {
     const int n0 = min(s.nac, ACAP);
-    const float thr = float(mh + 2.0 * s.Ed);
+    if (w == 0) {
+      float bl = OpsF::inf();
+      unsigned long long bk = ~0ull;
+      for (int q = lane; q < n0; q += 32) {
+        const unsigned long long key = s.ac_key[q];
+        const float L = s.ac_d[q];
+        if (key != ~0ull && (L < bl || (L == bl && key < bk))) {
+          bl = L;
+          bk = key;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        const float ol = __shfl_xor_sync(0xffffffffu, bl, o);
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        if (ol < bl || (ol == bl && ok < bk)) {
+          bl = ol;
+          bk = ok;
+        }
+      }
+      if (lane == 0) {
+        s.ref_key = bk;
+        s.red_d[0] = double(bl);
+      }
+    }
+    __syncthreads();
+    const unsigned long long rk = s.ref_key;
+    unsigned long long n64 = 0;
+    double dref = OpsD::inf();
+    if (rk != ~0ull) {
+      if (w == 0) {
+        V3<double> qa, qb;
+        const double e2 = exact_warp(int(rk >> 32), int(rk & 0xffffffffu), qa, qb, !(s.red_d[0] > s.m64));
+        update_best(e2, rk, qa, qb);
+        ++n64;
+        if (lane == 0) s.red_d[1] = OpsD::sqrt(e2);
+      }
+      __syncthreads();
+      dref = s.red_d[1];
+      if (tid == 0) s.redo = (dref + s.m64 > mh + s.Eam) || (dref + s.m64 > s.cull);
+    } else if (tid == 0) {
+      s.redo = 0;
+    }
+    __syncthreads();
+    if (s.redo) return;
+    // candidates that can attain the binary64 minimum (a zero reference: only
+    // smaller keys), compacted by warp 0; their smallest certificate decides
+    // whether the crossing tests can be skipped
     if (w == 0) {
       int m = 0;
+      float lmin = OpsF::inf();
       for (int q0 = 0; q0 < n0; q0 += 32) {
         const int q = q0 + lane;
         const unsigned long long key = q < n0 ? s.ac_key[q] : ~0ull;
-        const bool keep = q < n0 && key != ~0ull && s.ac_d[q] <= thr;
+        const bool keep = key != ~0ull && key != rk && double(s.ac_d[q]) <= dref + s.m64 && (dref > 0.0 || key < rk);
         const uint32_t mk = __ballot_sync(0xffffffffu, keep);
+        if (keep) lmin = fminf(lmin, s.ac_d[q]);
         __syncwarp();
         if (keep) s.ac_key[m + __popc(mk & lanemask_lt())] = key;
         m += __popc(mk);
         __syncwarp();
       }
-      if (lane == 0) s.nac = m;
+      lmin = warp_min(lmin);
+      if (lane == 0) {
+        s.nac = m;
+        s.red_d[2] = double(lmin);
+      }
     }
     __syncthreads();
     const int n = s.nac;
+    const bool cross = !(s.red_d[2] > s.m64);
     int n2 = 1;
     while (n2 < n) n2 <<= 1;
     if (n2 <= 32) {
@@ -1457,20 +1761,13 @@ struct Cta {
           __syncthreads();
         }
     }
-    unsigned long long n64 = 0;
-    // a pair whose FP32 minimum exceeds 4E has no intersecting triangles:
-    // no crossing tests, and no zero distance that would end the rounds early
-    const bool may_touch = !(mh > 4.0 * s.Ed);
-    // round 0: the smallest key alone when it may be a zero distance (that
-    // settles most intersecting pairs); then NW candidates per round
-    const int first = may_touch ? 1 : 0;
-    for (int r0 = 0; r0 < n; r0 = (r0 == 0 && first ? 1 : r0 + NW)) {
-      const int q = (r0 == 0 && first) ? (w == 0 ? 0 : n) : r0 + w;
+    for (int r0 = 0; r0 < n; r0 += NW) {
+      const int q = r0 + w;
       const unsigned long long key = q < n ? s.ac_key[q] : ~0ull;
       double e2 = OpsD::inf();
       if (key != ~0ull) {
         V3<double> qa, qb;
-        e2 = exact_warp(int(key >> 32), int(key & 0xffffffffu), qa, qb, may_touch);
+        e2 = exact_warp(int(key >> 32), int(key & 0xffffffffu), qa, qb, cross);
         update_best(e2, key, qa, qb);
         ++n64;
       }
@@ -1487,18 +1784,39 @@ struct Cta {
   // change over the interval), so the list decides exactly like the full scan.
   __device__ bool decide_list(double t, int kidx) {
     set_time(t, kidx);
-    const int n = s.nil;
+    const int n = il_count();
     const T eps = T(s.eps), Ed = T(s.Ed);
     bool yes_any = false;
     unsigned long long n32 = 0, n64 = 0;
     for (int r0 = w * 32; r0 < n; r0 += NT) {
       const int k = r0 + lane;
       const bool have = k < n;
-      const unsigned long long ent = have ? s.il[k] : 0ull;
+      const unsigned long long ent = have ? il_entry(k) : 0ull;
       const int ag = int((ent >> 24) & 0xffffffu), bg = int(ent & 0xffffffu);
       T d = O::inf();
+      double L = -OpsD::inf();
+      int feat = 0;
       if (have) {
         V X[3], Y[3];
+        // FP32: B's triangle in its tile's local frame (a particle of several
+        // tiles), with that tile's margin; else B's body frame and the pair's
+        float o[3] = {0.f, 0.f, 0.f}, to[3] = {s.tr[0], s.tr[1], s.tr[2]};
+        double Eloc = s.Ed;
+        if constexpr (PREC == 0) {
+          const int64_t slot = s.offB / TT + s.j + bg / TT;
+          if (s.nB > TT && slot < A.cap_tiles) {
+            const float4 f = A.tile_sph[slot];
+            o[0] = f.x;
+            o[1] = f.y;
+            o[2] = f.z;
+            double t[3];
+            local_origin(o, t);
+            to[0] = float(t[0]);
+            to[1] = float(t[1]);
+            to[2] = float(t[2]);
+            Eloc = ERR_REL32 * (A.st[16 * A.n + s.i] + double(f.w) + sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]));
+          }
+        }
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           const float4 f = A.tris[q * A.n_tris + s.offA + ag];
@@ -1506,9 +1824,10 @@ struct Cta {
           if constexpr (PREC == 0) {
             X[q] = V{f.x, f.y, f.z};
             const float *R = s.Rr;
-            Y[q] = V{fmaf(R[0], g.x, fmaf(R[1], g.y, fmaf(R[2], g.z, s.tr[0]))),
-                     fmaf(R[3], g.x, fmaf(R[4], g.y, fmaf(R[5], g.z, s.tr[1]))),
-                     fmaf(R[6], g.x, fmaf(R[7], g.y, fmaf(R[8], g.z, s.tr[2])))};
+            const float bx = g.x - o[0], by = g.y - o[1], bz = g.z - o[2];
+            Y[q] = V{fmaf(R[0], bx, fmaf(R[1], by, fmaf(R[2], bz, to[0]))),
+                     fmaf(R[3], bx, fmaf(R[4], by, fmaf(R[5], bz, to[1]))),
+                     fmaf(R[6], bx, fmaf(R[7], by, fmaf(R[8], bz, to[2])))};
           } else {
             const V3<double> x = to_world_exact(s.RA, s.XA, f.x, f.y, f.z);
             const V3<double> y = to_world_exact(s.RB, s.XB, g.x, g.y, g.z);
@@ -1517,33 +1836,61 @@ struct Cta {
           }
         }
         V pa, pb;
-        T d2 = GT::tri_dist2_features(X, Y, pa, pb);
-        if (!(O::sqrt(d2) < eps - Ed)) {
-          V x;
-          bool hit = false;
-          for (int q = 0; q < 3 && !hit; ++q)
-            hit = GT::seg_tri_cross(X[q], X[q == 2 ? 0 : q + 1], Y[0], Y[1], Y[2], x);
-          for (int q = 0; q < 3 && !hit; ++q)
-            hit = GT::seg_tri_cross(Y[q], Y[q == 2 ? 0 : q + 1], X[0], X[1], X[2], x);
-          if (hit) d2 = T(0);
+        T d2;
+        if constexpr (PREC == 0) {
+          // features only: crossing triangles have no separating direction,
+          // so their certificate never clears them
+          d2 = GT::tri_dist2_features(X, Y, pa, pb, feat);
+          L = certificate(X, Y, pa, pb, Eloc);
+        } else {
+          d2 = GT::tri_dist2_features(X, Y, pa, pb);
+          if (!(O::sqrt(d2) <= eps)) {
+            V x;
+            bool hit = false;
+            for (int q = 0; q < 3 && !hit; ++q)
+              hit = GT::seg_tri_cross(X[q], X[q == 2 ? 0 : q + 1], Y[0], Y[1], Y[2], x);
+            for (int q = 0; q < 3 && !hit; ++q)
+              hit = GT::seg_tri_cross(Y[q], Y[q == 2 ? 0 : q + 1], X[0], X[1], X[2], x);
+            if (hit) d2 = T(0);
+          }
         }
         d = O::sqrt(d2);
         ++n32;
       }
-      bool yes = have && (PREC == 0 ? d < eps - Ed : d <= eps);
+      bool yes = have && PREC == 1 && d <= eps;
+      bool apart = !have;
+      if constexpr (PREC == 0) {
+        // certified apart, or in contact by the binary64 value of the
+        // closest FP32 feature; the rest in binary64 in full below
+        apart = !have || L > s.eps + s.m64;
+        // the lane with the smallest FP32 distance among those within eps
+        const bool cand = have && !apart && d < eps;
+        const T dm = warp_min(cand ? d : O::inf());
+        const uint32_t pm = __ballot_sync(0xffffffffu, cand && d == dm);
+        if (pm) {
+          const bool pick = lane == __ffs(pm) - 1;
+          V3<double> qa, qb;
+          double e2 = OpsD::inf();
+          if (pick) {
+            e2 = feature64(feat, ag, bg, qa, qb);
+            ++n64;
+          }
+          yes = pick && OpsD::sqrt(e2) <= s.eps;
+        }
+      }
       if (__any_sync(0xffffffffu, yes)) {
         yes_any = true;
         break;
       }
       if constexpr (PREC == 0) {
-        // the FP32 band: binary64, one triangle pair per warp
-        uint32_t bm = __ballot_sync(0xffffffffu, have && d <= eps + Ed);
+        // not settled: binary64, one triangle pair per warp
+        uint32_t bm = __ballot_sync(0xffffffffu, have && !apart);
         while (bm && !yes_any) {
           const int src = __ffs(bm) - 1;
           bm &= bm - 1;
           V3<double> qa, qb;
           const double e2 = exact_warp(__shfl_sync(0xffffffffu, ag, src), __shfl_sync(0xffffffffu, bg, src), qa, qb,
-                                       !(s.eps > 6.0 * s.Ed));
+                                       true);
           ++n64;
           if (OpsD::sqrt(e2) <= s.eps) yes_any = true;
         }
@@ -1705,9 +2052,9 @@ struct Cta {
     const float dx = c[0][0] - c[1][0], dy = c[0][1] - c[1][1], dz = c[0][2] - c[1][2];
     return double(sqrtf(dx * dx + dy * dy + dz * dz)) - double(r[0]) - double(r[1]) - double(mg);
   }
-  // The FP32 distance of triangles a, b at ts in A's frame (B moved by the
-  // FP32 relative pose, as in the tile scan) less 2E, rounded down: the same
-  // lower bound the pair-interval list keeps.
+  // Certified lower bound of the binary64 distance of triangles a, b at ts
+  // (A's frame, B moved by the FP32 relative pose, as in the tile scan): the
+  // same lower bound the pair-interval list keeps.
   __device__ double tri_dist32_lb(int a, int b) const {
     using GF = Geo<OpsF>;
     V3<float> X[3], Y[3];
@@ -1721,8 +2068,8 @@ struct Cta {
                        fmaf(R[6], g.x, fmaf(R[7], g.y, fmaf(R[8], g.z, s.tr[2])))};
     }
     V3<float> pa, pb;
-    const float d = OpsF::sqrt(GF::tri_dist2(X, Y, pa, pb));
-    return double(__fsub_rd(d, 2.0f * float(s.Ed)));
+    GF::tri_dist2_features(X, Y, pa, pb);
+    return certificate(X, Y, pa, pb, s.Ed);
   }
   // The narrowing loop after a false decision at ts.  The triangle pairs are
   // those of the pair-interval list collected at ts with the narrowing's
@@ -1748,7 +2095,8 @@ struct Cta {
     // the paper's unfolding constrained by a global contact time.
     const bool useL0 = s.ilover == 0;
     if (useL0) {
-      const int n = s.nil;
+      // the shared-memory part is sorted; a spilled part is visited unsorted
+      const int n = s.nil < ILCAP ? s.nil : ILCAP;
       int n2 = 1;
       while (n2 < n) n2 <<= 1;
       for (int q = n + tid; q < n2; q += NT) s.il[q] = ~0ull;
@@ -1785,7 +2133,7 @@ struct Cta {
       }
       __syncthreads();
       const bool useL = useL0;
-      const int64_t cnt = useL ? (int64_t)s.nil : (int64_t)s.nA * s.nB;
+      const int64_t cnt = useL ? (int64_t)il_count() : (int64_t)s.nA * s.nB;
       if (tid == 0) s.bound = okey(O::inf());  // earliest candidate time so far
       __syncthreads();
       double best = O::inf();
@@ -1793,13 +2141,17 @@ struct Cta {
       for (int64_t q = tid; q < cnt; q += NT) {
         int a, b;
         if (useL) {
-          const unsigned long long ent = s.il[q];
+          const unsigned long long ent = il_entry(int(q));
           a = int((ent >> 24) & 0xffffffu);
           b = int(ent & 0xffffffu);
           const double dlb = double(__uint_as_float(uint32_t(ent >> 48) << 16));
           const double tlb = dlb > s.eps ? ts + (dlb - s.eps) / rate * (1.0 - 1e-9) : -O::inf();
-          // sorted by distance: this thread's later entries cannot be earlier
-          if (tlb > okey_value(*(volatile unsigned long long *)&s.bound)) break;
+          if (tlb > okey_value(*(volatile unsigned long long *)&s.bound)) {
+            // sorted by distance in shared memory: this thread's later shared
+            // entries cannot be earlier; go on with its spilled ones
+            if (q < ILCAP) q = tid + (int64_t)((ILCAP - tid + NT - 1) / NT) * NT - NT;
+            continue;
+          }
         } else {
           a = int(q / s.nB);
           b = int(q - (int64_t)a * s.nB);
@@ -2191,7 +2543,7 @@ cudaError_t launch_pairs(const PairArgs &a, int num_sms, cudaStream_t s) {
     per_sm = q < 1 ? 1 : q;
   }
   const int want = a.ctas_per_sm > 0 && a.ctas_per_sm < per_sm ? a.ctas_per_sm : per_sm;
-  int64_t grid = (int64_t)num_sms * want;
+  int64_t grid = (int64_t)num_sms * (want < MAX_PAIR_CTAS_PER_SM ? want : MAX_PAIR_CTAS_PER_SM);
   if (a.max_pairs < grid) grid = a.max_pairs > 0 ? a.max_pairs : 1;
   pair_kernel<PREC, MODE><<<(unsigned)grid, Cfg<PREC>::NT, smem, s>>>(a);
   return cudaGetLastError();

@@ -18,6 +18,71 @@ extern template cudaError_t launch_pairs<1, MODE_NTIME>(const PairArgs &, int, c
 
 constexpr int SORT_CAP = 4096;
 
+// Contact candidates of the FP32 mode, decided in binary64: the feature the
+// FP32 pass found closest (its binary64 value within eps_pair makes the
+// pair's binary64 distance within it), else the full binary64 triangle
+// distance.  The pose of both particles at the pair's evaluation time is
+// recomputed here exactly as the pair kernel computes it.  Accepted
+// candidates get their binary64 distance and points and are counted per
+// pair; rejected ones are marked (pair index -1).
+__global__ void __launch_bounds__(256) contact_verify(const PairArgs A) {
+  __shared__ double rc[POSE_TERMS + 1], rs[POSE_TERMS + 1];
+  if (threadIdx.x == 0) pose_reciprocals(rc, rs);
+  __syncthreads();
+  using GD = Geo<OpsD>;
+  using D = OpsD;
+  const int64_t nst = min((int64_t)*A.st_count, A.st_cap);
+  const int64_t n = A.n;
+  const double *st = A.st;
+  unsigned long long n64 = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nst; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pk = A.st_keys[3 * e];
+    const int a = A.st_keys[3 * e + 1], b = A.st_keys[3 * e + 2];
+    const int feat = int(A.st_geom[7 * e]);
+    const int64_t i = A.pairs[2 * pk], j = A.pairs[2 * pk + 1];
+    const double eps = D::add(st[15 * n + i], st[15 * n + j]);
+    double t;
+    if (A.t_eval) {
+      t = A.t_eval[pk];
+    } else {  // the pair start, as the pair kernel sets it
+      const double ti = st[13 * n + i], tj = st[13 * n + j];
+      const bool si = A.is_static && A.is_static[i], sj = A.is_static && A.is_static[j];
+      t = (sj && !si) ? ti : ((si && !sj) ? tj : (ti < tj ? ti : tj));
+    }
+    double RA[9], XA[3], RB[9], XB[3];
+    pose_exact(st, n, i, t, rc, rs, RA, XA);
+    pose_exact(st, n, j, t, rc, rs, RB, XB);
+    const int64_t oa = A.tri_off[i], ob = A.tri_off[j];
+    V3<double> X[3], Y[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float4 f = A.tris[q * A.n_tris + oa + a], g = A.tris[q * A.n_tris + ob + b];
+      X[q] = to_world_exact(RA, XA, f.x, f.y, f.z);
+      Y[q] = to_world_exact(RB, XB, g.x, g.y, g.z);
+    }
+    V3<double> pa, pb;
+    double e2 = GD::feature_dist2(feat, X, Y, pa, pb);
+    ++n64;
+    double dd = D::sqrt(e2);
+    if (!(dd <= eps)) {
+      e2 = GD::tri_dist2(X, Y, pa, pb);
+      dd = D::sqrt(e2);
+    }
+    if (dd <= eps) {
+      atomicAdd(reinterpret_cast<unsigned long long *>(&A.pc[pk]), 1ull);
+      double *gg = A.st_geom + 7 * e;
+      gg[0] = dd;
+      gg[1] = pa.x; gg[2] = pa.y; gg[3] = pa.z;
+      gg[4] = pb.x; gg[5] = pb.y; gg[6] = pb.z;
+    } else {
+      A.st_keys[3 * e] = -1;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) n64 += __shfl_xor_sync(0xffffffffu, n64, o);
+  if ((threadIdx.x & 31) == 0 && n64) atomicAdd(&A.stats[ST_FP64], n64);
+}
+
 __global__ void contact_scatter(const int32_t *st_keys, const unsigned long long *st_count, int64_t st_cap,
                                 const int64_t *po, int32_t *pcur, int32_t *sidx, int64_t cap,
                                 uint32_t *err) {
@@ -25,6 +90,7 @@ __global__ void contact_scatter(const int32_t *st_keys, const unsigned long long
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nst;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int32_t pk = st_keys[3 * e];
+    if (pk < 0) continue;  // a candidate the binary64 decision rejected
     const int64_t slot = po[pk] + atomicAdd(&pcur[pk], 1);
     if (slot < cap) sidx[slot] = int32_t(e);
   }
@@ -105,11 +171,15 @@ __global__ void __launch_bounds__(256) contact_sort(const int32_t *st_keys, cons
   }
 }
 
+// The number of contacts; if the staging area overflowed, the number staged
+// instead (FP32 mode: candidates, at least the contacts), a capacity that
+// suffices for calling again
 __global__ void contact_total(const int64_t *total, const unsigned long long *st_count, int64_t st_cap,
                               int64_t *n_contacts, uint32_t *err) {
   const int64_t t = *total;
-  *n_contacts = t;
-  if ((int64_t)*st_count > st_cap) set_err(err, ERR_CAPACITY);
+  const int64_t staged = (int64_t)*st_count;
+  *n_contacts = staged > st_cap ? (staged > t ? staged : t) : t;
+  if (staged > st_cap) set_err(err, ERR_CAPACITY);
 }
 
 // Tiles of the particles with more than one tile, listed as (particle, tile)
@@ -285,6 +355,8 @@ PairArgs make_args(const dem_particles &P, const int32_t *pairs, int64_t max_pai
   a.err = S.err;
   a.stats = S.stats;
   a.wait_polls = S.wait_polls;
+  a.ilg = S.ilg;
+  a.ilg_cap = S.ilg_cap;
   return a;
 }
 
@@ -314,8 +386,13 @@ cudaError_t finish_narrow(int prec, PairArgs &a, const dem_particles &P, const i
     trace_end(S, rec, s);
     S.launches += 1;
   }
-  // per-pair offsets, scatter, sort
+  // per-pair offsets, scatter, sort (FP32 mode: the candidates decided in
+  // binary64 first)
   const int rec_c = trace_begin(S, TR_CONTACTS, s);
+  if (prec == 0 && max_pairs > 0) {
+    contact_verify<<<num_sms * 8, 256, 0, s>>>(a);
+    S.launches += 1;
+  }
   int64_t *total = S.tmp;
   if (max_pairs > 0) {
     S.launches += scan_exclusive_i64(S.pc, S.po, max_pairs, total, S.scan_part, s);

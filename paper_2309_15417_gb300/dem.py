@@ -54,7 +54,7 @@ class DemError(RuntimeError):
 class dem_config(C.Structure):
     _fields_ = [("K", C.c_int32), ("bisect_tol", C.c_double), ("precision", C.c_int32),
                 ("ctime_method", C.c_int32), ("max_particles", C.c_int64), ("max_pairs", C.c_int64),
-                ("max_contacts", C.c_int64), ("max_triangles", C.c_int64)]
+                ("max_contacts", C.c_int64), ("max_triangles", C.c_int64), ("list_spill", C.c_int64)]
 
 
 class dem_particles(C.Structure):
@@ -200,11 +200,11 @@ def _check(ctx, rc):
 # ------------------------------------------------------------------ C-ABI mirrors
 
 def dem_create(K=8, tol=1e-3, precision=DEM_PREC_FP32_FIXUP, max_particles=65536, max_pairs=1 << 20,
-               max_contacts=1 << 20, max_triangles=0, ctime_method=0):
+               max_contacts=1 << 20, max_triangles=0, ctime_method=0, list_spill=0):
     L = load()
     cfg = dem_config(K=K, bisect_tol=tol, precision=precision, ctime_method=ctime_method,
-                     max_particles=max_particles,
-                     max_pairs=max_pairs, max_contacts=max_contacts, max_triangles=max_triangles)
+                     max_particles=max_particles, max_pairs=max_pairs, max_contacts=max_contacts,
+                     max_triangles=max_triangles, list_spill=list_spill)
     h = C.c_void_p()
     rc = L.dem_create(C.byref(cfg), C.byref(h))
     if rc != 0:
@@ -352,12 +352,13 @@ class Context:
     """Owns a dem_ctx and output buffers sized for its capacities."""
 
     def __init__(self, K=8, tol=1e-3, precision=DEM_PREC_FP32_FIXUP, max_particles=65536, max_pairs=1 << 20,
-                 max_contacts=1 << 20, max_triangles=0, ctime_method=0, device="cuda"):
+                 max_contacts=1 << 20, max_triangles=0, ctime_method=0, device="cuda", list_spill=0):
         import torch
         self.device = torch.device(device)
         self.max_pairs = int(max_pairs)
         self.max_contacts = int(max_contacts)
-        self.h = dem_create(K, tol, precision, max_particles, max_pairs, max_contacts, max_triangles, ctime_method)
+        self.h = dem_create(K, tol, precision, max_particles, max_pairs, max_contacts, max_triangles, ctime_method,
+                            list_spill)
         z = lambda *s, dt: torch.zeros(*s, dtype=dt, device=self.device)
         self.pairs = z(self.max_pairs, 2, dt=torch.int32)
         self.n_pairs = z(1, dt=torch.int64)

@@ -58,7 +58,8 @@ def test_noalloc_rejects_null_arguments_before_any_launch(L):
 
 @pytest.mark.parametrize("field,value", [("K", -1), ("bisect_tol", -1e-3), ("precision", 7), ("ctime_method", 5),
                                          ("max_particles", -1), ("max_pairs", -5), ("max_contacts", -1),
-                                         ("max_triangles", -1), ("max_pairs", 1 << 40)])
+                                         ("max_triangles", -1), ("max_pairs", 1 << 40), ("list_spill", -1),
+                                         ("list_spill", (1 << 24) + 1)])
 def test_bad_configuration_is_rejected_before_any_allocation(L, field, value):
     cfg = D.dem_config()
     setattr(cfg, field, value)

@@ -57,9 +57,10 @@ def test_contact_capacity_exceeded_then_recovered(dem):
     small.build_candidates(sc)
     small.narrow_phase(sc)
     assert _status(dem, small) == dem.DEM_ERR_CAPACITY
-    assert int(small.n_contacts.item()) == nc
+    need = int(small.n_contacts.item())  # a sufficient capacity (FP32: staged candidates)
+    assert need >= nc
     small.close()
-    big = _ctx(dem, w, max_contacts=nc)
+    big = _ctx(dem, w, max_contacts=need)
     big.build_candidates(sc)
     big.narrow_phase(sc)
     assert _status(dem, big) == dem.DEM_OK

@@ -15,10 +15,11 @@ pytestmark = pytest.mark.gpu
 PRECS = [0, 1]
 
 
-def _gpu_narrowing(dem, w, pairs, prec):
+def _gpu_narrowing(dem, w, pairs, prec, list_spill=0):
     import torch
     c = dem.Context(K=w.K, tol=w.tol, precision=prec, max_particles=max(w.n, 16), max_pairs=max(len(pairs), 1),
-                    max_contacts=1 << 18, max_triangles=w.n_tris, ctime_method=dem.DEM_CTIME_NARROWING)
+                    max_contacts=1 << 18, max_triangles=w.n_tris, ctime_method=dem.DEM_CTIME_NARROWING,
+                    list_spill=list_spill)
     sc = dem.Scene.from_workload(w)
     pt = torch.from_numpy(np.ascontiguousarray(pairs, np.int32).reshape(-1, 2)).cuda()
     c.collision_times(sc, pairs=pt)
@@ -30,9 +31,9 @@ def _gpu_narrowing(dem, w, pairs, prec):
     return out
 
 
-def _check(dem, w, pairs, prec):
+def _check(dem, w, pairs, prec, list_spill=0):
     o = oracle.collision_times_narrowing(w, pairs)
-    g = _gpu_narrowing(dem, w, pairs, prec)
+    g = _gpu_narrowing(dem, w, pairs, prec, list_spill)
     assert np.array_equal(g["status"], o["status"])
     assert np.array_equal(g["t_coll"], o["t_coll"])
     assert np.array_equal(g["tri_ab"], o["tri_ab"])
@@ -70,24 +71,29 @@ def test_narrowing_static_floor(dem, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_narrowing_list_overflow(dem, prec):
-    """Fast head-on 320-triangle icospheres: the pair-interval list overflows
-    and every narrowing iteration runs over all triangle pairs."""
+@pytest.mark.parametrize("spill", [0, 1])
+def test_narrowing_list_overflow(dem, prec, spill):
+    """Fast head-on 320-triangle icospheres: the pair-interval list outgrows
+    its 512 shared-memory entries; with the default global spill the list
+    holds them, with a one-entry spill it overflows and every narrowing
+    iteration runs over all triangle pairs."""
     for frac in (0.3, 0.9):
         w = W.injected_head_on(0.1 + frac * 0.8, 800.0, 0.05, 1e-3, subdiv=2)
-        o = _check(dem, w, np.array([[0, 1]], np.int32), prec)
+        o = _check(dem, w, np.array([[0, 1]], np.int32), prec, list_spill=spill)
         assert o["status"][0] == 2
 
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("seed", [0, 1])
-def test_narrowing_fast_rotating_packing(dem, seed, prec):
+@pytest.mark.parametrize("spill", [0, 1])
+def test_narrowing_fast_rotating_packing(dem, seed, prec, spill):
     """v, w ~ N(0, 150): the narrowing's motion bound (~0.3) lets far more
-    triangle pairs into the pair-interval list than it holds, so the
-    iterations visit every triangle pair, pruned by bounding spheres and (FP32
-    mode) FP32 distances at ts."""
+    triangle pairs into the pair-interval list than its shared-memory part
+    holds (the global spill takes them; with a one-entry spill the iterations
+    visit every triangle pair, pruned by bounding spheres and, in the FP32
+    mode, certified FP32 lower bounds at ts)."""
     w = W.dense_packing(seed, nside=4, vsig=150.0, wsig=150.0)
-    o = _check(dem, w, oracle.broad_phase(w), prec)
+    o = _check(dem, w, oracle.broad_phase(w), prec, list_spill=spill)
     assert (o["status"] == 2).sum() >= 3
 
 
