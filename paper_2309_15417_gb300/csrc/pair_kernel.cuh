@@ -1150,7 +1150,10 @@ struct Cta {
             ok = pick && gd <= s.eps;
           }
           yes = ok;
-          if (!apart && !__any_sync(0xffffffffu, ok)) why |= WHY_DEC;
+          // every lane votes (a vote behind a lane-dependent && would leave
+          // the lanes that skip it out of a full-mask collective)
+          const bool any_ok = __any_sync(0xffffffffu, ok);
+          if (!apart && !any_ok) why |= WHY_DEC;
         }
         if (CONTACTS) put_candidates(have && !apart, pk, ta * TT + a, tb * TT + b, feat);
         if (ARGMIN) {
@@ -1892,7 +1895,8 @@ struct Cta {
           const double e2 = exact_warp(__shfl_sync(0xffffffffu, ag, src), __shfl_sync(0xffffffffu, bg, src), qa, qb,
                                        true);
           ++n64;
-          if (OpsD::sqrt(e2) <= s.eps) yes_any = true;
+          // lane 0's value: the loop condition stays warp-uniform whatever e2 is
+          if (__shfl_sync(0xffffffffu, OpsD::sqrt(e2) <= s.eps ? 1 : 0, 0)) yes_any = true;
         }
         if (yes_any) break;
       }
