@@ -28,7 +28,7 @@ N > 1 (launched with torch.distributed.run): every rank runs an independent
 replica (its own seeded column) -- weak scaling, no collective on the data
 path; value = particle-steps of all ranks / max time over ranks.
 --impl reference: the FP64 CPU oracle on this machine's cores, each step one
-sweep of a sub-column (6^3 particles over its floor patch).
+sweep of a sub-column (10^3 particles over its floor patch).
 """
 from __future__ import annotations
 
@@ -58,7 +58,7 @@ WORKLOAD = ("settling column: 100^3 icospheres (half 80, half 320 triangles, r=1
 L2_BYTES = 129 * 1024 * 1024
 FLUSH_BYTES = 512 * 1024 * 1024
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "pair_kernel_settling_column.md")
-REF_SIDE = 6  # sub-column of the oracle samples
+REF_SIDE = 10  # sub-column of the oracle samples (about 1 s per oracle sweep on 16 cores)
 
 
 def parse():
@@ -461,12 +461,14 @@ def e2e_leg(dem, run, steps):
         run.sweep()
         h_cur.copy_(run.sc.state, non_blocking=True)
         h_old.copy_(run.old, non_blocking=True)
-        torch.cuda.synchronize()
-        m = int(h_outs[1][0])
+        # this step's counts first (the pinned buffers hold the previous step's)
+        h_outs[1].copy_(c.n_pairs)
+        h_outs[11].copy_(c.n_contacts)
+        m = min(int(h_outs[1][0]), m_cap)
         nc = min(int(h_outs[11][0]), c.max_contacts)
         b = 2 * h_cur.numel() * 8
         for t, h in zip(outs, h_outs):  # outputs, only their filled parts
-            n = m if t.shape[0] == m_cap else t.shape[0]
+            n = min(m, t.shape[0]) if t.shape[0] == m_cap else t.shape[0]
             h[:n].copy_(t[:n], non_blocking=True)
             b += n * t[:1].numel() * t.element_size()
         h_ck[:nc].copy_(c.contacts[:nc], non_blocking=True)
@@ -774,7 +776,7 @@ def narrowing_leg(args, dem, W, dev, reps=10):
 # ------------------------------------------------------------------ CPU oracle
 
 def oracle_sweeps(seed, sweeps, n_threads=None):
-    """The FP64 oracle's sweeps of a 6^3 sub-column over its floor patch (the
+    """The FP64 oracle's sweeps of a REF_SIDE^3 sub-column over its floor patch (the
     same particles, spacing, floor quads and parameters as the full column).
     Returns (advances, seconds, threads, description)."""
     import oracle
@@ -796,10 +798,13 @@ def oracle_sweeps(seed, sweeps, n_threads=None):
     return adv, secs, nt, desc
 
 
+CPU_SWEEPS = 12  # oracle sweeps of the cpu_baseline sample (10-30 s of host work)
+
+
 def cpu_baseline(args):
-    adv, secs, nt, desc = oracle_sweeps(args.seed, 3)
+    adv, secs, nt, desc = oracle_sweeps(args.seed, CPU_SWEEPS)
     v = sum(adv) / sum(secs)
-    return {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": desc + "; 3 sweeps",
+    return {"value": v, "unit": UNIT, "cores": nt, "kind": "oracle", "sample": desc + f"; {CPU_SWEEPS} sweeps",
             "seconds": sum(secs)}
 
 
