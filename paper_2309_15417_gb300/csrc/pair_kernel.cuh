@@ -1258,11 +1258,14 @@ struct Cta {
   // scanned this tile pair (seen0) -- a tile pair that pass 0's tile test
   // culled has never had any of its pairs evaluated.
   template <bool DECIDE, bool ARGMIN, bool CONTACTS>
-  __device__ void scan_tiles(int ta, int tb, bool pass1, T th0, int64_t pk, bool seen0 = true) {
+  __device__ void scan_tiles(int ta, int tb, bool pass1, T th0, int64_t pk, bool seen0 = true, bool merged = false) {
     const int na = min(TT, s.nA - ta * TT), nb = min(TT, s.nB - tb * TT);
     const int nga = (na + G - 1) / G, ngb = (nb + G - 1) / G;
     // culling margin: FP32 spheres of the tiles' FP32 vertices, the tile's scale
     const T Elb = T(PREC == 0 ? s.Et : s.Elb);
+    // a merged pass (closest pair, contacts and interval list in one scan)
+    // never culls below the first pass's threshold th0
+    const T lift = merged ? th0 : -O::inf();
     if (tid == 0) {
       s.ngp = 0;
       s.gpnext = 0;
@@ -1270,7 +1273,7 @@ struct Cta {
     __syncthreads();
     // level 1: group pairs (32 x 32 triangles)
     {
-      const T gth = pass1 ? T(bitsd(s.bound)) + Elb : th0 + Elb;
+      const T gth = pass1 ? fmax(T(bitsd(s.bound)), lift) + Elb : th0 + Elb;
       for (int q = tid; q < nga * ngb; q += NT) {
         const int ga = q / ngb, gb = q - ga * ngb;
         const T dx = s.GA[0][ga] - s.GB[0][gb], dy = s.GA[1][ga] - s.GB[1][gb], dz = s.GA[2][ga] - s.GB[2][gb];
@@ -1305,7 +1308,7 @@ struct Cta {
       if (pass1) {
         unsigned long long bb = lane == 0 ? *(volatile unsigned long long *)&s.bound : 0ull;
         bb = __shfl_sync(0xffffffffu, bb, 0);
-        bnd = T(bitsd(bb));
+        bnd = fmax(T(bitsd(bb)), lift);
         if (double(s.gplb[p]) > double(bnd) + double(Elb)) break;  // sorted: later ones fail too
       }
       const uint32_t gpe = s.gp[p];
@@ -1350,7 +1353,7 @@ struct Cta {
               atomicMin(&s.bound, dbits(ub));
             }
             __syncwarp();
-            const T bn = T(bitsd(*(volatile unsigned long long *)&s.bound)) + Elb;
+            const T bn = fmax(T(bitsd(*(volatile unsigned long long *)&s.bound)) + Elb, lift);
             const T t1 = bn + ar + br;
             cand = valid && d2c <= t1 * t1 && !(seen0 && d2c <= t0 * t0);
           }
@@ -1516,8 +1519,50 @@ struct Cta {
       s.ilcol = extra > 0.0 ? 1 : 0;
     }
     __syncthreads();
-    const bool multi = nta > 1 || ntb > 1;
-    const int nq = nta * ntb;
+    // Closest pair (with contacts and the interval list on the way) of two
+    // single-tile meshes in the FP32 mode: one scan whose culling threshold is
+    // the larger of th0 and the shrinking closest-pair bound, so every
+    // triangle pair within th0 is evaluated once and the closest pair is
+    // searched in the same traversal.  Large meshes (a floor) keep the two
+    // passes, and so does the FP64 mode: the closest-pair bound starts loose
+    // (tile and triangle-centroid distances), and a first pass at th0 often
+    // settles the pair alone, which pays where every evaluation is binary64.
+    if (PREC == 0 && !DECIDE && ARGMIN && nta == 1 && ntb == 1) {
+      for (int attempt = 0;; ++attempt) {
+        const bool ok = attempt == 0 ? argmin_pass<CONTACTS>(th0, nta, ntb, pk, true)
+                                     : argmin_pass<false>(th0, nta, ntb, pk, true);
+        if (!ok) return false;
+        if (tid == 0) s.ilcol = 0;
+        const double mh2 = block_min(double(mw));
+        if (tid == 0) s.cull = fmax(bitsd(s.bound), double(th0));
+        __syncthreads();
+        if constexpr (PREC == 0) {
+          argmin_list(mh2);
+          if (s.redo && attempt < 2) {
+            // the binary64 reference lies beyond the slack the candidates or
+            // the culling used: search again, argmin alone, with a wider one
+            __syncthreads();
+            if (tid == 0) {
+              s.Eam = attempt == 0 ? s.Eam * 1024.0 : OpsD::inf();
+              s.nac = 0;
+              s.redo = 0;
+            }
+            mw = O::inf();
+            bd2 = OpsD::inf();
+            bkey = ~0ull;
+            wbd2 = OpsD::inf();
+            wbkey = ~0ull;
+            qn = 0;
+            __syncthreads();
+            continue;
+          }
+        }
+        reduce_best();
+        if (tid == 0) s.mhat = mh2;
+        __syncthreads();
+        return false;
+      }
+    }
     if (!pass0<DECIDE, ARGMIN, CONTACTS>(th0, nta, ntb, pk)) return false;
     if (tid == 0) s.ilcol = 0;
     if (DECIDE && ARGMIN) {
@@ -1534,44 +1579,7 @@ struct Cta {
         if (!complete && nta > 0 && ntb > 0) {
           if (tid == 0) s.bound = dbits(mh + slack);  // inf if nothing seen
           __syncthreads();
-          // the nearest tile pair first (it tightens the bound), then the
-          // others in chunks tested in parallel against the bound at the
-          // chunk's start; a selected tile pair is tested again against the
-          // bound as it is when its turn comes
-          const int q0 = multi ? bound_by_tiles(nta, ntb) : 0;
-          {
-            const int ta = q0 / ntb, tb = q0 - (q0 / ntb) * ntb;
-            // whether pass 0 scanned this tile pair (the same test, same pose)
-            const bool seen0 = !multi || __syncthreads_or(tid == 0 && tile_near(ta, tb, double(th0)));
-            if (!load_tiles(ta, tb)) return false;
-            frames(ta, tb);
-            if (tid == 0) stat(ST_TILES, 1);
-            scan_tiles<false, true, false>(ta, tb, true, th0, pk, seen0);
-          }
-          for (int c0 = 0; multi && c0 < nq; c0 += NT) {
-            const int q = c0 + tid;
-            const bool near = q < nq && q != q0 &&
-                              tile_near(q / ntb, q - (q / ntb) * ntb, bitsd(*(volatile unsigned long long *)&s.bound));
-            const uint32_t m = __ballot_sync(0xffffffffu, near);
-            if (lane == 0) s.tmask[w] = m;
-            __syncthreads();
-            for (int wq = 0; wq < NW; ++wq) {
-              uint32_t mm = s.tmask[wq];
-              while (mm) {
-                const int qq = c0 + wq * 32 + __ffs(mm) - 1;
-                mm &= mm - 1;
-                const int ta = qq / ntb, tb = qq - ta * ntb;
-                if (!__syncthreads_or(tid == 0 && tile_near(ta, tb, bitsd(*(volatile unsigned long long *)&s.bound))))
-                  continue;
-                const bool seen0 = __syncthreads_or(tid == 0 && tile_near(ta, tb, double(th0)));
-                if (!load_tiles(ta, tb)) return false;
-                frames(ta, tb);
-                if (tid == 0) stat(ST_TILES, 1);
-                scan_tiles<false, true, false>(ta, tb, true, th0, pk, seen0);
-              }
-            }
-            __syncthreads();
-          }
+          if (!argmin_pass<false>(th0, nta, ntb, pk, false)) return false;
         }
         const double mh2 = block_min(double(mw));
         if (tid == 0) s.cull = complete ? double(th0) : bitsd(s.bound);
@@ -1612,6 +1620,63 @@ struct Cta {
     const bool f = DECIDE ? (*(volatile int *)&s.found != 0) : false;
     __syncthreads();
     return f;
+  }
+
+  // The closest-pair search over the tile pairs: the nearest tile pair first
+  // (it tightens the bound), then the others in chunks tested in parallel
+  // against the bound at the chunk's start; a selected tile pair is tested
+  // again against the bound as it is when its turn comes.  After a first
+  // pass (merged = false) s.bound holds its minimum plus the slack and tile
+  // pairs that pass scanned skip the triangle pairs it evaluated; a merged
+  // pass starts from an unbounded search and never culls below th0.  False
+  // if a tile copy timed out.
+  template <bool CONTACTS>
+  __device__ bool argmin_pass(T th0, int nta, int ntb, int64_t pk, bool merged) {
+    if (nta <= 0 || ntb <= 0) return true;
+    const bool multi = nta > 1 || ntb > 1;
+    const int nq = nta * ntb;
+    if (merged) {
+      if (tid == 0) s.bound = dbits(OpsD::inf());
+      __syncthreads();
+    }
+    const double lift = merged ? double(th0) : -OpsD::inf();
+    const int q0 = multi ? bound_by_tiles(nta, ntb) : 0;
+    {
+      const int ta = q0 / ntb, tb = q0 - (q0 / ntb) * ntb;
+      // whether a first pass scanned this tile pair (the same test, same pose)
+      const bool seen0 = !merged && (!multi || __syncthreads_or(tid == 0 && tile_near(ta, tb, double(th0))));
+      if (!load_tiles(ta, tb)) return false;
+      frames(ta, tb);
+      if (tid == 0) stat(ST_TILES, 1);
+      scan_tiles<false, true, CONTACTS>(ta, tb, true, th0, pk, seen0, merged);
+    }
+    for (int c0 = 0; multi && c0 < nq; c0 += NT) {
+      const int q = c0 + tid;
+      const bool near = q < nq && q != q0 &&
+                        tile_near(q / ntb, q - (q / ntb) * ntb,
+                                  fmax(bitsd(*(volatile unsigned long long *)&s.bound), lift));
+      const uint32_t m = __ballot_sync(0xffffffffu, near);
+      if (lane == 0) s.tmask[w] = m;
+      __syncthreads();
+      for (int wq = 0; wq < NW; ++wq) {
+        uint32_t mm = s.tmask[wq];
+        while (mm) {
+          const int qq = c0 + wq * 32 + __ffs(mm) - 1;
+          mm &= mm - 1;
+          const int ta = qq / ntb, tb = qq - ta * ntb;
+          if (!__syncthreads_or(tid == 0 && tile_near(ta, tb, fmax(bitsd(*(volatile unsigned long long *)&s.bound),
+                                                                   lift))))
+            continue;
+          const bool seen0 = !merged && __syncthreads_or(tid == 0 && tile_near(ta, tb, double(th0)));
+          if (!load_tiles(ta, tb)) return false;
+          frames(ta, tb);
+          if (tid == 0) stat(ST_TILES, 1);
+          scan_tiles<false, true, CONTACTS>(ta, tb, true, th0, pk, seen0, merged);
+        }
+      }
+      __syncthreads();
+    }
+    return true;
   }
 
   // The first pass of an evaluation: every tile pair whose tile bound is
