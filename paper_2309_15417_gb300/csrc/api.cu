@@ -164,6 +164,7 @@ dem_status dem_create(const dem_config *cfg, dem_ctx **out) {
             alloc(c, &S.bucket_start, S.table_size) && alloc(c, &S.bucket_cur, S.table_size) &&
             alloc(c, &S.bucket_ids, np) && alloc(c, &S.bucket_sph, np) && alloc(c, &S.bucket_sph32, np) &&
             alloc(c, &S.bucket_cell, np) && alloc(c, &S.pcnt, np) && alloc(c, &S.poff, np) &&
+            alloc(c, &S.pcache, (size_t)dem::PCACHE * (size_t)np) && alloc(c, &S.pcache_ok, np) &&
             alloc(c, &S.rho_max, 1) && alloc(c, &S.static_ids, np) && alloc(c, &S.n_static, 1) &&
             alloc(c, &S.spose, 12 * np) && alloc(c, &S.sbox, 6 * np) && alloc(c, &S.sbox32, 6 * np) && alloc(c, &S.st_keys, 3 * nc) && alloc(c, &S.st_geom, 7 * nc) &&
             alloc(c, &S.st_count, 1) && alloc(c, &S.pc, nq) && alloc(c, &S.po, nq) && alloc(c, &S.pcur, nq) &&

@@ -271,7 +271,10 @@ __device__ __noinline__ bool hose_meet(const double *cur, const double *old, int
 // neighbour cell c, then the lanes share the static boxes; counts are
 // combined with warp prefix sums.  WRITE: the partners are written at the
 // particle's offset and sorted by partner index (bitonic in registers for up
-// to 32).
+// to 32).  With a partner cache (pc, pc_ok), the count pass also keeps a
+// particle's partners when at most PCACHE of them, at most two grid partners
+// per lane and one static partner per lane, were found; the write pass then
+// copies them instead of scanning the cells again.
 __device__ __forceinline__ int warp_incl_sum(int v, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -287,7 +290,8 @@ __global__ void __launch_bounds__(256, 6) k_pairs(int64_t n, const double *st, c
                         const int32_t *bcnt, const int64_t *bstart, const int32_t *ids,
                         uint32_t mask, const int32_t *static_ids, const int32_t *n_static,
                         const unsigned long long *sbox, const double *hose_old, int64_t *pcnt,
-                        const int64_t *poff, int32_t *pairs, int64_t cap, const int64_t *n_pairs, uint32_t *err) {
+                        const int64_t *poff, int32_t *pairs, int64_t cap, const int64_t *n_pairs,
+                        int32_t *pc, uint8_t *pc_ok, uint32_t *err) {
   if (WRITE && blockIdx.x == 0 && threadIdx.x == 0 && *n_pairs > cap) set_err(err, ERR_CAPACITY);
   const int lane = threadIdx.x & 31;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -295,6 +299,23 @@ __global__ void __launch_bounds__(256, 6) k_pairs(int64_t n, const double *st, c
   const int64_t nm = n - ns;  // moving particles, all in bucket order
   for (int64_t r = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; r < nm; r += nwarp) {
     const int64_t i = ids[r];
+    if (WRITE && pc_ok && pc_ok[i]) {
+      // the count pass kept every partner: copy and sort them
+      const int64_t o = poff[i];
+      const int tot = int(pcnt[i]);
+      int32_t key = lane < tot ? pc[(int64_t)PCACHE * i + lane] : 0x7fffffff;
+      for (int k = 2; k <= 32; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          const int32_t other = __shfl_xor_sync(0xffffffffu, key, j);
+          const bool lower = (lane & j) == 0, up = (lane & k) == 0;
+          key = (lower == up) ? min(key, other) : max(key, other);
+        }
+      if (lane < tot && o + lane < cap) {
+        pairs[2 * (o + lane)] = int32_t(i);
+        pairs[2 * (o + lane) + 1] = key;
+      }
+      continue;
+    }
     const Sphere4 si = bsph[r];
     const float4 si32 = bsph32[r];
     const int4 ci = bcell[r];
@@ -356,13 +377,36 @@ __global__ void __launch_bounds__(256, 6) k_pairs(int64_t n, const double *st, c
       return gg <= D::mul(si.w, si.w);
     };
     int c = 0, cs = 0;
-    for (int64_t q = b0; q < b1; ++q) c += is_pair(q, ids[q]) ? 1 : 0;
-    for (int q = lane; q < ns; q += 32) cs += meets_box(q) ? 1 : 0;
+    int32_t g0 = -1, g1 = -1, s0 = -1;  // the count pass's first partners of this lane
+    for (int64_t q = b0; q < b1; ++q) {
+      const int32_t j = ids[q];
+      if (is_pair(q, j)) {
+        if (c == 0) g0 = j;
+        if (c == 1) g1 = j;
+        ++c;
+      }
+    }
+    for (int q = lane; q < ns; q += 32)
+      if (meets_box(q)) {
+        if (cs == 0) s0 = static_ids[q];
+        ++cs;
+      }
     const int inc = warp_incl_sum(c, lane), incs = warp_incl_sum(cs, lane);
     const int tgrid = __shfl_sync(0xffffffffu, inc, 31);
     const int total = tgrid + __shfl_sync(0xffffffffu, incs, 31);
     if (!WRITE) {
       if (lane == 0) pcnt[i] = total;
+      if (pc) {
+        // every lane votes; the cache holds the list only if it is complete
+        const bool fits = __all_sync(0xffffffffu, c <= 2 && cs <= 1) && total <= PCACHE;
+        if (fits) {
+          int32_t *row = pc + (int64_t)PCACHE * i;
+          if (c > 0) row[inc - c] = g0;
+          if (c > 1) row[inc - c + 1] = g1;
+          if (cs > 0) row[tgrid + incs - cs] = s0;
+        }
+        if (lane == 0) pc_ok[i] = fits ? 1 : 0;
+      }
       continue;
     }
     const int64_t o = poff[i];
@@ -441,12 +485,12 @@ cudaError_t launch_broad(const dem_particles &P, int32_t *pairs, int64_t cap, in
   k_pairs<false><<<wgrid, tb, 0, s>>>(n, P.state, S.bucket_sph, S.bucket_sph32, S.bucket_cell, S.sbox32,
                                       S.bucket_cnt, S.bucket_start,
                                       S.bucket_ids, mask, S.static_ids, S.n_static, S.sbox, hose_old, S.pcnt,
-                                      nullptr, nullptr, 0, nullptr, S.err);
+                                      nullptr, nullptr, 0, nullptr, S.pcache, S.pcache_ok, S.err);
   S.launches += 2 + scan_exclusive_i64(S.pcnt, S.poff, n, n_pairs, S.scan_part, s);
   k_pairs<true><<<wgrid, tb, 0, s>>>(n, P.state, S.bucket_sph, S.bucket_sph32, S.bucket_cell, S.sbox32,
                                      S.bucket_cnt, S.bucket_start,
-                                     S.bucket_ids, mask, S.static_ids, S.n_static, S.sbox, hose_old, nullptr,
-                                     S.poff, pairs, cap, n_pairs, S.err);
+                                     S.bucket_ids, mask, S.static_ids, S.n_static, S.sbox, hose_old, S.pcnt,
+                                     S.poff, pairs, cap, n_pairs, S.pcache, S.pcache_ok, S.err);
   S.launches += 1;
   trace_end(S, rec, s);
   return cudaGetLastError();

@@ -107,6 +107,8 @@ struct Scratch {
   int4 *bucket_cell;              // [n] their cells, same order
   int64_t *pcnt;                  // [n] candidates per particle
   int64_t *poff;                  // [n]
+  int32_t *pcache = nullptr;      // [n][PCACHE] partners found by the count pass (optional)
+  uint8_t *pcache_ok = nullptr;   // [n] 1: the particle's partners are all in pcache
   unsigned long long *rho_max;    // [1] (bits of a non-negative double)
   int32_t *static_ids;            // [n] static particles, in order of discovery
   int32_t *n_static;              // [1]
@@ -142,6 +144,7 @@ struct Scratch {
 
 constexpr int TILE_TRIS = 320;                 // triangles per shared-memory tile of the pair kernel
 constexpr int MAX_PAIR_CTAS_PER_SM = 4;        // persistent CTAs of the pair kernel per SM, at most
+constexpr int PCACHE = 8;                      // partners per particle the broad phase's count pass keeps
 constexpr int64_t SCAN_BLOCK = 2048;           // elements per scan block
 constexpr int64_t SCAN_PART_CAP = 4096;        // partial sums (=> up to 8M elements)
 
