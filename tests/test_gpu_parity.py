@@ -297,6 +297,26 @@ def test_ctime_dense_full_size_sampled(dem, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_ctime_search_heavy_packing(dem, prec):
+    """The bench's search-heavy packing (14^3 icospheres of 320 triangles at
+    volume fraction 0.35, v ~ N(0,10), w ~ N(0,2), dt = 1e-2): most pairs
+    start apart and a fifth meet inside the step, so the samples and the
+    bisection do the work.  The GPU computes every candidate pair; every pair
+    that bisected (status 2) and a sample of the others equal the oracle."""
+    w = W.dense_packing(0, nside=14, phi=0.35, vsig=10.0, wsig=2.0, dt=1e-2)
+    pairs = oracle.broad_phase(w)
+    g = gpu_ctime(dem, w, pairs, prec)
+    rng = np.random.default_rng(3)
+    bis = np.nonzero(g["status"] == 2)[0]
+    assert len(bis) >= 100
+    idx = np.unique(np.concatenate([bis, rng.choice(len(pairs), 120, replace=False)]))
+    o = oracle.collision_times(w, pairs[idx])
+    assert np.array_equal(g["status"][idx], o["status"])
+    assert np.array_equal(g["t_coll"][idx], o["t_coll"])
+    assert np.array_equal(g["tri_ab"][idx], o["tri_ab"])
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_ctime_head_on_closed_form(dem, prec):
     for frac in (0.05, 0.5, 0.93):
         gap = 0.1 + frac * 1e-3
