@@ -155,11 +155,21 @@ def _profile_traffic():
     return float(m.group(1))
 
 
+def _code_only(path):
+    """A source file without its comments and blank lines: what the compiler
+    sees of it, so that a comment edit does not mark a profile stale."""
+    t = open(path, encoding="utf-8").read()
+    t = re.sub(r"/\*.*?\*/", "", t, flags=re.S)
+    t = re.sub(r"//[^\n]*", "", t)
+    return "\n".join(l.rstrip() for l in t.split("\n") if l.strip()).encode()
+
+
 def kernel_source_hash():
+    """sha256 of the pair kernel's code (pair_kernel.cuh, geom.cuh), comments
+    and blank lines removed."""
     csrc = os.path.join(ROOT, "paper_2309_15417_gb300", "csrc")
-    src = open(os.path.join(csrc, "pair_kernel.cuh"), "rb").read()
-    geo = open(os.path.join(csrc, "geom.cuh"), "rb").read()
-    return hashlib.sha256(src + geo).hexdigest()
+    return hashlib.sha256(_code_only(os.path.join(csrc, "pair_kernel.cuh")) +
+                          _code_only(os.path.join(csrc, "geom.cuh"))).hexdigest()
 
 
 def _rot(q):

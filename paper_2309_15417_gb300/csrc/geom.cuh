@@ -35,8 +35,10 @@ struct OpsF {
   static __device__ __forceinline__ float add(float a, float b) { return a + b; }
   static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
   static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
-  // hardware-approximate quotient and square root (a few ulp): the FP32
-  // results only have to stay inside the caller's error band
+  // hardware-approximate quotient and square root (a few ulp): FP32 closest
+  // points only choose the direction of a separation certificate (a lower
+  // bound whatever the direction) and rank candidates, so their accuracy
+  // decides how much binary64 work follows, never a result
   static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
   static __device__ __forceinline__ float sqrt(float a) {
     return a > 1e-30f ? a * rsqrtf(a) : __fsqrt_rn(a);  // tiny and denormal inputs: exact path

@@ -192,7 +192,7 @@ struct __align__(128) Smem {
   unsigned long long il[ILCAP];
   int nil, ilover, ilcol;
   uint32_t tmask[NW];                 // near tile pairs of a chunk, one ballot per warp
-  double ilthr;                       // distance threshold of the list (eps + delta + 2E)
+  double ilthr;                       // threshold of the list: FP32, on certificates, eps + delta + m64; FP64 th0
   double delta;                       // bound on the change of any distance over the interval
   double gR[GRID_MAX][2][9], gX[GRID_MAX][2][3];  // poses at the sample times
   unsigned long long bound;           // bits of a non-negative double
@@ -743,15 +743,15 @@ struct Cta {
   // The same binary64 triangle distance with one warp per triangle pair.
   // Lanes 0..5 run the six edge-triangle crossing tests in binary64.  Lanes
   // 8..13 (vertex-triangle) and 16..24 (edge-edge) first compute their
-  // feature distance in FP32 (A's frame); only features whose FP32 distance
-  // is within 2E of the smallest one are then recomputed in binary64: every
-  // feature that can attain the binary64 minimum is among them, so the
-  // minimum and its first attaining feature (sequential order, strict "<")
-  // are those of Geo<OpsD>::tri_dist2.  cross = false skips the crossing
-  // tests: the caller knows the FP32 distance of the pair exceeds 4E, so the
-  // binary64 distance is positive (|d32 - d64| <= E) and no crossing exists.
-  // a, b index triangles within
-  // particles i, j.  Every lane returns the result.
+  // feature in FP32 (A's frame) with its certificate; the feature closest in
+  // FP32 is recomputed in binary64 as the reference, then every feature whose
+  // certificate does not exceed the reference (plus m64): every feature that
+  // can attain the binary64 minimum is among them, so the minimum and its
+  // first attaining feature (sequential order, strict "<") are those of
+  // Geo<OpsD>::tri_dist2.  cross = false skips the crossing tests: the caller
+  // has certified the pair's binary64 distance positive, so no crossing
+  // exists.  a, b index triangles within particles i, j.  Every lane returns
+  // the result.
   __device__ __noinline__ double exact_warp(int a, int b, V3<double> &pa, V3<double> &pb, bool cross = true) const {
     using GF = Geo<OpsF>;
     V3<double> v{0.0, 0.0, 0.0};
